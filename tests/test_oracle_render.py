@@ -1,0 +1,154 @@
+"""Oracle pins for Mark / Compact / Resolve (Sec. 4.2, Sec. 4.4, Sec. 4.6) and the
+paper's closed-form MCU geometry (Sec. 3.1, Sec. 5.2, Sec. 5.3).
+
+* the set of marked MCUs equals a brute-force set computed here with numpy (fp32 index
+  arithmetic, the MCU formula of Sec. 4.2 with ceil for partial MCUs);
+* compact: ascending, unique, count = popcount(flags);
+* nearest colourise equals indexing the sequentially decoded texture (independent of
+  the random-access decode and of the needed set);
+* bilinear colourise is within 1 of an FP64 bilinear of the full decoded texture.
+"""
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden():
+    with open(os.path.join(GOLDEN, "paper_constants.json")) as f:
+        return {k: v["value"] for k, v in json.load(f).items() if not k.startswith("_")}
+
+
+def test_paper_mcu_geometry():
+    g = _golden()
+    mw = g["mcu_px_420"]
+    n = (4096 // mw) * (4096 // mw)
+    assert n == g["mcus_4096_420"]
+    assert n * g["dus_per_mcu_420"] == g["dus_4096_420"]
+    assert g["dus_per_mcu_420"] * 63 == g["acs_per_mcu"]
+    # the paper's side-table arithmetic (Sec. 5.3; it prints 160/9 truncated to 17.777)
+    trunc3 = lambda x: int(x * 1000) / 1000
+    assert trunc3((32 + 16 * 8) / 9) == g["index_bits_per_mcu"]
+    assert 3 * 12 == g["dc_bits_per_mcu"]
+    assert trunc3((32 + 16 * 8) / 9 + 3 * 12) == g["overhead_bits_per_mcu"]
+    assert round(g["overhead_bits_per_mcu"] / 256, 2) == g["overhead_bpp"]
+    kb = g["key_bits"]
+    assert kb["mcu"] + kb["tex"] + kb["mip"] == 32
+    assert (1 << kb["mcu"]) == n  # 16 bits cover one 4k texture's MCUs
+    # the generator's encoder agrees with the closed form
+    e = synth.encode_coefs(np.zeros((4, 6, 64), np.int16), 2, 2, 420)
+    assert e.nmcu == 4 and e.width == 32
+
+
+def _taps_np(u, v, w, h, filt):
+    """Texel taps with fp32 index arithmetic, written with numpy."""
+    w32 = np.float32(w)
+    h32 = np.float32(h)
+    uw = (u.astype(np.float32) * w32).astype(np.float32)
+    vh = (v.astype(np.float32) * h32).astype(np.float32)
+    if filt == 0:
+        x = np.mod(np.floor(uw).astype(np.int64), w)
+        y = np.mod(np.floor(vh).astype(np.int64), h)
+        return [(x, y)], None, None
+    xs = (uw - np.float32(0.5)).astype(np.float32)
+    ys = (vh - np.float32(0.5)).astype(np.float32)
+    x0 = np.floor(xs)
+    y0 = np.floor(ys)
+    fx = (xs - x0).astype(np.float64)
+    fy = (ys - y0).astype(np.float64)
+    x0 = x0.astype(np.int64)
+    y0 = y0.astype(np.int64)
+    xa, xb = np.mod(x0, w), np.mod(x0 + 1, w)
+    ya, yb = np.mod(y0, h), np.mod(y0 + 1, h)
+    return [(xa, ya), (xb, ya), (xa, yb), (xb, yb)], fx, fy
+
+
+def _brute_marks(ts, gb, filt):
+    keys = set()
+    valid = gb.tex_id != 0xFFFF
+    tex = gb.tex_id[valid]
+    mip = gb.mip[valid]
+    u = gb.uv[..., 0][valid]
+    v = gb.uv[..., 1][valid]
+    gid = 0
+    for t, l, e in ts.uploads():
+        sel = (tex == t) & (mip == l)
+        if sel.any():
+            mw = 16 if e.sampling == 420 else 8
+            for x, y in _taps_np(u[sel], v[sel], e.width, e.height, filt)[0]:
+                keys |= set((gid + x // mw + (y // mw) * e.mcus_x).tolist())
+        gid += e.nmcu
+    return keys
+
+
+def _small_scene(seed=3, W=320, H=180, nq=30):
+    sizes = [(64, 64), (128, 128), (256, 256), (96, 48)]
+    ts = synth.make_texture_set(seed, sizes, [60, 75, 90, 50], [420, 420, 444, 420])
+    gb = synth.gbuffer_scene(seed, W, H, ts.sizes, ts.nlevels, synth.Pose(quad_seed=seed), nquads=nq)
+    return ts, gb
+
+
+@pytest.mark.parametrize("filt", [0, 1])
+def test_mark_equals_brute_force_config1(filt):
+    ts, gb = synth.config1()
+    o = oracle.texset_from(ts)
+    flags = o.mark(gb, filt)
+    assert set(np.nonzero(flags)[0].tolist()) == _brute_marks(ts, gb, filt)
+
+
+@pytest.mark.parametrize("filt", [0, 1])
+def test_mark_equals_brute_force_scene(filt):
+    ts, gb = _small_scene()
+    o = oracle.texset_from(ts)
+    flags = o.mark(gb, filt)
+    ref = _brute_marks(ts, gb, filt)
+    assert len(ref) > 50
+    assert set(np.nonzero(flags)[0].tolist()) == ref
+    work = o.compact(flags)
+    assert work.size == int(flags.sum())
+    assert (np.diff(work.astype(np.int64)) > 0).all()
+
+
+def _full_textures(ts):
+    return {(t, l): oracle.Decoded(e.jfif).rgba for t, l, e in ts.uploads()}
+
+
+@pytest.mark.parametrize("filt", [0, 1])
+def test_colorize_equals_full_decode(filt):
+    ts, gb = _small_scene(seed=5)
+    o = oracle.texset_from(ts)
+    out = o.colorize(gb.uv, gb.tex_id, gb.mip, filt)
+    full = _full_textures(ts)
+    ref = np.zeros(gb.tex_id.shape + (3,), np.float64)
+    valid = gb.tex_id != 0xFFFF
+    for (t, l), img in full.items():
+        sel = valid & (gb.tex_id == t) & (gb.mip == l)
+        if not sel.any():
+            continue
+        h, w = img.shape[:2]
+        taps, fx, fy = _taps_np(gb.uv[..., 0][sel], gb.uv[..., 1][sel], w, h, filt)
+        c = [img[y, x, :3].astype(np.float64) for x, y in taps]
+        if filt == 0:
+            ref[sel] = c[0]
+        else:
+            fx = fx[:, None]
+            fy = fy[:, None]
+            ref[sel] = (1 - fy) * ((1 - fx) * c[0] + fx * c[1]) + fy * ((1 - fx) * c[2] + fx * c[3])
+    ref = np.clip(np.floor(ref + 0.5), 0, 255)
+    diff = np.abs(out[..., :3].astype(np.int32) - ref.astype(np.int32))
+    if filt == 0:
+        assert diff.max() == 0
+    else:
+        assert diff.max() <= 1
+    assert (out[~valid] == [0, 0, 0, 255]).all()
+    assert (out[..., 3] == 255).all()
+    # exactly the marked MCUs were decoded
+    flags = o.mark(gb, filt)
+    assert o.cached() == int(flags.sum())
