@@ -1,0 +1,250 @@
+/*
+ * jt.h — C ABI of the GB300 variable-rate (JPEG) texture path.
+ *
+ * Textures stay in GPU memory as baseline-JPEG entropy streams plus a per-MCU index.
+ * Each frame runs against a deferred G-buffer (uv, texture id, mip level per pixel):
+ *   jt_mark      — flag the MCUs (JPEG blocks) the pixels touch           (paper Sec. 4.2)
+ *   jt_decode    — compact the flags into a work list, then Huffman-decode, dequantise,
+ *                  IDCT, upsample chroma and convert to RGB into the block cache
+ *                                                                        (Sec. 4.3, Sec. 5.2)
+ *   jt_colorize  — look up each pixel's texel(s) in the block cache      (Sec. 4.4)
+ * Textures, levels and the cache key follow Sec. 4.6; the index follows Sec. 5.1/5.3.
+ *
+ * Conventions
+ *  - All functions return a jt_status. On failure jt_last_error() describes the cause.
+ *  - "device" pointers are CUDA device (or managed) memory on the context's device.
+ *    "host" pointers are ordinary host memory. Nothing is retained past the call unless
+ *    stated; work enqueued on a stream reads caller buffers until that stream reaches it.
+ *  - A jt_stream is a cudaStream_t (NULL = the legacy default stream).
+ *  - A context is not thread-safe; calls on one context must be serialised by the caller
+ *    and its frames must not overlap on different streams.
+ *  - Device-side problems (a corrupt stream, a capacity overflow, a pixel naming a level
+ *    that was never uploaded) never trap: kernels finish with bounded loops and set bits
+ *    in a device error word. jt_get_stats() synchronises, reads and clears that word and
+ *    returns the matching status.
+ */
+#ifndef JT_H
+#define JT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  JT_OK = 0,
+  JT_ERR_INVALID_ARG = 1,    /* bad argument; nothing was enqueued */
+  JT_ERR_CUDA = 2,           /* a CUDA runtime call failed (no device, launch failure) */
+  JT_ERR_OOM = 3,            /* device allocation failed */
+  JT_ERR_CORRUPT_STREAM = 4, /* an MCU's bits are not a valid baseline coding */
+  JT_ERR_CAPACITY = 5,       /* needed blocks exceed the block cache */
+  JT_ERR_UNSUPPORTED = 6,    /* e.g. a pixel names a (texture, level) never uploaded */
+  JT_ERR_STATE = 7           /* call out of order (e.g. jt_decode without jt_mark) */
+} jt_status;
+
+/* Bits of jt_stats.error_bits (the device error word). */
+#define JT_DEVERR_CORRUPT 0x1u     /* invalid code, category or run, or bits past the stream */
+#define JT_DEVERR_CAPACITY 0x2u    /* needed cache units > capacity; extra tiles not written */
+#define JT_DEVERR_MISSING 0x4u     /* a pixel names a (texture, level) that does not exist */
+#define JT_DEVERR_TIMEOUT 0x8u     /* a bounded wait in the compaction scan gave up */
+
+#define JT_FILTER_NEAREST 0
+#define JT_FILTER_BILINEAR 1
+#define JT_MAX_VIEWS 16
+#define JT_MAX_LEVELS 16
+#define JT_EMPTY_TEXTURE 0xFFFFu
+
+typedef struct jt_ctx jt_ctx;
+typedef struct jt_graph jt_graph;
+typedef void* jt_stream;
+
+/* One entry of the random-access index (Sec. 5.1, Sec. 5.3): the MCU's first bit in the
+ * unstuffed entropy stream and the DC value each component (Y, Cb, Cr) had just before
+ * this MCU. Packed, 10 bytes. */
+#pragma pack(push, 2)
+typedef struct {
+  uint32_t bit_offset;
+  int16_t dc_pred[3];
+} jt_block_index;
+#pragma pack(pop)
+
+/* A Huffman table specification as in a JPEG DHT segment (T.81 B.2.4.2): bits[i] = number
+ * of codes of length i+1, vals = symbols in code order (sum(bits) <= 256). */
+typedef struct {
+  uint8_t bits[16];
+  uint8_t vals[256];
+} jt_huff_spec;
+
+/* Deferred G-buffer (Sec. 4 "Geometry Pass"), structure of arrays, caller-owned device
+ * memory, row-major [height][width]:
+ *   uv     float32 pairs (u, v); repeat wrap; 16-byte aligned
+ *   tex_id uint16, JT_EMPTY_TEXTURE for pixels without texture;  8-byte aligned
+ *   mip    uint8 mip level;                                       4-byte aligned */
+typedef struct {
+  const float* uv;
+  const uint16_t* tex_id;
+  const uint8_t* mip;
+  int32_t width;
+  int32_t height;
+} jt_gbuffer;
+
+/* One view of a batched frame: its G-buffer and its RGBA8 output (device, 16-byte
+ * aligned, [height][width][4]). */
+typedef struct {
+  jt_gbuffer g;
+  uint8_t* out_rgba;
+} jt_view;
+
+typedef struct {
+  uint64_t needed_blocks;   /* MCUs in the last compaction's work list */
+  uint64_t cache_units;     /* 256-byte block-cache units those MCUs occupy */
+  uint64_t capacity_units;  /* block-cache capacity in 256-byte units */
+  uint64_t total_blocks;    /* MCUs over all uploaded levels (the key space) */
+  uint32_t levels;          /* uploaded (texture, level) pairs */
+  uint32_t error_bits;      /* JT_DEVERR_* bits seen since the last jt_get_stats */
+} jt_stats;
+
+/* Launch configuration picked by the autotuner (or set by hand). */
+typedef struct {
+  int32_t decode_warps;      /* warps per decode CTA (2..16) */
+  int32_t decode_ctas_per_sm;/* resident decode CTAs per SM of the persistent grid (>= 1) */
+  int32_t pixel_threads;     /* threads per CTA of mark and colourise (64..1024, mult. of 32) */
+  int32_t pixel_ctas_per_sm; /* CTAs per SM of the grid-stride mark and colourise grids */
+} jt_tuning;
+
+/* ---- context ------------------------------------------------------------------------- */
+
+/* Creates a context on CUDA device `device` with a block cache of `max_cache_blocks`
+ * 16x16 RGBA8 blocks (1 KiB each; a 4:4:4 MCU of 8x8 texels takes a quarter block).
+ * Owns all device memory it allocates; the caller owns *out and frees it with jt_destroy. */
+jt_status jt_create(jt_ctx** out, int device, uint64_t max_cache_blocks);
+jt_status jt_destroy(jt_ctx* ctx);
+const char* jt_last_error(const jt_ctx* ctx);
+const char* jt_status_string(jt_status s);
+
+/* ---- textures (Sec. 4.6, Sec. 5.1) --------------------------------------------------- */
+
+/* Uploads one mip level of one texture: the unstuffed entropy-coded segment of a baseline
+ * sequential JPEG scan (bytes 0xFF 0x00 replaced by 0xFF, no markers, no restart
+ * intervals; `nbits` coded bits in `nbytes` bytes), its per-MCU index (`nblocks` =
+ * ceil(width/mw) * ceil(height/mw) entries, MCU order row-major, mw = 16 at 4:2:0, 8 at
+ * 4:4:4), two quantisation tables (luma, chroma; 64 entries each in natural row-major
+ * order, `qt` points to 128 uint16) and four Huffman specs (DC luma, AC luma, DC chroma,
+ * AC chroma). Components: Y uses table 0, Cb and Cr table 1.
+ * `sampling` is 420 (MCU = 4 Y + Cb + Cr data units, 16x16 texels) or 444 (Y, Cb, Cr,
+ * 8x8 texels). All pointers are host memory and are copied; they may be freed on return.
+ * MCUs of the level get consecutive global ids (gids) in upload order: the first level
+ * uploaded starts at gid 0 and each level starts where the previous one ended.
+ * 0 <= tex_id < 0xFFFF, 0 <= level < JT_MAX_LEVELS, 1 <= width, height <= 65535; a
+ * (tex_id, level) pair may be uploaded once. Not allowed between jt_mark and jt_decode. */
+jt_status jt_upload_texture(jt_ctx* ctx, int tex_id, int level, int width, int height, int sampling,
+                            const uint8_t* bitstream, uint64_t nbytes, uint64_t nbits,
+                            const jt_block_index* index, uint64_t nblocks, const uint16_t* qt,
+                            const jt_huff_spec huff[4]);
+
+/* ---- per-frame path -------------------------------------------------------------------- */
+
+/* Mark (Sec. 4.2): for every pixel with a texture, computes the texel(s) its uv falls on at
+ * its mip level — nearest: x = floor(u*w) mod w; bilinear: the four texels around
+ * u*w - 1/2 — and flags the MCUs that hold them. Flags accumulate over calls until the
+ * next jt_decode, so several views marked in turn are decoded once (union). */
+jt_status jt_mark(jt_ctx* ctx, const jt_gbuffer* g, int filter, jt_stream stream);
+
+/* Compact + decode (Sec. 4.3): turns the flags into a work list of gids in ascending order
+ * (exclusive prefix sum, which also assigns each needed MCU its block-cache slot) and
+ * clears the flags; then decodes every listed MCU into its slot: Huffman decode from the
+ * MCU's index entry, dequantise, 8x8 integer IDCT, 4:2:0 chroma replication, YCbCr->RGB,
+ * RGBA8 tile (alpha 255). Needs no host synchronisation: the count stays on the device. */
+jt_status jt_decode(jt_ctx* ctx, jt_stream stream);
+
+/* Resolve (Sec. 4.4): writes RGBA8 per pixel from the block cache (nearest, or bilinear
+ * with fp32 weights and round-half-up). Pixels without texture get (0,0,0,255). `filter`
+ * must match the jt_mark call(s) of this frame. out_rgba: device, [height][width][4],
+ * 16-byte aligned. */
+jt_status jt_colorize(jt_ctx* ctx, const jt_gbuffer* g, int filter, uint8_t* out_rgba, jt_stream stream);
+
+/* Synchronises the last stream used, reads the counts and the device error word (and
+ * clears it). Returns JT_ERR_CORRUPT_STREAM / JT_ERR_CAPACITY / JT_ERR_UNSUPPORTED when the
+ * corresponding error bit was set, else JT_OK; *out is filled either way. */
+jt_status jt_get_stats(jt_ctx* ctx, jt_stats* out);
+
+/* ---- batched frames, CUDA graphs, autotuning ------------------------------------------- */
+
+/* One frame over `nviews` views (<= JT_MAX_VIEWS): one mark launch over all views into the
+ * shared flags (an MCU needed by several views is decoded once), one compaction, one
+ * persistent decode over the merged work list, one colourise launch over all views. */
+jt_status jt_frame(jt_ctx* ctx, const jt_view* views, int nviews, int filter, jt_stream stream);
+
+/* The same frame captured once into a CUDA graph; replay with jt_graph_launch. The views'
+ * pointers are baked into the graph: their contents may change between launches, the
+ * buffers may not move. The graph belongs to ctx and must be destroyed before it. */
+jt_status jt_frame_graph(jt_ctx* ctx, const jt_view* views, int nviews, int filter, jt_stream stream,
+                         jt_graph** out);
+jt_status jt_graph_launch(jt_graph* g, jt_stream stream);
+jt_status jt_graph_destroy(jt_graph* g);
+
+/* Reference form for comparison: per view and per texture id present in the frame, a
+ * mark, compaction, decode and colourise restricted to that texture (4 launches each,
+ * plus one colourise per view for empty pixels). Same output as jt_frame. */
+jt_status jt_frame_plain(jt_ctx* ctx, const jt_view* views, int nviews, int filter, jt_stream stream);
+
+jt_status jt_get_tuning(const jt_ctx* ctx, jt_tuning* out);
+jt_status jt_set_tuning(jt_ctx* ctx, const jt_tuning* t);
+
+/* Times `reps` graph replays of the frame for each candidate launch configuration
+ * (decode warps per CTA x decode CTAs per SM x pixel-kernel shape), keeps the fastest in
+ * the context and returns it with its median frame time in milliseconds. */
+jt_status jt_autotune(jt_ctx* ctx, const jt_view* views, int nviews, int filter, jt_stream stream, int reps,
+                      jt_tuning* best, float* best_ms);
+
+/* ---- inspection (tests, tools) ---------------------------------------------------------- */
+
+/* Pass timing. While enabled, every frame enqueued by jt_frame / jt_frame_graph (graphs
+ * captured while enabled) records CUDA events on its stream at the pass boundaries; the
+ * events belong to the context. jt_profile_read waits for the last recorded frame and
+ * returns its durations in milliseconds: ms[0] mark, ms[1] compaction, ms[2] decode,
+ * ms[3] colourise. */
+jt_status jt_profile(jt_ctx* ctx, int enable);
+jt_status jt_profile_read(jt_ctx* ctx, float ms[4]);
+
+/* Copies the last work list (gids, ascending) to dst (host or device), at most cap entries;
+ * *count receives the full length. Synchronises. */
+jt_status jt_read_work_list(jt_ctx* ctx, uint32_t* dst, uint64_t cap, uint64_t* count);
+/* Copies the cache-unit offset of each gid in [gid_begin, gid_begin + n) to dst (valid for
+ * gids in the last work list). Synchronises. */
+jt_status jt_read_slots(jt_ctx* ctx, uint64_t gid_begin, uint64_t n, uint32_t* dst);
+/* Copies 256-byte cache units [unit_begin, unit_begin + n) to dst. A 4:2:0 MCU is 4 units
+ * (16 rows of 16 RGBA8 texels), a 4:4:4 MCU one unit (8 rows of 8). Synchronises. */
+jt_status jt_read_cache(jt_ctx* ctx, uint64_t unit_begin, uint64_t n, uint8_t* dst);
+
+/* ---- differentiable colourise (float chain; not in the paper) ---------------------------- */
+
+/* Registers `count` coefficient textures with ids first_tex_id.. first_tex_id+count-1, each
+ * width x height texels at 4:2:0, level 0, whose content is given per call as dequantised
+ * DCT coefficients: float32 [count][height/16][width/16][6][64] (data units Y00 Y01 Y10
+ * Y11 Cb Cr, coefficient k = v*8+u in natural order). width and height must be multiples
+ * of 16. They share the gid space with uploaded textures but are only valid for the two
+ * calls below. */
+jt_status jt_register_coeff_textures(jt_ctx* ctx, int first_tex_id, int count, int width, int height);
+
+/* Forward of the float chain F = bilinear(RGB(upsample(IDCT_f(c) + 128))) with the
+ * orthonormal 8x8 IDCT, JFIF colour matrix, chroma replication and bilinear weights of
+ * jt_colorize, without rounding or clamping. coeffs: device float32 as registered;
+ * out_rgb: device float32 [height][width][3]; empty pixels get 0. */
+jt_status jt_colorize_float(jt_ctx* ctx, const jt_gbuffer* g, const float* coeffs, float* out_rgb,
+                            jt_stream stream);
+
+/* Adjoint of jt_colorize_float: grad_coeffs = J^T grad_frame, where grad_frame is
+ * float32 [height][width][3] (device). grad_coeffs (device, the coefficients' shape) is
+ * overwritten: zero except for the MCUs the frame touches. Recomputes the needed set
+ * from the G-buffer; stores no decoded blocks. */
+jt_status jt_colorize_backward(jt_ctx* ctx, const jt_gbuffer* g, const float* grad_frame, float* grad_coeffs,
+                               jt_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* JT_H */

@@ -1,0 +1,918 @@
+// Host implementation of the C ABI declared in include/jt.h: context and memory
+// management, texture upload (decode-table construction), the per-frame launch sequence,
+// batched frames, CUDA-graph capture, the per-texture reference pipeline and autotuning.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "jt_internal.cuh"
+
+using namespace jt;
+
+namespace {
+
+enum class Phase { Idle, Marked, Decoded };
+
+struct Level {
+  int tex, level;
+  void* stream_mem = nullptr;
+  void* index_mem = nullptr;
+};
+
+}  // namespace
+
+struct jt_ctx {
+  int device = 0;
+  int sm_count = 0;
+  uint64_t cap_units = 0;
+  std::string last_error;
+  cudaStream_t last_stream = nullptr;
+  Phase phase = Phase::Idle;
+  jt_tuning tuning{};
+  int decode_occ[17] = {};  // resident decode CTAs per SM by warps per CTA
+
+  // textures
+  std::vector<DevDesc> descs;
+  std::vector<Level> levels;
+  DevDesc* d_descs = nullptr;
+  size_t d_descs_cap = 0;
+  std::vector<int32_t> map;  // [map_ntex * 16]
+  uint32_t map_ntex = 0;
+  int32_t* d_map = nullptr;
+  std::vector<HuffSet> hsets;
+  HuffSet* d_huff = nullptr;
+  std::vector<std::vector<uint16_t>> qsets;  // zig-zag order, 128 entries
+  uint16_t* d_quant = nullptr;
+  uint64_t ngid = 0;
+
+  // per-frame buffers
+  uint8_t* flags = nullptr;
+  uint32_t* slot = nullptr;
+  uint32_t* work = nullptr;
+  uint64_t* tile_status = nullptr;
+  uint64_t gid_cap = 0;
+  uint8_t* cache = nullptr;
+  FrameState* state = nullptr;
+
+  // coefficient textures (float chain)
+  int coef_first = -1, coef_count = 0, coef_w = 0, coef_h = 0;
+  uint32_t coef_gid_base = 0;
+  float4* float_tiles = nullptr;
+  uint32_t float_tile_cap = 0;
+  cudaStream_t capture_stream = nullptr;
+
+  // pass timing (jt_profile)
+  bool profiling = false;
+  cudaEvent_t prof[5] = {};
+};
+
+struct jt_graph {
+  jt_ctx* ctx;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+constexpr uint64_t kMaxGids = 1ull << 26;   // count field of the scan status word
+constexpr uint64_t kMaxUnits = 1ull << 28;  // units field of the scan status word
+
+jt_status fail(jt_ctx* c, jt_status s, const char* fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->last_error = buf;
+  }
+  return s;
+}
+
+#define JT_CUDA(c, call)                                                                          \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess) return fail((c), JT_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+template <typename T>
+jt_status dev_alloc(jt_ctx* c, T** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, e == cudaErrorMemoryAllocation ? JT_ERR_OOM : JT_ERR_CUDA, "cudaMalloc(%zu): %s", bytes,
+                cudaGetErrorString(e));
+  }
+  return JT_OK;
+}
+
+template <typename T>
+void dev_free(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+// Natural index of the k-th zig-zag coefficient (inverse of the kernel's closed form).
+void zigzag_natural(int nat[64]) {
+  for (int r = 0; r < 8; ++r)
+    for (int c = 0; c < 8; ++c) {
+      const int s = r + c;
+      const int before = s <= 7 ? s * (s + 1) / 2 : 64 - (15 - s) * (16 - s) / 2;
+      const int along = (s & 1) ? r - (s > 7 ? s - 7 : 0) : (s < 7 ? s : 7) - r;
+      nat[before + along] = r * 8 + c;
+    }
+}
+
+// Canonical decode tables of one Huffman spec (T.81 Annex C code assignment).
+bool build_table(const jt_huff_spec& spec, HuffTable& t, std::string& why) {
+  std::memset(&t, 0, sizeof t);
+  int n = 0;
+  uint64_t kraft = 0;
+  for (int l = 1; l <= 16; ++l) {
+    n += spec.bits[l - 1];
+    kraft += (uint64_t)spec.bits[l - 1] << (16 - l);
+  }
+  if (n == 0 || n > 256) {
+    why = "Huffman spec with no symbols or more than 256";
+    return false;
+  }
+  if (kraft > (1u << 16)) {
+    why = "Huffman code lengths violate the Kraft inequality";
+    return false;
+  }
+  std::memcpy(t.vals, spec.vals, n);
+  int code = 0, k = 0;
+  for (int l = 1; l <= 16; ++l) {
+    const int nl = spec.bits[l - 1];
+    if (nl == 0) {
+      t.maxcode[l] = -1;
+      t.valoff[l] = 0;
+    } else {
+      t.valoff[l] = k - code;
+      for (int i = 0; i < nl; ++i, ++k, ++code) {
+        if (l <= kLutBits) {
+          const int first = code << (kLutBits - l), cnt = 1 << (kLutBits - l);
+          for (int j = 0; j < cnt; ++j) t.lut[first + j] = (uint16_t)((l << 8) | spec.vals[k]);
+        }
+      }
+      t.maxcode[l] = code - 1;
+    }
+    code <<= 1;
+  }
+  t.maxcode[0] = -1;
+  return true;
+}
+
+jt_status grow_frame_buffers(jt_ctx* c, uint64_t need) {
+  if (need <= c->gid_cap) return JT_OK;
+  uint64_t cap = std::max<uint64_t>(need, c->gid_cap + c->gid_cap / 2);
+  cap = std::min<uint64_t>(std::max<uint64_t>(cap, 4096), kMaxGids);
+  cap = (cap + 15) & ~15ull;
+  dev_free(c->flags);
+  dev_free(c->slot);
+  dev_free(c->work);
+  dev_free(c->tile_status);
+  c->gid_cap = 0;
+  jt_status s;
+  if ((s = dev_alloc(c, &c->flags, cap + 16)) != JT_OK) return s;
+  if ((s = dev_alloc(c, &c->slot, cap * 4)) != JT_OK) return s;
+  if ((s = dev_alloc(c, &c->work, cap * 4)) != JT_OK) return s;
+  const uint64_t tiles = cap / kScanTile + 2;
+  if ((s = dev_alloc(c, &c->tile_status, tiles * 8)) != JT_OK) return s;
+  JT_CUDA(c, cudaMemset(c->flags, 0, cap + 16));
+  JT_CUDA(c, cudaMemset(c->slot, 0, cap * 4));
+  JT_CUDA(c, cudaMemset(c->work, 0, cap * 4));
+  JT_CUDA(c, cudaMemset(c->tile_status, 0, tiles * 8));
+  c->gid_cap = cap;
+  return JT_OK;
+}
+
+jt_status sync_descs(jt_ctx* c) {
+  if (c->descs.size() > c->d_descs_cap) {
+    dev_free(c->d_descs);
+    size_t cap = std::max<size_t>(64, c->descs.size() * 2);
+    jt_status s = dev_alloc(c, &c->d_descs, cap * sizeof(DevDesc));
+    if (s != JT_OK) return s;
+    c->d_descs_cap = cap;
+  }
+  JT_CUDA(c, cudaMemcpy(c->d_descs, c->descs.data(), c->descs.size() * sizeof(DevDesc), cudaMemcpyHostToDevice));
+  dev_free(c->d_map);
+  jt_status s = dev_alloc(c, &c->d_map, c->map.size() * 4);
+  if (s != JT_OK) return s;
+  JT_CUDA(c, cudaMemcpy(c->d_map, c->map.data(), c->map.size() * 4, cudaMemcpyHostToDevice));
+  return JT_OK;
+}
+
+jt_status sync_tables(jt_ctx* c) {
+  dev_free(c->d_huff);
+  jt_status s = dev_alloc(c, &c->d_huff, std::max<size_t>(1, c->hsets.size()) * sizeof(HuffSet));
+  if (s != JT_OK) return s;
+  if (!c->hsets.empty())
+    JT_CUDA(c, cudaMemcpy(c->d_huff, c->hsets.data(), c->hsets.size() * sizeof(HuffSet), cudaMemcpyHostToDevice));
+  dev_free(c->d_quant);
+  if ((s = dev_alloc(c, &c->d_quant, std::max<size_t>(1, c->qsets.size()) * 256)) != JT_OK) return s;
+  for (size_t i = 0; i < c->qsets.size(); ++i)
+    JT_CUDA(c, cudaMemcpy(c->d_quant + i * 128, c->qsets[i].data(), 256, cudaMemcpyHostToDevice));
+  return JT_OK;
+}
+
+TexLookup lookup(const jt_ctx* c) { return TexLookup{c->d_descs, c->d_map, c->map_ntex}; }
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+jt_status check_gbuffer(jt_ctx* c, const jt_gbuffer* g) {
+  if (!g || !g->uv || !g->tex_id || !g->mip) return fail(c, JT_ERR_INVALID_ARG, "null G-buffer pointer");
+  if (g->width <= 0 || g->height <= 0) return fail(c, JT_ERR_INVALID_ARG, "empty G-buffer");
+  if ((uint64_t)g->width * g->height >= (1ull << 31)) return fail(c, JT_ERR_INVALID_ARG, "G-buffer too large");
+  if (!aligned(g->uv, 16) || !aligned(g->tex_id, 8) || !aligned(g->mip, 4))
+    return fail(c, JT_ERR_INVALID_ARG, "G-buffer arrays must be 16/8/4-byte aligned (uv/tex_id/mip)");
+  return JT_OK;
+}
+
+jt_status make_views(jt_ctx* c, const jt_view* views, int n, bool need_out, ViewSet& vs) {
+  if (!views || n <= 0 || n > JT_MAX_VIEWS) return fail(c, JT_ERR_INVALID_ARG, "need 1..%d views", JT_MAX_VIEWS);
+  std::memset(&vs, 0, sizeof vs);
+  uint64_t quads = 0;
+  for (int i = 0; i < n; ++i) {
+    jt_status s = check_gbuffer(c, &views[i].g);
+    if (s != JT_OK) return s;
+    if (need_out && (!views[i].out_rgba || !aligned(views[i].out_rgba, 16)))
+      return fail(c, JT_ERR_INVALID_ARG, "view %d: output must be a 16-byte aligned device pointer", i);
+    View& v = vs.v[i];
+    v.uv = reinterpret_cast<const float4*>(views[i].g.uv);
+    v.tex = views[i].g.tex_id;
+    v.mip = views[i].g.mip;
+    v.out = reinterpret_cast<uint4*>(views[i].out_rgba);
+    v.npx = (uint32_t)((uint64_t)views[i].g.width * views[i].g.height);
+    v.quad_begin = (uint32_t)quads;
+    quads += (v.npx + 3) / 4;
+  }
+  if (quads >= (1ull << 31)) return fail(c, JT_ERR_INVALID_ARG, "views too large");
+  vs.n = n;
+  vs.total_quads = (uint32_t)quads;
+  return JT_OK;
+}
+
+int pixel_grid(const jt_ctx* c, uint32_t quads) {
+  const int threads = c->tuning.pixel_threads;
+  const uint64_t want = (quads + threads - 1) / threads;
+  const uint64_t cap = (uint64_t)c->sm_count * std::max(1, c->tuning.pixel_ctas_per_sm);
+  return (int)std::max<uint64_t>(1, std::min(want, cap));
+}
+
+jt_status check_launch(jt_ctx* c, const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(c, JT_ERR_CUDA, "%s launch: %s", what, cudaGetErrorString(e));
+  return JT_OK;
+}
+
+jt_status enqueue_mark(jt_ctx* c, const ViewSet& vs, int filter, int only_tex, int coef_mode, cudaStream_t s) {
+  if (c->descs.empty()) return fail(c, JT_ERR_STATE, "no textures uploaded");
+  MarkArgs a{};
+  a.views = vs;
+  a.tl = lookup(c);
+  a.flags = c->flags;
+  a.state = c->state;
+  a.filter = filter;
+  a.only_tex = only_tex;
+  a.coef_mode = coef_mode;
+  launch_mark(a, c->tuning.pixel_threads, pixel_grid(c, vs.total_quads), s);
+  return check_launch(c, "mark");
+}
+
+jt_status enqueue_scan(jt_ctx* c, uint64_t gid_lo, uint64_t gid_hi, cudaStream_t s) {
+  gid_lo &= ~15ull;  // 16-byte aligned vector access to the flags
+  ScanArgs a{};
+  a.flags = c->flags + gid_lo;
+  a.gid_lo = (uint32_t)gid_lo;
+  a.n = (uint32_t)(gid_hi - gid_lo);
+  a.slot = c->slot;
+  a.work = c->work;
+  a.work_cap = (uint32_t)c->gid_cap;
+  a.tile_status = c->tile_status;
+  a.state = c->state;
+  a.cap_units = (uint32_t)c->cap_units;
+  const uint32_t ntiles = (a.n + kScanTile - 1) / kScanTile;
+  const int grid = (int)std::max<uint32_t>(1, std::min<uint32_t>(ntiles, (uint32_t)c->sm_count * 4));
+  launch_scan(a, grid, s);
+  return check_launch(c, "scan");
+}
+
+jt_status enqueue_decode(jt_ctx* c, cudaStream_t s) {
+  DecodeArgs a{};
+  a.descs = c->d_descs;
+  a.ndesc = (uint32_t)c->descs.size();
+  a.huff = c->d_huff;
+  a.quant = c->d_quant;
+  a.work = c->work;
+  a.work_cap = (uint32_t)c->gid_cap;
+  a.slot = c->slot;
+  a.cache = c->cache;
+  a.cap_units = (uint32_t)c->cap_units;
+  a.state = c->state;
+  const int w = c->tuning.decode_warps;
+  const int per_sm = std::max(1, std::min(c->tuning.decode_ctas_per_sm, c->decode_occ[w]));
+  launch_decode(a, w, c->sm_count * per_sm, s);
+  return check_launch(c, "decode");
+}
+
+jt_status enqueue_colorize(jt_ctx* c, const ViewSet& vs, int filter, int only_tex, cudaStream_t s) {
+  ColorizeArgs a{};
+  a.views = vs;
+  a.tl = lookup(c);
+  a.slot = c->slot;
+  a.cache = c->cache;
+  a.cap_units = (uint32_t)c->cap_units;
+  a.state = c->state;
+  a.filter = filter;
+  a.only_tex = only_tex;
+  launch_colorize(a, c->tuning.pixel_threads, pixel_grid(c, vs.total_quads), s);
+  return check_launch(c, "colorize");
+}
+
+jt_status enqueue_frame(jt_ctx* c, const ViewSet& vs, int filter, cudaStream_t s) {
+  jt_status st;
+  auto mark_time = [&](int i) {
+    if (c->profiling) cudaEventRecord(c->prof[i], s);
+  };
+  mark_time(0);
+  if ((st = enqueue_mark(c, vs, filter, -1, 0, s)) != JT_OK) return st;
+  mark_time(1);
+  if ((st = enqueue_scan(c, 0, c->ngid, s)) != JT_OK) return st;
+  mark_time(2);
+  if ((st = enqueue_decode(c, s)) != JT_OK) return st;
+  mark_time(3);
+  if ((st = enqueue_colorize(c, vs, filter, -1, s)) != JT_OK) return st;
+  mark_time(4);
+  return check_launch(c, "event record");
+}
+
+bool valid_filter(int f) { return f == JT_FILTER_NEAREST || f == JT_FILTER_BILINEAR; }
+
+bool valid_tuning(const jt_ctx* c, const jt_tuning& t) {
+  const bool w_ok = t.decode_warps == 2 || t.decode_warps == 4 || t.decode_warps == 6 || t.decode_warps == 8;
+  return w_ok && c->decode_occ[t.decode_warps] > 0 && t.decode_ctas_per_sm >= 1 && t.pixel_threads >= 64 &&
+         t.pixel_threads <= 1024 && t.pixel_threads % 32 == 0 && t.pixel_ctas_per_sm >= 1 &&
+         t.pixel_ctas_per_sm <= 32;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* jt_status_string(jt_status s) {
+  switch (s) {
+    case JT_OK: return "ok";
+    case JT_ERR_INVALID_ARG: return "invalid argument";
+    case JT_ERR_CUDA: return "CUDA error";
+    case JT_ERR_OOM: return "out of device memory";
+    case JT_ERR_CORRUPT_STREAM: return "corrupt entropy-coded stream";
+    case JT_ERR_CAPACITY: return "block cache capacity exceeded";
+    case JT_ERR_UNSUPPORTED: return "unsupported";
+    case JT_ERR_STATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+const char* jt_last_error(const jt_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "null context"; }
+
+jt_status jt_create(jt_ctx** out, int device, uint64_t max_cache_blocks) {
+  if (!out) return JT_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (max_cache_blocks == 0 || max_cache_blocks * 4 > kMaxUnits) return JT_ERR_INVALID_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return JT_ERR_CUDA;
+  }
+  DeviceGuard g(device);
+  if (!g.ok) return JT_ERR_CUDA;
+  jt_ctx* c = new jt_ctx();
+  c->device = device;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+    delete c;
+    return JT_ERR_CUDA;
+  }
+  c->sm_count = prop.multiProcessorCount;
+  // the kernel's IDCT constants must be round(8192 cos(k pi / 16))
+  int kc[8];
+  idct_constants(kc);
+  for (int k = 1; k < 8; ++k)
+    if (kc[k] != (int)std::lround(8192.0 * std::cos(k * M_PI / 16.0))) {
+      delete c;
+      return JT_ERR_UNSUPPORTED;
+    }
+  for (int w : {2, 4, 6, 8}) c->decode_occ[w] = decode_max_ctas_per_sm(w);
+  cudaGetLastError();
+  c->tuning.decode_warps = 4;
+  c->tuning.decode_ctas_per_sm = std::max(1, c->decode_occ[4]);
+  c->tuning.pixel_threads = 256;
+  c->tuning.pixel_ctas_per_sm = 8;
+  c->cap_units = max_cache_blocks * 4;
+  if (dev_alloc(c, &c->cache, c->cap_units * kUnitBytes) != JT_OK || dev_alloc(c, &c->state, sizeof(FrameState)) != JT_OK ||
+      cudaMemset(c->state, 0, sizeof(FrameState)) != cudaSuccess || cudaMemset(c->cache, 0, c->cap_units * kUnitBytes) != cudaSuccess ||
+      grow_frame_buffers(c, 4096) != JT_OK || sync_tables(c) != JT_OK) {
+    jt_destroy(c);
+    return JT_ERR_OOM;
+  }
+  c->map_ntex = 0;
+  if (sync_descs(c) != JT_OK) {
+    jt_destroy(c);
+    return JT_ERR_OOM;
+  }
+  *out = c;
+  return JT_OK;
+}
+
+jt_status jt_destroy(jt_ctx* c) {
+  if (!c) return JT_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  cudaDeviceSynchronize();
+  for (Level& l : c->levels) {
+    if (l.stream_mem) cudaFree(l.stream_mem);
+    if (l.index_mem) cudaFree(l.index_mem);
+  }
+  dev_free(c->d_descs);
+  dev_free(c->d_map);
+  dev_free(c->d_huff);
+  dev_free(c->d_quant);
+  dev_free(c->flags);
+  dev_free(c->slot);
+  dev_free(c->work);
+  dev_free(c->tile_status);
+  dev_free(c->cache);
+  dev_free(c->state);
+  dev_free(c->float_tiles);
+  if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+  for (cudaEvent_t& e : c->prof)
+    if (e) cudaEventDestroy(e);
+  delete c;
+  return JT_OK;
+}
+
+jt_status jt_profile(jt_ctx* c, int enable) {
+  if (!c) return JT_ERR_INVALID_ARG;
+  DeviceGuard dg(c->device);
+  if (enable && !c->prof[0])
+    for (cudaEvent_t& e : c->prof) JT_CUDA(c, cudaEventCreate(&e));
+  c->profiling = enable != 0;
+  return JT_OK;
+}
+
+jt_status jt_profile_read(jt_ctx* c, float ms[4]) {
+  if (!c || !ms) return JT_ERR_INVALID_ARG;
+  if (!c->prof[0]) return fail(c, JT_ERR_STATE, "profiling was never enabled");
+  DeviceGuard dg(c->device);
+  JT_CUDA(c, cudaEventSynchronize(c->prof[4]));
+  for (int i = 0; i < 4; ++i) JT_CUDA(c, cudaEventElapsedTime(&ms[i], c->prof[i], c->prof[i + 1]));
+  return JT_OK;
+}
+
+static jt_status add_level(jt_ctx* c, int tex_id, int level, DevDesc d, Level L) {
+  if ((uint32_t)tex_id >= c->map_ntex) {
+    uint32_t n = std::max<uint32_t>((uint32_t)tex_id + 1, c->map_ntex * 2);
+    n = std::min<uint32_t>(n, 0xFFFF);
+    c->map.resize((size_t)n * JT_MAX_LEVELS, -1);
+    c->map_ntex = n;
+  }
+  c->map[(size_t)tex_id * JT_MAX_LEVELS + level] = (int32_t)c->descs.size();
+  c->descs.push_back(d);
+  c->levels.push_back(L);
+  c->ngid += d.nmcu;
+  jt_status s = grow_frame_buffers(c, c->ngid);
+  if (s != JT_OK) return s;
+  return sync_descs(c);
+}
+
+jt_status jt_upload_texture(jt_ctx* c, int tex_id, int level, int width, int height, int sampling,
+                            const uint8_t* bitstream, uint64_t nbytes, uint64_t nbits, const jt_block_index* index,
+                            uint64_t nblocks, const uint16_t* qt, const jt_huff_spec huff[4]) {
+  if (!c) return JT_ERR_INVALID_ARG;
+  if (c->phase == Phase::Marked) return fail(c, JT_ERR_STATE, "upload between jt_mark and jt_decode");
+  if (tex_id < 0 || tex_id >= 0xFFFF || level < 0 || level >= JT_MAX_LEVELS)
+    return fail(c, JT_ERR_INVALID_ARG, "texture id %d / level %d out of range", tex_id, level);
+  if (width <= 0 || height <= 0 || width > 65535 || height > 65535)
+    return fail(c, JT_ERR_INVALID_ARG, "bad size %dx%d", width, height);
+  if (sampling != 420 && sampling != 444) return fail(c, JT_ERR_INVALID_ARG, "sampling must be 420 or 444");
+  if (!bitstream || !index || !qt || !huff) return fail(c, JT_ERR_INVALID_ARG, "null upload pointer");
+  if (nbits > nbytes * 8 || nbytes >= (1ull << 31)) return fail(c, JT_ERR_INVALID_ARG, "bad stream size");
+  if ((uint32_t)tex_id < c->map_ntex && c->map[(size_t)tex_id * JT_MAX_LEVELS + level] >= 0)
+    return fail(c, JT_ERR_INVALID_ARG, "texture %d level %d already uploaded", tex_id, level);
+  const int mw = sampling == 420 ? 16 : 8;
+  const uint64_t mx = (width + mw - 1) / mw, my = (height + mw - 1) / mw;
+  if (nblocks != mx * my) return fail(c, JT_ERR_INVALID_ARG, "index has %llu entries, expected %llu",
+                                      (unsigned long long)nblocks, (unsigned long long)(mx * my));
+  if (c->ngid + nblocks > kMaxGids) return fail(c, JT_ERR_UNSUPPORTED, "more than 2^26 MCUs in one context");
+  DeviceGuard g(c->device);
+  if (!g.ok) return fail(c, JT_ERR_CUDA, "cannot select device %d", c->device);
+
+  // decode tables (deduplicated by content)
+  HuffSet hs;
+  std::string why;
+  for (int t = 0; t < 4; ++t)
+    if (!build_table(huff[t], hs.t[t], why)) return fail(c, JT_ERR_INVALID_ARG, "Huffman table %d: %s", t, why.c_str());
+  int hset = -1;
+  for (size_t i = 0; i < c->hsets.size(); ++i)
+    if (std::memcmp(&c->hsets[i], &hs, sizeof hs) == 0) hset = (int)i;
+  int nat[64];
+  zigzag_natural(nat);
+  std::vector<uint16_t> qz(128);
+  for (int comp = 0; comp < 2; ++comp)
+    for (int k = 0; k < 64; ++k) qz[comp * 64 + k] = qt[comp * 64 + nat[k]];
+  int qset = -1;
+  for (size_t i = 0; i < c->qsets.size(); ++i)
+    if (c->qsets[i] == qz) qset = (int)i;
+  bool tables_changed = false;
+  if (hset < 0) {
+    if (c->hsets.size() >= 255) return fail(c, JT_ERR_UNSUPPORTED, "more than 255 distinct Huffman table sets");
+    c->hsets.push_back(hs);
+    hset = (int)c->hsets.size() - 1;
+    tables_changed = true;
+  }
+  if (qset < 0) {
+    if (c->qsets.size() >= 255) return fail(c, JT_ERR_UNSUPPORTED, "more than 255 distinct quantisation tables");
+    c->qsets.push_back(qz);
+    qset = (int)c->qsets.size() - 1;
+    tables_changed = true;
+  }
+  if (tables_changed) {
+    jt_status s = sync_tables(c);
+    if (s != JT_OK) return s;
+  }
+
+  // stream words (zero padded) and index
+  Level L{tex_id, level};
+  const uint64_t words = (nbytes + 3) / 4 + kStreamPadBytes / 4;
+  jt_status s;
+  if ((s = dev_alloc(c, reinterpret_cast<uint8_t**>(&L.stream_mem), words * 4)) != JT_OK) return s;
+  if ((s = dev_alloc(c, reinterpret_cast<uint8_t**>(&L.index_mem), nblocks * sizeof(jt_block_index) + 16)) != JT_OK) {
+    cudaFree(L.stream_mem);
+    return s;
+  }
+  if (cudaMemset(L.stream_mem, 0, words * 4) != cudaSuccess ||
+      cudaMemcpy(L.stream_mem, bitstream, nbytes, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(L.index_mem, index, nblocks * sizeof(jt_block_index), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(L.stream_mem);
+    cudaFree(L.index_mem);
+    return fail(c, JT_ERR_CUDA, "upload copy failed");
+  }
+  DevDesc d{};
+  d.stream = static_cast<const uint32_t*>(L.stream_mem);
+  d.index = static_cast<const uint16_t*>(L.index_mem);
+  d.gid_base = (uint32_t)c->ngid;
+  d.nmcu = (uint32_t)nblocks;
+  d.nwords = (uint32_t)words;
+  d.nbits = (uint32_t)nbits;
+  d.width = (uint16_t)width;
+  d.height = (uint16_t)height;
+  d.mcus_x = (uint16_t)mx;
+  d.mcus_y = (uint16_t)my;
+  d.sampling = sampling == 420 ? kSampling420 : kSampling444;
+  d.units = sampling == 420 ? 4 : 1;
+  d.hset = (uint8_t)hset;
+  d.qset = (uint8_t)qset;
+  return add_level(c, tex_id, level, d, L);
+}
+
+jt_status jt_mark(jt_ctx* c, const jt_gbuffer* g, int filter, jt_stream stream) {
+  if (!c) return JT_ERR_INVALID_ARG;
+  if (!valid_filter(filter)) return fail(c, JT_ERR_INVALID_ARG, "bad filter %d", filter);
+  jt_view v{};
+  if (g) v.g = *g;
+  ViewSet vs;
+  jt_status s = make_views(c, &v, 1, false, vs);
+  if (s != JT_OK) return s;
+  DeviceGuard dg(c->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if ((s = enqueue_mark(c, vs, filter, -1, 0, st)) != JT_OK) return s;
+  c->phase = Phase::Marked;
+  c->last_stream = st;
+  return JT_OK;
+}
+
+jt_status jt_decode(jt_ctx* c, jt_stream stream) {
+  if (!c) return JT_ERR_INVALID_ARG;
+  if (c->phase != Phase::Marked) return fail(c, JT_ERR_STATE, "jt_decode needs a preceding jt_mark");
+  DeviceGuard dg(c->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  jt_status s;
+  if ((s = enqueue_scan(c, 0, c->ngid, st)) != JT_OK) return s;
+  if ((s = enqueue_decode(c, st)) != JT_OK) return s;
+  c->phase = Phase::Decoded;
+  c->last_stream = st;
+  return JT_OK;
+}
+
+jt_status jt_colorize(jt_ctx* c, const jt_gbuffer* g, int filter, uint8_t* out_rgba, jt_stream stream) {
+  if (!c) return JT_ERR_INVALID_ARG;
+  if (c->phase != Phase::Decoded) return fail(c, JT_ERR_STATE, "jt_colorize needs a preceding jt_decode");
+  if (!valid_filter(filter)) return fail(c, JT_ERR_INVALID_ARG, "bad filter %d", filter);
+  jt_view v{};
+  if (g) v.g = *g;
+  v.out_rgba = out_rgba;
+  ViewSet vs;
+  jt_status s = make_views(c, &v, 1, true, vs);
+  if (s != JT_OK) return s;
+  DeviceGuard dg(c->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if ((s = enqueue_colorize(c, vs, filter, -1, st)) != JT_OK) return s;
+  c->last_stream = st;
+  return JT_OK;
+}
+
+jt_status jt_get_stats(jt_ctx* c, jt_stats* out) {
+  if (!c || !out) return JT_ERR_INVALID_ARG;
+  DeviceGuard dg(c->device);
+  JT_CUDA(c, cudaStreamSynchronize(c->last_stream));
+  FrameState fs;
+  JT_CUDA(c, cudaMemcpy(&fs, c->state, sizeof fs, cudaMemcpyDeviceToHost));
+  JT_CUDA(c, cudaMemset(&c->state->err, 0, sizeof(uint32_t)));
+  JT_CUDA(c, cudaDeviceSynchronize());
+  out->needed_blocks = fs.count;
+  out->cache_units = fs.units;
+  out->capacity_units = c->cap_units;
+  out->total_blocks = c->ngid;
+  out->levels = (uint32_t)c->descs.size();
+  out->error_bits = fs.err;
+  if (fs.err & JT_DEVERR_CORRUPT) return fail(c, JT_ERR_CORRUPT_STREAM, "corrupt entropy-coded data in a needed MCU");
+  if (fs.err & JT_DEVERR_CAPACITY) return fail(c, JT_ERR_CAPACITY, "needed %u cache units, capacity %llu", fs.units,
+                                              (unsigned long long)c->cap_units);
+  if (fs.err & JT_DEVERR_MISSING) return fail(c, JT_ERR_UNSUPPORTED, "a pixel names a texture level that was not uploaded");
+  if (fs.err & JT_DEVERR_TIMEOUT) return fail(c, JT_ERR_CUDA, "compaction wait timed out");
+  return JT_OK;
+}
+
+jt_status jt_frame(jt_ctx* c, const jt_view* views, int nviews, int filter, jt_stream stream) {
+  if (!c) return JT_ERR_INVALID_ARG;
+  if (!valid_filter(filter)) return fail(c, JT_ERR_INVALID_ARG, "bad filter %d", filter);
+  if (c->phase == Phase::Marked) return fail(c, JT_ERR_STATE, "a marked frame is pending");
+  ViewSet vs;
+  jt_status s = make_views(c, views, nviews, true, vs);
+  if (s != JT_OK) return s;
+  DeviceGuard dg(c->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if ((s = enqueue_frame(c, vs, filter, st)) != JT_OK) return s;
+  c->phase = Phase::Decoded;
+  c->last_stream = st;
+  return JT_OK;
+}
+
+jt_status jt_frame_graph(jt_ctx* c, const jt_view* views, int nviews, int filter, jt_stream stream, jt_graph** out) {
+  if (!c || !out) return JT_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!valid_filter(filter)) return fail(c, JT_ERR_INVALID_ARG, "bad filter %d", filter);
+  if (c->phase == Phase::Marked) return fail(c, JT_ERR_STATE, "a marked frame is pending");
+  ViewSet vs;
+  jt_status s = make_views(c, views, nviews, true, vs);
+  if (s != JT_OK) return s;
+  if (c->descs.empty()) return fail(c, JT_ERR_STATE, "no textures uploaded");
+  DeviceGuard dg(c->device);
+  if (!c->capture_stream) JT_CUDA(c, cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
+  cudaStream_t cs = c->capture_stream;
+  // capture on the context's own stream (the caller's may be the legacy default stream)
+  JT_CUDA(c, cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  JT_CUDA(c, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  s = enqueue_frame(c, vs, filter, cs);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cs, &graph);
+  if (s != JT_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return s;
+  }
+  if (e != cudaSuccess) return fail(c, JT_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+  jt_graph* gr = new jt_graph();
+  gr->ctx = c;
+  gr->graph = graph;
+  e = cudaGraphInstantiate(&gr->exec, graph, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    delete gr;
+    return fail(c, JT_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  }
+  *out = gr;
+  return JT_OK;
+}
+
+jt_status jt_graph_launch(jt_graph* g, jt_stream stream) {
+  if (!g || !g->exec) return JT_ERR_INVALID_ARG;
+  jt_ctx* c = g->ctx;
+  if (c->phase == Phase::Marked) return fail(c, JT_ERR_STATE, "a marked frame is pending");
+  DeviceGuard dg(c->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  JT_CUDA(c, cudaGraphLaunch(g->exec, st));
+  c->phase = Phase::Decoded;
+  c->last_stream = st;
+  return JT_OK;
+}
+
+jt_status jt_graph_destroy(jt_graph* g) {
+  if (!g) return JT_ERR_INVALID_ARG;
+  DeviceGuard dg(g->ctx->device);
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  delete g;
+  return JT_OK;
+}
+
+jt_status jt_frame_plain(jt_ctx* c, const jt_view* views, int nviews, int filter, jt_stream stream) {
+  if (!c) return JT_ERR_INVALID_ARG;
+  if (!valid_filter(filter)) return fail(c, JT_ERR_INVALID_ARG, "bad filter %d", filter);
+  if (c->phase == Phase::Marked) return fail(c, JT_ERR_STATE, "a marked frame is pending");
+  if (c->descs.empty()) return fail(c, JT_ERR_STATE, "no textures uploaded");
+  ViewSet all;
+  jt_status s = make_views(c, views, nviews, true, all);
+  if (s != JT_OK) return s;
+  DeviceGuard dg(c->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // gid range of each texture id (over its levels)
+  std::map<int, std::pair<uint64_t, uint64_t>> ranges;
+  for (size_t i = 0; i < c->descs.size(); ++i) {
+    if (c->descs[i].sampling == kSamplingCoef) continue;
+    const uint64_t lo = c->descs[i].gid_base, hi = lo + c->descs[i].nmcu;
+    auto it = ranges.find(c->levels[i].tex);
+    if (it == ranges.end())
+      ranges[c->levels[i].tex] = {lo, hi};
+    else
+      it->second = {std::min(it->second.first, lo), std::max(it->second.second, hi)};
+  }
+  for (int v = 0; v < nviews; ++v) {
+    ViewSet one;
+    if ((s = make_views(c, views + v, 1, true, one)) != JT_OK) return s;
+    if ((s = enqueue_colorize(c, one, filter, JT_EMPTY_TEXTURE, st)) != JT_OK) return s;
+    for (const auto& kv : ranges) {
+      if ((s = enqueue_mark(c, one, filter, kv.first, 0, st)) != JT_OK) return s;
+      if ((s = enqueue_scan(c, kv.second.first, kv.second.second, st)) != JT_OK) return s;
+      if ((s = enqueue_decode(c, st)) != JT_OK) return s;
+      if ((s = enqueue_colorize(c, one, filter, kv.first, st)) != JT_OK) return s;
+    }
+  }
+  c->phase = Phase::Decoded;
+  c->last_stream = st;
+  return JT_OK;
+}
+
+jt_status jt_get_tuning(const jt_ctx* c, jt_tuning* out) {
+  if (!c || !out) return JT_ERR_INVALID_ARG;
+  *out = c->tuning;
+  return JT_OK;
+}
+
+jt_status jt_set_tuning(jt_ctx* c, const jt_tuning* t) {
+  if (!c || !t) return JT_ERR_INVALID_ARG;
+  if (!valid_tuning(c, *t)) return fail(c, JT_ERR_INVALID_ARG, "invalid tuning");
+  c->tuning = *t;
+  return JT_OK;
+}
+
+jt_status jt_autotune(jt_ctx* c, const jt_view* views, int nviews, int filter, jt_stream stream, int reps,
+                      jt_tuning* best, float* best_ms) {
+  if (!c) return JT_ERR_INVALID_ARG;
+  if (reps < 1 || reps > 1000) return fail(c, JT_ERR_INVALID_ARG, "reps must be 1..1000");
+  DeviceGuard dg(c->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  JT_CUDA(c, cudaEventCreate(&e0));
+  JT_CUDA(c, cudaEventCreate(&e1));
+  const jt_tuning saved = c->tuning;
+  auto measure = [&](const jt_tuning& t, float& ms) -> jt_status {
+    c->tuning = t;
+    jt_graph* g = nullptr;
+    jt_status s = jt_frame_graph(c, views, nviews, filter, stream, &g);
+    if (s != JT_OK) return s;
+    std::vector<float> times;
+    for (int i = 0; i < reps + 2; ++i) {
+      cudaEventRecord(e0, st);
+      cudaGraphLaunch(g->exec, st);
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      float t_ms = 0;
+      cudaEventElapsedTime(&t_ms, e0, e1);
+      if (i >= 2) times.push_back(t_ms);
+    }
+    jt_graph_destroy(g);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(c, JT_ERR_CUDA, "autotune run: %s", cudaGetErrorString(e));
+    std::sort(times.begin(), times.end());
+    ms = times[times.size() / 2];
+    return JT_OK;
+  };
+  jt_tuning cur = saved, top = saved;
+  float top_ms = 1e30f;
+  jt_status s = JT_OK;
+  // stage 1: decode shape
+  for (int w : {2, 4, 6, 8}) {
+    for (int per = 1; per <= std::min(4, c->decode_occ[w]); ++per) {
+      cur = saved;
+      cur.decode_warps = w;
+      cur.decode_ctas_per_sm = per;
+      float ms;
+      if ((s = measure(cur, ms)) != JT_OK) goto done;
+      if (ms < top_ms) {
+        top_ms = ms;
+        top = cur;
+      }
+    }
+  }
+  // stage 2: pixel-kernel shape
+  for (int th : {128, 256, 512}) {
+    for (int per : {4, 8, 16}) {
+      if (th * per > 2048 * 2) continue;
+      cur = top;
+      cur.pixel_threads = th;
+      cur.pixel_ctas_per_sm = per;
+      float ms;
+      if ((s = measure(cur, ms)) != JT_OK) goto done;
+      if (ms < top_ms) {
+        top_ms = ms;
+        top = cur;
+      }
+    }
+  }
+done:
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s != JT_OK) {
+    c->tuning = saved;
+    return s;
+  }
+  c->tuning = top;
+  if (best) *best = top;
+  if (best_ms) *best_ms = top_ms;
+  return JT_OK;
+}
+
+jt_status jt_read_work_list(jt_ctx* c, uint32_t* dst, uint64_t cap, uint64_t* count) {
+  if (!c || !count) return JT_ERR_INVALID_ARG;
+  DeviceGuard dg(c->device);
+  JT_CUDA(c, cudaStreamSynchronize(c->last_stream));
+  FrameState fs;
+  JT_CUDA(c, cudaMemcpy(&fs, c->state, sizeof fs, cudaMemcpyDeviceToHost));
+  *count = fs.count;
+  const uint64_t n = std::min<uint64_t>({cap, (uint64_t)fs.count, c->gid_cap});
+  if (n && dst) JT_CUDA(c, cudaMemcpy(dst, c->work, n * 4, cudaMemcpyDefault));
+  return JT_OK;
+}
+
+jt_status jt_read_slots(jt_ctx* c, uint64_t gid_begin, uint64_t n, uint32_t* dst) {
+  if (!c || (!dst && n)) return JT_ERR_INVALID_ARG;
+  if (gid_begin + n > c->ngid) return fail(c, JT_ERR_INVALID_ARG, "gid range beyond the uploaded levels");
+  DeviceGuard dg(c->device);
+  JT_CUDA(c, cudaStreamSynchronize(c->last_stream));
+  if (n) JT_CUDA(c, cudaMemcpy(dst, c->slot + gid_begin, n * 4, cudaMemcpyDefault));
+  return JT_OK;
+}
+
+jt_status jt_read_cache(jt_ctx* c, uint64_t unit_begin, uint64_t n, uint8_t* dst) {
+  if (!c || (!dst && n)) return JT_ERR_INVALID_ARG;
+  if (unit_begin + n > c->cap_units) return fail(c, JT_ERR_INVALID_ARG, "unit range beyond the cache");
+  DeviceGuard dg(c->device);
+  JT_CUDA(c, cudaStreamSynchronize(c->last_stream));
+  if (n) JT_CUDA(c, cudaMemcpy(dst, c->cache + unit_begin * kUnitBytes, n * kUnitBytes, cudaMemcpyDefault));
+  return JT_OK;
+}
+
+// ---- float chain ------------------------------------------------------------------------
+
+jt_status jt_register_coeff_textures(jt_ctx* c, int first_tex_id, int count, int width, int height) {
+  if (!c) return JT_ERR_INVALID_ARG;
+  (void)first_tex_id; (void)count; (void)width; (void)height;
+  return fail(c, JT_ERR_UNSUPPORTED, "float chain not built yet");
+}
+
+jt_status jt_colorize_float(jt_ctx* c, const jt_gbuffer* g, const float* coeffs, float* out_rgb, jt_stream stream) {
+  if (!c) return JT_ERR_INVALID_ARG;
+  (void)g; (void)coeffs; (void)out_rgb; (void)stream;
+  return fail(c, JT_ERR_UNSUPPORTED, "float chain not built yet");
+}
+
+jt_status jt_colorize_backward(jt_ctx* c, const jt_gbuffer* g, const float* grad_frame, float* grad_coeffs,
+                               jt_stream stream) {
+  if (!c) return JT_ERR_INVALID_ARG;
+  (void)g; (void)grad_frame; (void)grad_coeffs; (void)stream;
+  return fail(c, JT_ERR_UNSUPPORTED, "float chain not built yet");
+}
+
+}  // extern "C"

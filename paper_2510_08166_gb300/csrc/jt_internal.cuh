@@ -1,0 +1,172 @@
+// Internal device-side data model of the texture path (shared by the kernels and the
+// host implementation of the C ABI in jt_api.cu).
+//
+// HBM layout
+//   descs      DevDesc[ndesc]        one per uploaded (texture, level), sorted by gid_base
+//   desc_map   int32[ntex * 16]      (tex_id, level) -> desc index, -1 when absent
+//   streams    per level: uint32 words of the unstuffed entropy stream + >= 64 zero bytes
+//   index      per level: packed 10-byte {bit_offset, dc_pred[3]} entries
+//   huff       HuffSet[nh]           decode LUTs, deduplicated by content
+//   quant      uint16[nq][2][64]     quantisation tables in zig-zag order
+//   flags      uint8[ngid]           per-frame marks: cache units of the MCU (4, 1) or 0
+//   slot       uint32[ngid]          cache-unit offset of each needed gid
+//   work       uint32[ngid]          work list (needed gids, ascending)
+//   cache      uint8[cap_units*256]  RGBA8 tiles; a 4:2:0 MCU = 4 units, 4:4:4 = 1 unit
+//   state      FrameState            counts, work counter, error word
+#pragma once
+
+#include <cstdint>
+
+#include "../../include/jt.h"
+
+namespace jt {
+
+constexpr int kLutBits = 10;                 // first-level Huffman LUT: next 10 bits
+constexpr int kLutSize = 1 << kLutBits;
+constexpr int kStreamPadBytes = 64;          // zero padding after each entropy stream
+constexpr uint32_t kUnitBytes = 256;         // cache unit
+constexpr int kSampling420 = 0, kSampling444 = 1, kSamplingCoef = 2;
+
+// Decode tables of one Huffman spec. lut[i] for the next kLutBits bits i:
+// (code length << 8) | symbol, or 0 when the code is longer than kLutBits. Longer codes
+// use maxcode[l] / valoff[l] (index of the symbol = code + valoff[l]) for l = 1..16.
+struct HuffTable {
+  uint16_t lut[kLutSize];
+  int32_t maxcode[17];  // -1 when no code of length l
+  int32_t valoff[17];
+  uint8_t vals[256];
+};
+
+// Four tables: DC luma, AC luma, DC chroma, AC chroma.
+struct HuffSet {
+  HuffTable t[4];
+};
+
+struct DevDesc {
+  const uint32_t* stream;      // big-endian words (word i = bytes 4i..4i+3)
+  const uint16_t* index;       // packed 10-byte entries, read as 5 halfwords
+  uint32_t gid_base;
+  uint32_t nmcu;
+  uint32_t nwords;             // readable words including padding
+  uint32_t nbits;              // coded bits
+  uint16_t width, height;
+  uint16_t mcus_x, mcus_y;
+  uint8_t sampling;            // kSampling420 / kSampling444 / kSamplingCoef
+  uint8_t units;               // cache units per MCU: 4 or 1
+  uint8_t hset, qset;
+  uint32_t pad0;
+};
+static_assert(sizeof(DevDesc) == 48, "descriptor layout");
+
+struct FrameState {
+  uint32_t count;        // needed MCUs after the last compaction
+  uint32_t units;        // cache units they occupy
+  uint32_t decode_next;  // next work item for the persistent decoder
+  uint32_t err;          // JT_DEVERR_* bits
+  uint32_t scan_done;    // CTAs finished in the current compaction (reset by the last one)
+  uint32_t pad[3];
+};
+
+// One view of a (possibly batched) frame, passed by value in the kernel parameters.
+struct View {
+  const float4* uv;      // two pixels per float4
+  const uint16_t* tex;
+  const uint8_t* mip;
+  uint4* out;            // four RGBA8 pixels per uint4
+  uint32_t npx;
+  uint32_t quad_begin;   // prefix sum of ceil(npx/4) over earlier views
+};
+
+struct ViewSet {
+  View v[JT_MAX_VIEWS];
+  int n;
+  uint32_t total_quads;
+};
+
+struct TexLookup {
+  const DevDesc* descs;
+  const int32_t* desc_map;
+  uint32_t map_ntex;
+};
+
+// ---- launchers (defined in the kernel translation units) ----
+struct MarkArgs {
+  ViewSet views;
+  TexLookup tl;
+  uint8_t* flags;
+  FrameState* state;
+  int filter;
+  int only_tex;   // -1: all textures; otherwise only pixels with this texture id
+  int coef_mode;  // 0: JPEG levels only; 1: coefficient textures only
+};
+void launch_mark(const MarkArgs& a, int threads, int grid, cudaStream_t s);
+
+struct ScanArgs {
+  uint8_t* flags;        // flags of gids [gid_lo, gid_lo + n)
+  uint32_t gid_lo;
+  uint32_t n;
+  uint32_t* slot;        // indexed by gid
+  uint32_t* work;
+  uint32_t work_cap;
+  uint64_t* tile_status; // one word per tile
+  FrameState* state;
+  uint32_t cap_units;
+};
+constexpr int kScanThreads = 256;
+constexpr int kScanPerThread = 16;
+constexpr int kScanTile = kScanThreads * kScanPerThread;
+void launch_scan(const ScanArgs& a, int grid, cudaStream_t s);
+
+struct DecodeArgs {
+  const DevDesc* descs;
+  uint32_t ndesc;
+  const HuffSet* huff;    // set 0 is staged in shared memory
+  const uint16_t* quant;  // [nq][2][64] zig-zag order
+  const uint32_t* work;
+  uint32_t work_cap;
+  const uint32_t* slot;
+  uint8_t* cache;
+  uint32_t cap_units;
+  FrameState* state;
+};
+size_t decode_smem_bytes(int warps);
+void launch_decode(const DecodeArgs& a, int warps, int grid, cudaStream_t s);
+int decode_max_ctas_per_sm(int warps);
+
+struct ColorizeArgs {
+  ViewSet views;
+  TexLookup tl;
+  const uint32_t* slot;
+  const uint8_t* cache;
+  uint32_t cap_units;
+  FrameState* state;
+  int filter;
+  int only_tex;
+};
+void launch_colorize(const ColorizeArgs& a, int threads, int grid, cudaStream_t s);
+
+// Float chain (differentiable colourise).
+struct FloatArgs {
+  ViewSet views;          // one view
+  TexLookup tl;
+  const uint32_t* slot;   // gid -> work position (coefficient textures use 1 unit per MCU)
+  const uint32_t* work;
+  const float* coef;      // [T][my][mx][6][64]
+  uint32_t coef_gid_base; // gid of coefficient texture 0, MCU 0
+  float4* tiles;          // [count][16][16] float4 (RGB + pad), scratch
+  uint32_t tile_cap;      // tiles available
+  float* frame;           // [npx][3] forward output or gradient input
+  float* grad_coef;       // [T][my][mx][6][64] backward output
+  FrameState* state;
+};
+void launch_float_tiles(const FloatArgs& a, int grid, cudaStream_t s);
+void launch_float_colorize(const FloatArgs& a, int threads, int grid, cudaStream_t s);
+void launch_float_zero_tiles(const FloatArgs& a, int grid, cudaStream_t s);
+void launch_float_scatter(const FloatArgs& a, int threads, int grid, cudaStream_t s);
+void launch_float_adjoint(const FloatArgs& a, int grid, cudaStream_t s);
+
+// The integer IDCT constants the decode kernel is compiled with, for the host-side check
+// against round(8192 cos(k pi / 16)), k = 1..7.
+void idct_constants(int out[8]);
+
+}  // namespace jt
