@@ -108,10 +108,11 @@ typedef struct {
 
 /* Launch configuration picked by the autotuner (or set by hand). */
 typedef struct {
-  int32_t decode_warps;      /* warps per decode CTA (2..16) */
-  int32_t decode_ctas_per_sm;/* resident decode CTAs per SM of the persistent grid (>= 1) */
-  int32_t pixel_threads;     /* threads per CTA of mark and colourise (64..1024, mult. of 32) */
-  int32_t pixel_ctas_per_sm; /* CTAs per SM of the grid-stride mark and colourise grids */
+  int32_t decode_mcus_per_warp; /* MCUs a decode warp takes at a time: 4, 8, 16 or 32 */
+  int32_t decode_warps;         /* warps per decode CTA: 2, 4, 8 or 16 */
+  int32_t decode_ctas_per_sm;   /* resident decode CTAs per SM of the persistent grid (>= 1) */
+  int32_t pixel_threads;        /* threads per CTA of mark and colourise (64..1024, mult. of 32) */
+  int32_t pixel_ctas_per_sm;    /* CTAs per SM of the grid-stride mark and colourise grids */
 } jt_tuning;
 
 /* ---- context ------------------------------------------------------------------------- */
@@ -193,9 +194,9 @@ jt_status jt_frame_plain(jt_ctx* ctx, const jt_view* views, int nviews, int filt
 jt_status jt_get_tuning(const jt_ctx* ctx, jt_tuning* out);
 jt_status jt_set_tuning(jt_ctx* ctx, const jt_tuning* t);
 
-/* Times `reps` graph replays of the frame for each candidate launch configuration
- * (decode warps per CTA x decode CTAs per SM x pixel-kernel shape), keeps the fastest in
- * the context and returns it with its median frame time in milliseconds. */
+/* Times `reps` graph replays of the frame for each candidate launch configuration (decode
+ * MCUs per warp x warps per CTA x CTAs per SM, then the pixel-kernel shape), keeps the
+ * fastest in the context and returns it with its median frame time in milliseconds. */
 jt_status jt_autotune(jt_ctx* ctx, const jt_view* views, int nviews, int filter, jt_stream stream, int reps,
                       jt_tuning* best, float* best_ms);
 

@@ -4,18 +4,21 @@
 //
 // GB300 design (the paper's one 64-thread block per MCU with a 32-lane code compare,
 // Sec. 5.2, is prior art here):
-//  * persistent grid, warps fetch 32 work items at a time from a device counter, so the
-//    uneven MCU sizes balance dynamically and the count never goes to the host;
-//  * one lane per MCU runs that MCU's serial entropy chain: a 64-bit bit buffer refilled
-//    by aligned 32-bit loads, one 10-bit first-level LUT lookup per symbol in shared
-//    memory (codes longer than 10 bits take a short MAXCODE walk), value bits extracted
-//    together with the code;
-//  * the 32 lanes step through the MCU's data units in lockstep; coefficients go to a
-//    transposed per-warp buffer coef[k][lane] (int16, zig-zag order k, conflict-free);
-//  * each lane then runs the 8x8 integer IDCT on its own column with even/odd butterflies
-//    (an exact integer factorisation of the matrix product of the decode spec);
-//  * pixels go to a per-lane shared buffer; finally the warp writes each of its 32 tiles
-//    cooperatively (32 lanes x 32 B = one 1 KiB 4:2:0 tile per step, coalesced).
+//  * persistent grid; each warp fetches M work items (M = 4, 8, 16 or 32 MCUs per warp) at
+//    a time from a device counter, so uneven MCU sizes balance dynamically and the count
+//    never goes to the host. Small M gives many warps for frames with few needed MCUs
+//    (latency hiding); large M amortises per-warp overhead for full decodes;
+//  * entropy phase: lane m < M runs MCU m's serial entropy chain over all its data units —
+//    a 64-bit bit buffer refilled by aligned 32-bit loads, one 10-bit first-level LUT
+//    lookup per symbol in shared memory (codes longer than 10 bits take a short MAXCODE
+//    walk), the value bits extracted together with the code — and writes dequantised
+//    coefficients into a per-warp buffer coef[du][natural k][m] (int16);
+//  * IDCT phase: all 32 lanes share the 8x8 integer IDCTs of the warp's 6M data units,
+//    one column (then one row) of one data unit per lane and step, with even/odd
+//    butterflies (an exact integer factorisation of the matrix product of the decode
+//    spec); rows of pixels go to a per-MCU shared buffer;
+//  * colour phase: the warp writes each MCU's RGBA8 tile cooperatively (32 lanes x 32 B =
+//    one 1 KiB 4:2:0 tile per step, coalesced).
 //
 // Decode spec (identical in the oracle): dequantised d = clamp16(q * Q); column pass
 // t = clamp16(floor((sum_v K[y][v] d[v][u] + 2^8) / 2^9)); row pass
@@ -63,8 +66,11 @@ __device__ __forceinline__ void idct8(const int in[8], int out[8]) {
 __device__ __forceinline__ int sat16(int v) { return min(32767, max(-32768, v)); }
 __device__ __forceinline__ uint32_t clamp255(int v) { return (uint32_t)min(255, max(0, v)); }
 
-constexpr int kCoefWords = 64 * 32 / 2;  // int16 [64][32] per warp
-constexpr int kPixStride = 97;           // words per lane: Y 64 + Cb 16 + Cr 16, +1 pad
+constexpr int kPixStride = 97;  // words per MCU: Y 64 + Cb 16 + Cr 16, +1 pad
+
+// Shared memory of one warp: coefficients [6][64][M] int16 (natural order), pixels
+// [M][97] words, per-MCU cache offset and descriptor bits.
+__host__ __device__ constexpr size_t warp_smem(int M) { return (size_t)6 * 64 * M * 2 + (size_t)M * kPixStride * 4 + (size_t)M * 8; }
 
 struct BitReader {
   uint64_t buf;  // valid bits MSB-aligned
@@ -74,7 +80,7 @@ struct BitReader {
   uint32_t nwords;
 
   __device__ __forceinline__ void load_word() {
-    uint32_t w = wp < nwords ? __ldg(words + wp) : 0u;
+    const uint32_t w = wp < nwords ? __ldg(words + wp) : 0u;
     ++wp;
     buf |= (uint64_t)__byte_perm(w, 0, 0x0123) << (32 - cnt);
     cnt += 32;
@@ -96,94 +102,82 @@ struct BitReader {
   __device__ __forceinline__ uint64_t position() const { return (uint64_t)wp * 32 - (uint64_t)cnt; }
 };
 
-// Decodes one data unit of `lane`'s MCU into col[k * 32] (k in zig-zag order, dequantised,
-// saturated to int16). Returns false on an invalid coding.
-__device__ __forceinline__ bool decode_du(BitReader& br, const HuffTable* dct, const HuffTable* act,
-                                          const uint16_t* __restrict__ qz, int16_t& pred, int16_t* col) {
-  int k = 0;
+constexpr uint32_t kBadEntry = 0xFFFFFFFFu;
+
+// Entry for a code longer than kLutBits (MAXCODE walk over lengths kLutBits+1..16), in the
+// LUT's format; kBadEntry when no code matches or the symbol is invalid for the class.
+__device__ __noinline__ uint32_t long_code_entry(const HuffTable* t, uint32_t top, bool dc) {
 #pragma unroll 1
-  while (k < 64) {
-    br.refill();
-    const HuffTable* t = k == 0 ? dct : act;
-    const uint32_t top = (uint32_t)(br.buf >> 48);
-    const uint32_t e = t->lut[top >> (16 - kLutBits)];
-    uint32_t len = e >> 8, sym = e & 255;
-    if (len == 0) {  // code longer than kLutBits
-#pragma unroll 1
-      for (int l = kLutBits + 1; l <= 16; ++l) {
-        const int code = (int)(top >> (16 - l));
-        if (code <= t->maxcode[l]) {
-          const int vi = code + t->valoff[l];
-          if (vi < 0 || vi > 255) return false;
-          len = l;
-          sym = t->vals[vi];
-          break;
-        }
+  for (int l = kLutBits + 1; l <= 16; ++l) {
+    const int code = (int)(top >> (16 - l));
+    if (code <= t->maxcode[l]) {
+      const int vi = code + t->valoff[l];
+      if (vi < 0 || vi > 255) return kBadEntry;
+      const uint32_t sym = t->vals[vi];
+      const uint32_t r = dc ? 0 : sym >> 4, s = dc ? sym : sym & 15;
+      if (s > (dc ? 11u : 10u)) return kBadEntry;
+      if (s == 0) {
+        if (dc) return lut_entry(l, 0, 0, kLutKindValue, 0);
+        return (r == 0 || r == 15) ? lut_entry(l, r, 0, kLutKindEnd, 0) : kBadEntry;
       }
-      if (len == 0) return false;
+      return lut_entry(l, r, s, kLutKindBits, 0);
     }
-    uint32_t r, s;
-    if (k == 0) {
-      r = 0;
-      s = sym;
-      if (s > 11) return false;
-    } else {
-      r = sym >> 4;
-      s = sym & 15;
-      if (s > 10) return false;
-    }
-    const uint32_t total = len + s;
-    const uint32_t bits = (uint32_t)(br.buf >> (64 - total));
-    br.buf <<= total;
-    br.cnt -= (int)total;
-    const uint32_t mag = bits & ((1u << s) - 1u);
-    const int v = (int)mag - ((mag < ((1u << s) >> 1)) ? (int)((1u << s) - 1u) : 0);
-    if (k == 0) {
-      pred = (int16_t)(uint16_t)((int)pred + v);
-      col[0] = (int16_t)sat16((int)pred * (int)__ldg(qz));
-      k = 1;
-    } else if (s) {
-      k += (int)r;
-      if (k > 63) return false;
-      col[k * 32] = (int16_t)sat16(v * (int)__ldg(qz + k));
-      ++k;
-    } else if (r == 15) {
-      k += 16;
-      if (k > 63) return false;
-    } else {
-      k = 64;  // end of block
-    }
+  }
+  return kBadEntry;
+}
+
+// Decodes the next symbol's entry and consumes its code (and, for kind 1, its value bits);
+// for kind 2 the value bits are read here too. Returns false on an invalid code.
+__device__ __forceinline__ bool next_symbol(BitReader& br, const HuffTable* t, bool dc, uint32_t& e, int& v) {
+  br.refill();
+  const uint32_t top = (uint32_t)(br.buf >> 48);
+  e = t->lut[top >> (16 - kLutBits)];
+  if (e == 0) {
+    e = long_code_entry(t, top, dc);
+    if (e == kBadEntry) return false;
+  }
+  const uint32_t nb = e & 31;
+  br.buf <<= nb;
+  br.cnt -= (int)nb;
+  v = (int)e >> 16;
+  if (((e >> 13) & 3) == kLutKindBits) {
+    const uint32_t s = (e >> 9) & 15;
+    const uint32_t bits = (uint32_t)(br.buf >> (64 - s));
+    br.buf <<= s;
+    br.cnt -= (int)s;
+    v = (int)bits - ((bits < (1u << (s - 1))) ? (int)((1u << s) - 1u) : 0);
   }
   return true;
 }
 
-// 8x8 integer IDCT of the lane's column; writes 8 rows of 8 pixels as word pairs at
-// dst[y * row_words], dst[y * row_words + 1].
-__device__ __forceinline__ void idct_du(int16_t* col, uint32_t* dst, int row_words) {
-#pragma unroll
-  for (int u = 0; u < 8; ++u) {  // column pass
-    int in[8], out[8];
-#pragma unroll
-    for (int v = 0; v < 8; ++v) in[v] = col[zz_pos(v, u) * 32];
-    idct8(in, out);
-#pragma unroll
-    for (int y = 0; y < 8; ++y) col[zz_pos(y, u) * 32] = (int16_t)sat16((out[y] + 256) >> 9);
-  }
-#pragma unroll
-  for (int y = 0; y < 8; ++y) {  // row pass
-    int in[8], out[8];
-#pragma unroll
-    for (int x = 0; x < 8; ++x) in[x] = col[zz_pos(y, x) * 32];
-    idct8(in, out);
-    uint32_t w0 = 0, w1 = 0;
-#pragma unroll
-    for (int x = 0; x < 4; ++x) {
-      w0 |= clamp255(((out[x] + (1 << 18)) >> 19) + 128) << (8 * x);
-      w1 |= clamp255(((out[x + 4] + (1 << 18)) >> 19) + 128) << (8 * x);
+// Decodes one data unit into col[nat[k] * M] (dequantised, saturated to int16; col must
+// be zero on entry). Returns false on an invalid coding.
+template <int M>
+__device__ __forceinline__ bool decode_du(BitReader& br, const HuffTable* dct, const HuffTable* act,
+                                          const uint16_t* __restrict__ qz, const uint8_t* nat, int16_t& pred,
+                                          int16_t* col) {
+  uint32_t e;
+  int v;
+  if (!next_symbol(br, dct, true, e, v)) return false;  // DC difference
+  pred = (int16_t)(uint16_t)((int)pred + v);
+  col[0] = (int16_t)sat16((int)pred * (int)__ldg(qz));
+  int k = 1;
+#pragma unroll 1
+  while (k < 64) {  // AC: at most 63 symbols
+    if (!next_symbol(br, act, false, e, v)) return false;
+    const int r = (int)((e >> 5) & 15);
+    if (((e >> 13) & 3) == kLutKindEnd) {
+      if (r != 15) break;  // end of block
+      k += 16;             // zero run of 16
+      if (k > 63) return false;
+      continue;
     }
-    dst[y * row_words] = w0;
-    dst[y * row_words + 1] = w1;
+    k += r;
+    if (k > 63) return false;
+    col[nat[k] * M] = (int16_t)sat16(v * (int)__ldg(qz + k));
+    ++k;
   }
+  return true;
 }
 
 __device__ __forceinline__ uint32_t ycc_pixel(uint32_t Y, int ro, int go, int bo) {
@@ -210,18 +204,32 @@ __device__ __forceinline__ int find_desc(const DevDesc* descs, int n, uint32_t g
   return lo;
 }
 
-template <int W>
-__global__ void __launch_bounds__(W * 32) k_decode(const __grid_constant__ DecodeArgs a) {
+// Word offset of row y of data unit d inside an MCU's pixel buffer, and the row pitch.
+__device__ __forceinline__ int pix_row(int d, int y, bool s420) {
+  if (s420) return d < 4 ? ((d >> 1) * 8 + y) * 4 + (d & 1) * 2 : 64 + (d - 4) * 16 + y * 2;
+  return (d == 0 ? 0 : (d == 1 ? 64 : 80)) + y * 2;
+}
+
+template <int M>
+__global__ void k_decode(const __grid_constant__ DecodeArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   HuffSet* sh = reinterpret_cast<HuffSet*>(smem);
+  uint8_t* nat = smem + sizeof(HuffSet);  // natural index of zig-zag position k
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int16_t* coef = reinterpret_cast<int16_t*>(smem + sizeof(HuffSet)) + warp * (kCoefWords * 2);
-  uint32_t* pix = reinterpret_cast<uint32_t*>(smem + sizeof(HuffSet) + W * kCoefWords * 4) + warp * 32 * kPixStride;
+  uint8_t* wbase = smem + sizeof(HuffSet) + 64 + (size_t)warp * warp_smem(M);
+  int16_t* coef = reinterpret_cast<int16_t*>(wbase);                       // [6][64][M]
+  uint32_t* pix = reinterpret_cast<uint32_t*>(wbase + 6 * 64 * M * 2);     // [M][97]
+  uint32_t* moff = pix + M * kPixStride;                                   // [M] cache unit offset
+  uint32_t* minfo = moff + M;                                              // [M] ndu | 420 << 4 | store << 5
 
-  {  // stage Huffman set 0 (the set shared by every texture coded with the same tables)
+  {  // stage Huffman set 0 and the zig-zag table
     const uint4* src = reinterpret_cast<const uint4*>(a.huff);
     uint4* dst = reinterpret_cast<uint4*>(sh);
-    for (int i = threadIdx.x; i < (int)(sizeof(HuffSet) / 16); i += W * 32) dst[i] = __ldg(src + i);
+    for (int i = threadIdx.x; i < (int)(sizeof(HuffSet) / 16); i += blockDim.x) dst[i] = __ldg(src + i);
+    if (threadIdx.x < 64) {
+      const int r = threadIdx.x >> 3, c = threadIdx.x & 7;
+      nat[zz_pos(r, c)] = (uint8_t)threadIdx.x;
+    }
   }
   __syncthreads();
 
@@ -231,36 +239,42 @@ __global__ void __launch_bounds__(W * 32) k_decode(const __grid_constant__ Decod
 #pragma unroll 1
   for (;;) {
     uint32_t base = 0;
-    if (lane == 0) base = atomicAdd(&a.state->decode_next, 32u);
+    if (lane == 0) base = atomicAdd(&a.state->decode_next, (uint32_t)M);
     base = __shfl_sync(0xFFFFFFFFu, base, 0);
     if (base >= count) break;
 
+    // ---- set-up: lane m < M takes item base + m ----
     const uint32_t item = base + lane;
-    bool act = item < count;
-    int samp = kSampling420, ndu = 6;
-    uint32_t off = 0;
-    bool store = false, bad = false;
+    bool act = lane < M && item < count;
+    const uint32_t gid = act ? __ldg(a.work + item) : 0u;
+    int d0 = 0;  // the first item's level is shared by nearly all lanes (the list is sorted)
+    if (lane == 0) d0 = find_desc(a.descs, (int)a.ndesc, gid);
+    d0 = __shfl_sync(0xFFFFFFFFu, d0, 0);
+    int ndu = 0;
+    bool s420 = true, store = false, bad = false;
+    uint32_t off = 0, nbits = 0;
     BitReader br;
-    int16_t pred[3] = {0, 0, 0};
+    int16_t pr0 = 0, pr1 = 0, pr2 = 0;
     const HuffTable* hs = sh->t;
     const uint16_t* qz = a.quant;
-    uint32_t nbits = 0;
     if (act) {
-      const uint32_t gid = __ldg(a.work + item);
-      const DevDesc d = a.descs[find_desc(a.descs, (int)a.ndesc, gid)];
-      samp = d.sampling;
+      int di = d0;
+      const uint32_t b0 = __ldg(&a.descs[d0].gid_base);
+      if (gid < b0 || gid - b0 >= __ldg(&a.descs[d0].nmcu)) di = find_desc(a.descs, (int)a.ndesc, gid);
+      const DevDesc d = a.descs[di];
       const uint32_t mcu = gid - d.gid_base;
-      if (samp == kSamplingCoef || mcu >= d.nmcu) {
+      if (d.sampling == kSamplingCoef || mcu >= d.nmcu) {
         act = false;  // not a JPEG level: nothing to decode
       } else {
-        ndu = samp == kSampling420 ? 6 : 3;
+        s420 = d.sampling == kSampling420;
+        ndu = s420 ? 6 : 3;
         off = __ldg(a.slot + gid);
         store = off + d.units <= a.cap_units;
         const uint16_t* ix = d.index + (size_t)mcu * 5;
         const uint32_t bitpos = (uint32_t)__ldg(ix) | ((uint32_t)__ldg(ix + 1) << 16);
-        pred[0] = (int16_t)__ldg(ix + 2);
-        pred[1] = (int16_t)__ldg(ix + 3);
-        pred[2] = (int16_t)__ldg(ix + 4);
+        pr0 = (int16_t)__ldg(ix + 2);
+        pr1 = (int16_t)__ldg(ix + 3);
+        pr2 = (int16_t)__ldg(ix + 4);
         br.words = d.stream;
         br.nwords = d.nwords;
         nbits = d.nbits;
@@ -269,49 +283,88 @@ __global__ void __launch_bounds__(W * 32) k_decode(const __grid_constant__ Decod
         qz = a.quant + (size_t)d.qset * 128;
       }
     }
-
-#pragma unroll 1
-    for (int du = 0; du < 6; ++du) {
-      {  // clear the warp's coefficient buffer (4 KiB, 8 x 16 B per lane)
-        uint4* z = reinterpret_cast<uint4*>(coef);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) z[lane + 32 * i] = make_uint4(0, 0, 0, 0);
-      }
-      __syncwarp();
-      const bool mine = act && du < ndu;
-      const int comp = du < ndu - 2 ? 0 : (du == ndu - 2 ? 1 : 2);
-      if (mine && !bad) {
-        const int tb = comp == 0 ? 0 : 2;
-        if (!decode_du(br, hs + tb, hs + tb + 1, qz + (comp == 0 ? 0 : 64), pred[comp], coef + lane)) bad = true;
-      }
-      __syncwarp();
-      if (mine) {
-        uint32_t* dst;
-        int row_words;
-        if (samp == kSampling420) {
-          dst = pix + lane * kPixStride + (du < 4 ? ((du >> 1) * 8) * 4 + (du & 1) * 2 : 64 + (du - 4) * 16);
-          row_words = du < 4 ? 4 : 2;
-        } else {
-          dst = pix + lane * kPixStride + (du == 0 ? 0 : (du == 1 ? 64 : 80));
-          row_words = 2;
-        }
-        idct_du(coef + lane, dst, row_words);
-      }
-      __syncwarp();
+    if (lane < M) {
+      moff[lane] = off;
+      minfo[lane] = act ? ((uint32_t)ndu | (s420 ? 16u : 0u) | (store ? 32u : 0u)) : 0u;
     }
-    if (act && !bad && br.position() > nbits) bad = true;
-    any_bad |= bad;
+    {  // clear the coefficient buffer (768 M bytes)
+      uint4* z = reinterpret_cast<uint4*>(coef);
+#pragma unroll
+      for (int i = lane; i < 48 * M; i += 32) z[i] = make_uint4(0, 0, 0, 0);
+    }
+    __syncwarp();
 
-    // colour conversion + coalesced tile stores, one MCU of the warp at a time
+    // ---- entropy phase: each active lane decodes all data units of its MCU ----
+    if (act) {
 #pragma unroll 1
-    for (int m = 0; m < 32; ++m) {
-      const bool st_m = __shfl_sync(0xFFFFFFFFu, act && store, m);
-      if (!st_m) continue;
-      const int samp_m = __shfl_sync(0xFFFFFFFFu, samp, m);
-      const uint32_t off_m = __shfl_sync(0xFFFFFFFFu, off, m);
+      for (int du = 0; du < ndu && !bad; ++du) {
+        const int comp = du < ndu - 2 ? 0 : (du == ndu - 2 ? 1 : 2);
+        const int tb = comp == 0 ? 0 : 2;
+        int16_t pred = comp == 0 ? pr0 : (comp == 1 ? pr1 : pr2);
+        if (!decode_du<M>(br, hs + tb, hs + tb + 1, qz + (comp == 0 ? 0 : 64), nat, pred,
+                          coef + (size_t)du * 64 * M + lane))
+          bad = true;
+        if (comp == 0)
+          pr0 = pred;
+        else if (comp == 1)
+          pr1 = pred;
+        else
+          pr2 = pred;
+      }
+      if (!bad && br.position() > nbits) bad = true;
+      any_bad |= bad;
+    }
+    __syncwarp();
+
+    // ---- IDCT column pass: 48M columns (6 data units x 8 columns per MCU) ----
+#pragma unroll 1
+    for (int c = lane; c < 48 * M; c += 32) {
+      const int du_idx = c >> 3, u = c & 7;
+      const int d = du_idx / M, m = du_idx % M;
+      if (d >= (int)(minfo[m] & 7)) continue;
+      int16_t* col = coef + ((size_t)d * 64 + u) * M + m;
+      int in[8], out[8];
+#pragma unroll
+      for (int v = 0; v < 8; ++v) in[v] = col[v * 8 * M];
+      if ((in[0] | in[1] | in[2] | in[3] | in[4] | in[5] | in[6] | in[7]) == 0) continue;  // stays zero
+      idct8(in, out);
+#pragma unroll
+      for (int y = 0; y < 8; ++y) col[y * 8 * M] = (int16_t)sat16((out[y] + 256) >> 9);
+    }
+    __syncwarp();
+
+    // ---- IDCT row pass: 48M rows -> pixels ----
+#pragma unroll 1
+    for (int r = lane; r < 48 * M; r += 32) {
+      const int du_idx = r >> 3, y = r & 7;
+      const int d = du_idx / M, m = du_idx % M;
+      const uint32_t info = minfo[m];
+      if (d >= (int)(info & 7)) continue;
+      const int16_t* row = coef + ((size_t)d * 64 + y * 8) * M + m;
+      int in[8], out[8];
+#pragma unroll
+      for (int x = 0; x < 8; ++x) in[x] = row[x * M];
+      idct8(in, out);
+      uint32_t w0 = 0, w1 = 0;
+#pragma unroll
+      for (int x = 0; x < 4; ++x) {
+        w0 |= clamp255(((out[x] + (1 << 18)) >> 19) + 128) << (8 * x);
+        w1 |= clamp255(((out[x + 4] + (1 << 18)) >> 19) + 128) << (8 * x);
+      }
+      uint32_t* dst = pix + m * kPixStride + pix_row(d, y, (info & 16) != 0);
+      dst[0] = w0;
+      dst[1] = w1;
+    }
+    __syncwarp();
+
+    // ---- colour conversion + coalesced tile stores, one MCU at a time ----
+#pragma unroll 1
+    for (int m = 0; m < M; ++m) {
+      const uint32_t info = minfo[m];
+      if (!(info & 32)) continue;
       const uint32_t* P = pix + m * kPixStride;
-      uint8_t* tile = a.cache + (size_t)off_m * kUnitBytes;
-      if (samp_m == kSampling420) {
+      uint8_t* tile = a.cache + (size_t)moff[m] * kUnitBytes;
+      if (info & 16) {  // 4:2:0, 16x16: lane = (row r, half h)
         const int r = lane >> 1, h = lane & 1;
         const uint32_t y0 = P[r * 4 + h * 2], y1 = P[r * 4 + h * 2 + 1];
         const uint32_t cbw = P[64 + (r >> 1) * 2 + h], crw = P[80 + (r >> 1) * 2 + h];
@@ -328,7 +381,7 @@ __global__ void __launch_bounds__(W * 32) k_decode(const __grid_constant__ Decod
         uint4* dst = reinterpret_cast<uint4*>(tile + r * 64 + h * 32);
         dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
         dst[1] = make_uint4(o[4], o[5], o[6], o[7]);
-      } else {
+      } else {  // 4:4:4, 8x8: lane = (row r, quarter q)
         const int r = lane >> 2, q = lane & 3;
         const int wi = r * 2 + (q >> 1), sh0 = 16 * (q & 1);
         const uint32_t yw = P[wi], cbw = P[64 + wi], crw = P[80 + wi];
@@ -347,46 +400,48 @@ __global__ void __launch_bounds__(W * 32) k_decode(const __grid_constant__ Decod
   if (any_bad) atomicOr(&a.state->err, JT_DEVERR_CORRUPT);
 }
 
-// The dynamic shared-memory attribute is set by decode_max_ctas_per_sm(), which the
-// context calls for every variant on its device before the first launch.
-template <int W>
-void launch_w(const DecodeArgs& a, int grid, cudaStream_t s) {
-  k_decode<W><<<grid, W * 32, decode_smem_bytes(W), s>>>(a);
-}
+size_t smem_bytes(int warps, int M) { return sizeof(HuffSet) + 64 + (size_t)warps * warp_smem(M); }
 
-template <int W>
-int max_ctas() {
-  const size_t smem = decode_smem_bytes(W);
-  cudaFuncSetAttribute(k_decode<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <int M>
+int occupancy(int warps) {
+  const size_t smem = smem_bytes(warps, M);
+  if (smem > 227 * 1024) return 0;
+  if (cudaFuncSetAttribute(k_decode<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_decode<W>, W * 32, smem) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_decode<M>, warps * 32, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
   return n;
 }
 
 }  // namespace
 
-size_t decode_smem_bytes(int warps) {
-  return sizeof(HuffSet) + (size_t)warps * kCoefWords * 4 + (size_t)warps * 32 * kPixStride * 4;
-}
+size_t decode_smem_bytes(int warps, int mcus_per_warp) { return smem_bytes(warps, mcus_per_warp); }
 
+// The dynamic shared-memory attribute of each variant is set by decode_max_ctas_per_sm(),
+// which the context calls for every (warps, M) on its device before the first launch.
 void launch_decode(const DecodeArgs& a, int warps, int grid, cudaStream_t s) {
-  switch (warps) {
-    case 2: launch_w<2>(a, grid, s); break;
-    case 4: launch_w<4>(a, grid, s); break;
-    case 6: launch_w<6>(a, grid, s); break;
-    case 8: launch_w<8>(a, grid, s); break;
-    default: launch_w<4>(a, grid, s); break;
+  const size_t smem = smem_bytes(warps, a.mcus_per_warp);
+  switch (a.mcus_per_warp) {
+    case 4: k_decode<4><<<grid, warps * 32, smem, s>>>(a); break;
+    case 8: k_decode<8><<<grid, warps * 32, smem, s>>>(a); break;
+    case 16: k_decode<16><<<grid, warps * 32, smem, s>>>(a); break;
+    default: k_decode<32><<<grid, warps * 32, smem, s>>>(a); break;
   }
 }
 
-int decode_max_ctas_per_sm(int warps) {
-  switch (warps) {
-    case 2: return max_ctas<2>();
-    case 4: return max_ctas<4>();
-    case 6: return max_ctas<6>();
-    case 8: return max_ctas<8>();
-    default: return max_ctas<4>();
+int decode_max_ctas_per_sm(int warps, int mcus_per_warp) {
+  switch (mcus_per_warp) {
+    case 4: return occupancy<4>(warps);
+    case 8: return occupancy<8>(warps);
+    case 16: return occupancy<16>(warps);
+    case 32: return occupancy<32>(warps);
   }
+  return 0;
 }
 
 void idct_constants(int out[8]) {

@@ -36,7 +36,7 @@ struct jt_ctx {
   cudaStream_t last_stream = nullptr;
   Phase phase = Phase::Idle;
   jt_tuning tuning{};
-  int decode_occ[17] = {};  // resident decode CTAs per SM by warps per CTA
+  int decode_occ[33][17] = {};  // resident decode CTAs per SM by [MCUs per warp][warps per CTA]
 
   // textures
   std::vector<DevDesc> descs;
@@ -44,8 +44,10 @@ struct jt_ctx {
   DevDesc* d_descs = nullptr;
   size_t d_descs_cap = 0;
   std::vector<int32_t> map;  // [map_ntex * 16]
+  std::vector<LevelRec> lrec;  // [map_ntex * 16]
   uint32_t map_ntex = 0;
   int32_t* d_map = nullptr;
+  LevelRec* d_lrec = nullptr;
   std::vector<HuffSet> hsets;
   HuffSet* d_huff = nullptr;
   std::vector<std::vector<uint16_t>> qsets;  // zig-zag order, 128 entries
@@ -145,8 +147,27 @@ void zigzag_natural(int nat[64]) {
     }
 }
 
+int extend_value(uint32_t bits, int s) {  // T.81 EXTEND
+  if (s == 0) return 0;
+  return bits < (1u << (s - 1)) ? (int)bits - (1 << s) + 1 : (int)bits;
+}
+
+// First-level LUT entry for symbol `sym` with a code of length l, followed in the peeked
+// window by the bits `tail` (kLutBits - l bits). 0 = not decodable from the LUT.
+uint32_t fused_entry(bool dc, int l, uint8_t sym, uint32_t tail) {
+  const int r = dc ? 0 : sym >> 4, s = dc ? sym : sym & 15;
+  if (dc && s > 11) return 0;
+  if (!dc && s > 10) return 0;
+  if (!dc && s == 0) return (r == 0 || r == 15) ? lut_entry(l, r, 0, kLutKindEnd, 0) : 0;
+  if (l + s <= kLutBits) {
+    const uint32_t bits = (tail >> (kLutBits - l - s)) & ((1u << s) - 1u);
+    return lut_entry(l + s, r, 0, kLutKindValue, extend_value(bits, s));
+  }
+  return lut_entry(l, r, s, kLutKindBits, 0);
+}
+
 // Canonical decode tables of one Huffman spec (T.81 Annex C code assignment).
-bool build_table(const jt_huff_spec& spec, HuffTable& t, std::string& why) {
+bool build_table(const jt_huff_spec& spec, bool dc, HuffTable& t, std::string& why) {
   std::memset(&t, 0, sizeof t);
   int n = 0;
   uint64_t kraft = 0;
@@ -174,7 +195,7 @@ bool build_table(const jt_huff_spec& spec, HuffTable& t, std::string& why) {
       for (int i = 0; i < nl; ++i, ++k, ++code) {
         if (l <= kLutBits) {
           const int first = code << (kLutBits - l), cnt = 1 << (kLutBits - l);
-          for (int j = 0; j < cnt; ++j) t.lut[first + j] = (uint16_t)((l << 8) | spec.vals[k]);
+          for (int j = 0; j < cnt; ++j) t.lut[first + j] = fused_entry(dc, l, spec.vals[k], (uint32_t)j);
         }
       }
       t.maxcode[l] = code - 1;
@@ -219,9 +240,14 @@ jt_status sync_descs(jt_ctx* c) {
   }
   JT_CUDA(c, cudaMemcpy(c->d_descs, c->descs.data(), c->descs.size() * sizeof(DevDesc), cudaMemcpyHostToDevice));
   dev_free(c->d_map);
+  dev_free(c->d_lrec);
   jt_status s = dev_alloc(c, &c->d_map, c->map.size() * 4);
   if (s != JT_OK) return s;
-  JT_CUDA(c, cudaMemcpy(c->d_map, c->map.data(), c->map.size() * 4, cudaMemcpyHostToDevice));
+  if ((s = dev_alloc(c, &c->d_lrec, c->lrec.size() * sizeof(LevelRec))) != JT_OK) return s;
+  if (!c->map.empty()) {
+    JT_CUDA(c, cudaMemcpy(c->d_map, c->map.data(), c->map.size() * 4, cudaMemcpyHostToDevice));
+    JT_CUDA(c, cudaMemcpy(c->d_lrec, c->lrec.data(), c->lrec.size() * sizeof(LevelRec), cudaMemcpyHostToDevice));
+  }
   return JT_OK;
 }
 
@@ -238,7 +264,11 @@ jt_status sync_tables(jt_ctx* c) {
   return JT_OK;
 }
 
-TexLookup lookup(const jt_ctx* c) { return TexLookup{c->d_descs, c->d_map, c->map_ntex}; }
+TexLookup lookup(const jt_ctx* c) {
+  return TexLookup{c->d_descs, c->d_map, reinterpret_cast<const uint4*>(c->d_lrec), c->map_ntex};
+}
+
+bool pow2(uint32_t v) { return v && !(v & (v - 1)); }
 
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
@@ -254,7 +284,7 @@ jt_status check_gbuffer(jt_ctx* c, const jt_gbuffer* g) {
 jt_status make_views(jt_ctx* c, const jt_view* views, int n, bool need_out, ViewSet& vs) {
   if (!views || n <= 0 || n > JT_MAX_VIEWS) return fail(c, JT_ERR_INVALID_ARG, "need 1..%d views", JT_MAX_VIEWS);
   std::memset(&vs, 0, sizeof vs);
-  uint64_t quads = 0;
+  uint64_t quads = 0, tiles = 0;
   for (int i = 0; i < n; ++i) {
     jt_status s = check_gbuffer(c, &views[i].g);
     if (s != JT_OK) return s;
@@ -268,18 +298,23 @@ jt_status make_views(jt_ctx* c, const jt_view* views, int n, bool need_out, View
     v.npx = (uint32_t)((uint64_t)views[i].g.width * views[i].g.height);
     v.quad_begin = (uint32_t)quads;
     quads += (v.npx + 3) / 4;
+    v.width = views[i].g.width;
+    v.height = views[i].g.height;
+    v.tiles_x = (uint32_t)((v.width + kTileW - 1) / kTileW);
+    v.tile_begin = (uint32_t)tiles;
+    tiles += (uint64_t)v.tiles_x * ((v.height + kTileH - 1) / kTileH);
   }
   if (quads >= (1ull << 31)) return fail(c, JT_ERR_INVALID_ARG, "views too large");
   vs.n = n;
   vs.total_quads = (uint32_t)quads;
+  vs.total_tiles = (uint32_t)tiles;
   return JT_OK;
 }
 
-int pixel_grid(const jt_ctx* c, uint32_t quads) {
-  const int threads = c->tuning.pixel_threads;
-  const uint64_t want = (quads + threads - 1) / threads;
+// Persistent grid for the tiled screen passes: at most one CTA per tile.
+int pixel_grid(const jt_ctx* c, const ViewSet& vs) {
   const uint64_t cap = (uint64_t)c->sm_count * std::max(1, c->tuning.pixel_ctas_per_sm);
-  return (int)std::max<uint64_t>(1, std::min(want, cap));
+  return (int)std::max<uint64_t>(1, std::min<uint64_t>(vs.total_tiles, cap));
 }
 
 jt_status check_launch(jt_ctx* c, const char* what) {
@@ -298,7 +333,7 @@ jt_status enqueue_mark(jt_ctx* c, const ViewSet& vs, int filter, int only_tex, i
   a.filter = filter;
   a.only_tex = only_tex;
   a.coef_mode = coef_mode;
-  launch_mark(a, c->tuning.pixel_threads, pixel_grid(c, vs.total_quads), s);
+  launch_mark(a, c->tuning.pixel_threads, pixel_grid(c, vs), s);
   return check_launch(c, "mark");
 }
 
@@ -324,6 +359,7 @@ jt_status enqueue_decode(jt_ctx* c, cudaStream_t s) {
   DecodeArgs a{};
   a.descs = c->d_descs;
   a.ndesc = (uint32_t)c->descs.size();
+  a.mcus_per_warp = c->tuning.decode_mcus_per_warp;
   a.huff = c->d_huff;
   a.quant = c->d_quant;
   a.work = c->work;
@@ -333,7 +369,7 @@ jt_status enqueue_decode(jt_ctx* c, cudaStream_t s) {
   a.cap_units = (uint32_t)c->cap_units;
   a.state = c->state;
   const int w = c->tuning.decode_warps;
-  const int per_sm = std::max(1, std::min(c->tuning.decode_ctas_per_sm, c->decode_occ[w]));
+  const int per_sm = std::max(1, std::min(c->tuning.decode_ctas_per_sm, c->decode_occ[a.mcus_per_warp][w]));
   launch_decode(a, w, c->sm_count * per_sm, s);
   return check_launch(c, "decode");
 }
@@ -348,14 +384,18 @@ jt_status enqueue_colorize(jt_ctx* c, const ViewSet& vs, int filter, int only_te
   a.state = c->state;
   a.filter = filter;
   a.only_tex = only_tex;
-  launch_colorize(a, c->tuning.pixel_threads, pixel_grid(c, vs.total_quads), s);
+  launch_colorize(a, c->tuning.pixel_threads, pixel_grid(c, vs), s);
   return check_launch(c, "colorize");
 }
 
 jt_status enqueue_frame(jt_ctx* c, const ViewSet& vs, int filter, cudaStream_t s) {
   jt_status st;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (c->profiling) cudaStreamIsCapturing(s, &cap);
+  // while capturing, only an "external" record becomes an event-record node of the graph
+  const unsigned rec_flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
   auto mark_time = [&](int i) {
-    if (c->profiling) cudaEventRecord(c->prof[i], s);
+    if (c->profiling) cudaEventRecordWithFlags(c->prof[i], s, rec_flags);
   };
   mark_time(0);
   if ((st = enqueue_mark(c, vs, filter, -1, 0, s)) != JT_OK) return st;
@@ -371,9 +411,14 @@ jt_status enqueue_frame(jt_ctx* c, const ViewSet& vs, int filter, cudaStream_t s
 
 bool valid_filter(int f) { return f == JT_FILTER_NEAREST || f == JT_FILTER_BILINEAR; }
 
+const int kMcusPerWarp[] = {4, 8, 16, 32};
+const int kDecodeWarps[] = {2, 4, 8, 16};
+
 bool valid_tuning(const jt_ctx* c, const jt_tuning& t) {
-  const bool w_ok = t.decode_warps == 2 || t.decode_warps == 4 || t.decode_warps == 6 || t.decode_warps == 8;
-  return w_ok && c->decode_occ[t.decode_warps] > 0 && t.decode_ctas_per_sm >= 1 && t.pixel_threads >= 64 &&
+  const int M = t.decode_mcus_per_warp, W = t.decode_warps;
+  const bool m_ok = M == 4 || M == 8 || M == 16 || M == 32;
+  const bool w_ok = W == 2 || W == 4 || W == 8 || W == 16;
+  return m_ok && w_ok && c->decode_occ[M][W] > 0 && t.decode_ctas_per_sm >= 1 && t.pixel_threads >= 64 &&
          t.pixel_threads <= 1024 && t.pixel_threads % 32 == 0 && t.pixel_ctas_per_sm >= 1 &&
          t.pixel_ctas_per_sm <= 32;
 }
@@ -425,10 +470,12 @@ jt_status jt_create(jt_ctx** out, int device, uint64_t max_cache_blocks) {
       delete c;
       return JT_ERR_UNSUPPORTED;
     }
-  for (int w : {2, 4, 6, 8}) c->decode_occ[w] = decode_max_ctas_per_sm(w);
+  for (int M : kMcusPerWarp)
+    for (int W : kDecodeWarps) c->decode_occ[M][W] = decode_max_ctas_per_sm(W, M);
   cudaGetLastError();
-  c->tuning.decode_warps = 4;
-  c->tuning.decode_ctas_per_sm = std::max(1, c->decode_occ[4]);
+  c->tuning.decode_mcus_per_warp = 8;
+  c->tuning.decode_warps = 8;
+  c->tuning.decode_ctas_per_sm = std::max(1, c->decode_occ[8][8]);
   c->tuning.pixel_threads = 256;
   c->tuning.pixel_ctas_per_sm = 8;
   c->cap_units = max_cache_blocks * 4;
@@ -457,6 +504,7 @@ jt_status jt_destroy(jt_ctx* c) {
   }
   dev_free(c->d_descs);
   dev_free(c->d_map);
+  dev_free(c->d_lrec);
   dev_free(c->d_huff);
   dev_free(c->d_quant);
   dev_free(c->flags);
@@ -496,9 +544,16 @@ static jt_status add_level(jt_ctx* c, int tex_id, int level, DevDesc d, Level L)
     uint32_t n = std::max<uint32_t>((uint32_t)tex_id + 1, c->map_ntex * 2);
     n = std::min<uint32_t>(n, 0xFFFF);
     c->map.resize((size_t)n * JT_MAX_LEVELS, -1);
+    c->lrec.resize((size_t)n * JT_MAX_LEVELS, LevelRec{0, 0, 0, 0});
     c->map_ntex = n;
   }
   c->map[(size_t)tex_id * JT_MAX_LEVELS + level] = (int32_t)c->descs.size();
+  LevelRec& r = c->lrec[(size_t)tex_id * JT_MAX_LEVELS + level];
+  r.gid_base = d.gid_base;
+  r.wh = (uint32_t)d.width | ((uint32_t)d.height << 16);
+  r.info = level_info(d.mcus_x, d.sampling == kSampling444 ? 3 : 4, d.units, d.sampling, pow2(d.width),
+                      pow2(d.height));
+  r.pad = 0;
   c->descs.push_back(d);
   c->levels.push_back(L);
   c->ngid += d.nmcu;
@@ -533,7 +588,8 @@ jt_status jt_upload_texture(jt_ctx* c, int tex_id, int level, int width, int hei
   HuffSet hs;
   std::string why;
   for (int t = 0; t < 4; ++t)
-    if (!build_table(huff[t], hs.t[t], why)) return fail(c, JT_ERR_INVALID_ARG, "Huffman table %d: %s", t, why.c_str());
+    if (!build_table(huff[t], t % 2 == 0, hs.t[t], why))
+      return fail(c, JT_ERR_INVALID_ARG, "Huffman table %d: %s", t, why.c_str());
   int hset = -1;
   for (size_t i = 0; i < c->hsets.size(); ++i)
     if (std::memcmp(&c->hsets[i], &hs, sizeof hs) == 0) hset = (int)i;
@@ -822,17 +878,23 @@ jt_status jt_autotune(jt_ctx* c, const jt_view* views, int nviews, int filter, j
   jt_tuning cur = saved, top = saved;
   float top_ms = 1e30f;
   jt_status s = JT_OK;
-  // stage 1: decode shape
-  for (int w : {2, 4, 6, 8}) {
-    for (int per = 1; per <= std::min(4, c->decode_occ[w]); ++per) {
-      cur = saved;
-      cur.decode_warps = w;
-      cur.decode_ctas_per_sm = per;
-      float ms;
-      if ((s = measure(cur, ms)) != JT_OK) goto done;
-      if (ms < top_ms) {
-        top_ms = ms;
-        top = cur;
+  // stage 1: decode shape (MCUs per warp x warps per CTA at full occupancy, then fewer CTAs)
+  for (int M : kMcusPerWarp) {
+    for (int W : kDecodeWarps) {
+      const int occ = c->decode_occ[M][W];
+      if (occ <= 0) continue;
+      for (int per : {occ, std::max(1, occ / 2)}) {
+        cur = saved;
+        cur.decode_mcus_per_warp = M;
+        cur.decode_warps = W;
+        cur.decode_ctas_per_sm = per;
+        float ms;
+        if ((s = measure(cur, ms)) != JT_OK) goto done;
+        if (ms < top_ms) {
+          top_ms = ms;
+          top = cur;
+        }
+        if (occ == 1) break;
       }
     }
   }

@@ -27,11 +27,23 @@ constexpr int kStreamPadBytes = 64;          // zero padding after each entropy 
 constexpr uint32_t kUnitBytes = 256;         // cache unit
 constexpr int kSampling420 = 0, kSampling444 = 1, kSamplingCoef = 2;
 
-// Decode tables of one Huffman spec. lut[i] for the next kLutBits bits i:
-// (code length << 8) | symbol, or 0 when the code is longer than kLutBits. Longer codes
-// use maxcode[l] / valoff[l] (index of the symbol = code + valoff[l]) for l = 1..16.
+// Decode tables of one Huffman spec. lut[i] describes the symbol whose code starts the
+// next kLutBits bits i (0 when that code is longer than kLutBits, or its symbol is not
+// valid for the table's class; such codes take the MAXCODE walk, which also rejects
+// invalid symbols):
+//   bits  0..4   bits to consume now: code length + value bits (kind 1) or code length
+//   bits  5..8   run (AC zero run; 15 with kind 3 is ZRL)
+//   bits  9..12  size (value bits still to read, kind 2)
+//   bits 13..14  kind: 1 value decoded in the entry, 2 value bits follow, 3 EOB / ZRL
+//   bits 16..31  the decoded (sign-extended) value for kind 1
+// Longer codes use maxcode[l] / valoff[l] (index of the symbol = code + valoff[l]).
+constexpr uint32_t kLutKindValue = 1, kLutKindBits = 2, kLutKindEnd = 3;
+__host__ __device__ constexpr uint32_t lut_entry(uint32_t nbits, uint32_t run, uint32_t size, uint32_t kind,
+                                                 int value) {
+  return nbits | (run << 5) | (size << 9) | (kind << 13) | ((uint32_t)(value & 0xFFFF) << 16);
+}
 struct HuffTable {
-  uint16_t lut[kLutSize];
+  uint32_t lut[kLutSize];
   int32_t maxcode[17];  // -1 when no code of length l
   int32_t valoff[17];
   uint8_t vals[256];
@@ -67,6 +79,10 @@ struct FrameState {
   uint32_t pad[3];
 };
 
+// Screen passes walk each view in tiles of kTileW x kTileH pixels (one CTA per tile at a
+// time, one warp per 128-pixel row segment), so a CTA's pixels share MCUs.
+constexpr int kTileW = 128, kTileH = 32;
+
 // One view of a (possibly batched) frame, passed by value in the kernel parameters.
 struct View {
   const float4* uv;      // two pixels per float4
@@ -75,17 +91,41 @@ struct View {
   uint4* out;            // four RGBA8 pixels per uint4
   uint32_t npx;
   uint32_t quad_begin;   // prefix sum of ceil(npx/4) over earlier views
+  int32_t width, height;
+  uint32_t tiles_x;      // ceil(width / kTileW)
+  uint32_t tile_begin;   // prefix sum of tile counts over earlier views
 };
 
 struct ViewSet {
   View v[JT_MAX_VIEWS];
   int n;
   uint32_t total_quads;
+  uint32_t total_tiles;
 };
+
+// Per-(texture, level) record for the screen passes, indexed directly by
+// tex_id * JT_MAX_LEVELS + level; 16 bytes, one vector load. w == 0 marks a missing level.
+//   x: gid_base
+//   y: width (16) | height (16)
+//   z: mcus_x (16) | mcu shift (4: 4 at 4:2:0, 3 at 4:4:4) | units (4) | sampling (4) |
+//      width is a power of two (1) | height is a power of two (1)
+//   w: unused
+struct LevelRec {
+  uint32_t gid_base;
+  uint32_t wh;
+  uint32_t info;
+  uint32_t pad;
+};
+__host__ __device__ inline uint32_t level_info(uint32_t mcus_x, uint32_t shift, uint32_t units, uint32_t sampling,
+                                               bool wpow2, bool hpow2) {
+  return (mcus_x & 0xFFFF) | (shift << 16) | (units << 20) | (sampling << 24) | ((wpow2 ? 1u : 0u) << 28) |
+         ((hpow2 ? 1u : 0u) << 29);
+}
 
 struct TexLookup {
   const DevDesc* descs;
   const int32_t* desc_map;
+  const uint4* levels;  // LevelRec per (tex, level), same indexing as desc_map
   uint32_t map_ntex;
 };
 
@@ -120,6 +160,7 @@ void launch_scan(const ScanArgs& a, int grid, cudaStream_t s);
 struct DecodeArgs {
   const DevDesc* descs;
   uint32_t ndesc;
+  int mcus_per_warp;      // M: 4, 8, 16 or 32
   const HuffSet* huff;    // set 0 is staged in shared memory
   const uint16_t* quant;  // [nq][2][64] zig-zag order
   const uint32_t* work;
@@ -129,9 +170,9 @@ struct DecodeArgs {
   uint32_t cap_units;
   FrameState* state;
 };
-size_t decode_smem_bytes(int warps);
+size_t decode_smem_bytes(int warps, int mcus_per_warp);
 void launch_decode(const DecodeArgs& a, int warps, int grid, cudaStream_t s);
-int decode_max_ctas_per_sm(int warps);
+int decode_max_ctas_per_sm(int warps, int mcus_per_warp);
 
 struct ColorizeArgs {
   ViewSet views;

@@ -1,16 +1,21 @@
 // Screen-space passes over the deferred G-buffer: Mark (paper Sec. 4.2) and Resolve /
 // colourise (Sec. 4.4), for one or several views in one launch.
 //
-// Both are HBM-bound streams over the G-buffer (11 B/px read; colourise also writes 4 B/px
-// and gathers texels from the block cache). Each thread handles a quad of 4 consecutive
-// pixels with 32 B + 8 B + 4 B vector loads (and one 16 B store), in a grid-stride loop
-// over all views' quads; views are passed by value (__grid_constant__).
+// Both stream the G-buffer (11 B/px read; colourise also writes 4 B/px and gathers texels
+// from the block cache). A persistent grid walks the views in 128 x 32 pixel tiles, one
+// warp per 128-pixel row segment and one quad of 4 pixels per lane (32 B + 8 B + 4 B vector
+// loads, one 16 B store). Pixels of a tile share MCUs, so Mark keeps a 1024-entry table of
+// the gids its CTA already flagged in shared memory and stores each flag about once per CTA
+// instead of once per pixel (the byte stores of every SM to the same flag lines otherwise
+// dominate the pass). A pixel's (texture, level) record is one 16-byte load, kept in
+// registers while consecutive pixels share it; levels whose sides are powers of two (all
+// mip chains of power-of-two textures) wrap with a mask, MCU coordinates are shifts.
 //
-// Texel addressing (shared by both passes and fixed in fp32 with explicit rounding so it
-// is the same on every device): nearest x = floor(u * w) floor-mod w; bilinear
-// xs = u * w - 1/2, x0 = floor(xs), fx = xs - x0, taps x0 and x0 + 1 (floor-mod w); the MCU
-// of texel (x, y) is x / mw + (y / mw) * mcus_x with mw = 16 (4:2:0) or 8 (4:4:4), and its
-// key is the level's gid_base + MCU (Sec. 4.6).
+// Texel addressing (fixed in fp32 with explicit rounding so it is the same on every
+// device): nearest x = floor(u * w) floor-mod w; bilinear xs = u * w - 1/2, x0 = floor(xs),
+// fx = xs - x0, taps x0 and x0 + 1 (floor-mod w); the MCU of texel (x, y) is
+// x / mw + (y / mw) * mcus_x with mw = 16 (4:2:0) or 8 (4:4:4), and its key is the level's
+// gid_base + MCU (Sec. 4.6).
 #include <cuda_runtime.h>
 
 #include "jt_internal.cuh"
@@ -25,70 +30,88 @@ __device__ __forceinline__ int floor_mod_i(int a, int w) {
   return r < 0 ? r + w : r;
 }
 
-struct LevelInfo {
+struct Lvl {
   uint32_t gid_base;
-  int w, h, mcus_x, mw;
-  uint32_t units;
-  int sampling;
+  int w, h, mcus_x, shift;
+  uint32_t units, sampling;
+  bool wp2, hp2;
+  float wf, hf;
 };
 
-// (tex, mip) -> level; false when the pair was never uploaded.
-__device__ __forceinline__ bool lookup_level(const TexLookup& tl, uint32_t tex, uint32_t mip, LevelInfo& L) {
-  if (tex >= tl.map_ntex || mip >= JT_MAX_LEVELS) return false;
-  int di = __ldg(&tl.desc_map[tex * JT_MAX_LEVELS + mip]);
-  if (di < 0) return false;
-  const DevDesc* d = tl.descs + di;
-  L.gid_base = __ldg(&d->gid_base);
-  L.w = __ldg(&d->width);
-  L.h = __ldg(&d->height);
-  L.mcus_x = __ldg(&d->mcus_x);
-  L.sampling = __ldg(&d->sampling);
-  L.units = __ldg(&d->units);
-  L.mw = L.sampling == kSampling444 ? 8 : 16;
-  return true;
+// Cached (texture, level) lookup; returns false when the level does not exist.
+struct LevelCache {
+  uint32_t key = 0xFFFFFFFFu;
+  bool ok = false;
+  Lvl L;
+  __device__ __forceinline__ bool get(const TexLookup& tl, uint32_t tex, uint32_t mip) {
+    const uint32_t k = (tex << 4) | mip;
+    if (k != key) {
+      key = k;
+      ok = false;
+      if (tex < tl.map_ntex && mip < JT_MAX_LEVELS) {
+        const uint4 r = __ldg(tl.levels + (tex * JT_MAX_LEVELS + mip));
+        L.w = (int)(r.y & 0xFFFF);
+        if (L.w != 0) {
+          ok = true;
+          L.gid_base = r.x;
+          L.h = (int)(r.y >> 16);
+          L.mcus_x = (int)(r.z & 0xFFFF);
+          L.shift = (int)((r.z >> 16) & 15);
+          L.units = (r.z >> 20) & 15;
+          L.sampling = (r.z >> 24) & 15;
+          L.wp2 = (r.z >> 28) & 1;
+          L.hp2 = (r.z >> 29) & 1;
+          L.wf = (float)L.w;
+          L.hf = (float)L.h;
+        }
+      }
+    }
+    return ok;
+  }
+};
+
+__device__ __forceinline__ int wrap(int a, int w, bool pow2) { return pow2 ? (a & (w - 1)) : floor_mod_i(a, w); }
+
+__device__ __forceinline__ void nearest_texel(float u, float v, const Lvl& L, int& x, int& y) {
+  x = wrap(__float2int_rd(__fmul_rn(u, L.wf)), L.w, L.wp2);  // cvt.rmi saturates out-of-range values
+  y = wrap(__float2int_rd(__fmul_rn(v, L.hf)), L.h, L.hp2);
 }
 
-__device__ __forceinline__ void nearest_texel(float u, float v, const LevelInfo& L, int& x, int& y) {
-  float uw = __fmul_rn(u, (float)L.w);
-  float vh = __fmul_rn(v, (float)L.h);
-  x = floor_mod_i(__float2int_rd(uw), L.w);  // cvt.rmi saturates out-of-range values
-  y = floor_mod_i(__float2int_rd(vh), L.h);
-}
-
-__device__ __forceinline__ void bilinear_taps(float u, float v, const LevelInfo& L, int& xa, int& xb, int& ya,
-                                              int& yb, float& fx, float& fy) {
-  float xs = __fsub_rn(__fmul_rn(u, (float)L.w), 0.5f);
-  float ys = __fsub_rn(__fmul_rn(v, (float)L.h), 0.5f);
-  float x0 = floorf(xs), y0 = floorf(ys);
+__device__ __forceinline__ void bilinear_taps(float u, float v, const Lvl& L, int& xa, int& xb, int& ya, int& yb,
+                                              float& fx, float& fy) {
+  const float xs = __fsub_rn(__fmul_rn(u, L.wf), 0.5f);
+  const float ys = __fsub_rn(__fmul_rn(v, L.hf), 0.5f);
+  const float x0 = floorf(xs), y0 = floorf(ys);
   fx = __fsub_rn(xs, x0);
   fy = __fsub_rn(ys, y0);
-  xa = floor_mod_i(__float2int_rd(x0), L.w);
-  ya = floor_mod_i(__float2int_rd(y0), L.h);
+  xa = wrap(__float2int_rd(x0), L.w, L.wp2);
+  ya = wrap(__float2int_rd(y0), L.h, L.hp2);
   xb = xa + 1 == L.w ? 0 : xa + 1;
   yb = ya + 1 == L.h ? 0 : ya + 1;
 }
 
-// Locates the view of global quad q (views are few and sorted by quad_begin).
-__device__ __forceinline__ int view_of(const ViewSet& vs, uint32_t q) {
+// Locates the view of global tile `tile` (views are few and sorted by tile_begin).
+__device__ __forceinline__ int view_of_tile(const ViewSet& vs, uint32_t tile) {
   int vi = 0;
 #pragma unroll 1
   for (int i = 1; i < vs.n; ++i)
-    if (q >= vs.v[i].quad_begin) vi = i;
+    if (tile >= vs.v[i].tile_begin) vi = i;
   return vi;
 }
 
-// Loads the 4 pixels of quad `lq` of view V (n = pixels present, 0..4).
-__device__ __forceinline__ int load_quad(const View& V, uint32_t lq, float u[4], float v[4], uint32_t t[4],
-                                         uint32_t m[4]) {
-  uint32_t p0 = lq * 4;
-  int n = (int)min(4u, V.npx - p0);
-  if (n == 4) {
-    float4 a = __ldg(V.uv + 2 * lq), b = __ldg(V.uv + 2 * lq + 1);
+// Loads up to 4 pixels of row y starting at column x (n = pixels present, 0..4).
+__device__ __forceinline__ int load_px4(const View& V, int y, int x, float u[4], float v[4], uint32_t t[4],
+                                        uint32_t m[4]) {
+  const int n = (y < V.height && x < V.width) ? min(4, V.width - x) : 0;
+  const uint32_t p0 = (uint32_t)y * (uint32_t)V.width + (uint32_t)x;
+  if (n == 4 && (V.width & 3) == 0) {
+    const uint32_t lq = p0 >> 2;
+    const float4 a = __ldg(V.uv + 2 * lq), b = __ldg(V.uv + 2 * lq + 1);
     u[0] = a.x; v[0] = a.y; u[1] = a.z; v[1] = a.w;
     u[2] = b.x; v[2] = b.y; u[3] = b.z; v[3] = b.w;
-    uint2 tt = __ldg(reinterpret_cast<const uint2*>(V.tex) + lq);
+    const uint2 tt = __ldg(reinterpret_cast<const uint2*>(V.tex) + lq);
     t[0] = tt.x & 0xFFFF; t[1] = tt.x >> 16; t[2] = tt.y & 0xFFFF; t[3] = tt.y >> 16;
-    uint32_t mm = __ldg(reinterpret_cast<const uint32_t*>(V.mip) + lq);
+    const uint32_t mm = __ldg(reinterpret_cast<const uint32_t*>(V.mip) + lq);
     m[0] = mm & 255; m[1] = (mm >> 8) & 255; m[2] = (mm >> 16) & 255; m[3] = mm >> 24;
   } else {
     const float* uvs = reinterpret_cast<const float*>(V.uv);
@@ -109,114 +132,128 @@ __device__ __forceinline__ int load_quad(const View& V, uint32_t lq, float u[4],
   return n;
 }
 
+// Iterates the (view, row, column) of this thread's quads over the CTA's tiles:
+// f(V, y, x) for every row segment a warp owns; warps take rows w, w + nwarps, ...
+template <typename F>
+__device__ __forceinline__ void for_each_quad(const ViewSet& vs, F&& f) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+#pragma unroll 1
+  for (uint32_t tile = blockIdx.x; tile < vs.total_tiles; tile += gridDim.x) {
+    const int vi = view_of_tile(vs, tile);
+    const View& V = vs.v[vi];
+    const uint32_t lt = tile - V.tile_begin;
+    const int x = (int)(lt % V.tiles_x) * kTileW + lane * 4;
+    const int y0 = (int)(lt / V.tiles_x) * kTileH;
+#pragma unroll 1
+    for (int r = warp; r < kTileH; r += nwarps) f(V, y0 + r, x);
+  }
+}
+
 // ---------------------------------------------------------------------------------------
 // Mark
 // ---------------------------------------------------------------------------------------
+constexpr int kSeen = 1024;  // per-CTA table of recently flagged gids
+
 template <int FILTER>
 __global__ void k_mark(const __grid_constant__ MarkArgs a) {
-  const int lane = threadIdx.x & 31;
-  const uint32_t stride = gridDim.x * blockDim.x;
-  const uint32_t total = a.views.total_quads;
-  uint32_t last[4] = {kNoGid, kNoGid, kNoGid, kNoGid};
+  __shared__ uint32_t seen[kSeen];
+  for (int i = threadIdx.x; i < kSeen; i += blockDim.x) seen[i] = kNoGid;
+  __syncthreads();
+  LevelCache lc;
   bool missing = false;
-  // warp-uniform loop bound so every lane takes part in the neighbour shuffles
-  for (uint32_t q0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); q0 < total; q0 += stride) {
-    const uint32_t q = q0 + lane;
+  auto flag = [&](uint32_t g, uint8_t units) {
+    uint32_t& e = seen[(g ^ (g >> 10)) & (kSeen - 1)];
+    if (e != g) {  // racy by design: a duplicate store writes the same byte
+      e = g;
+      a.flags[g] = units;
+    }
+  };
+  for_each_quad(a.views, [&](const View& V, int y, int x) {
     float u[4], v[4];
     uint32_t t[4], m[4];
-    int n = 0;
-    if (q < total) {
-      const int vi = view_of(a.views, q);
-      n = load_quad(a.views.v[vi], q - a.views.v[vi].quad_begin, u, v, t, m);
-    }
+    const int n = load_px4(V, y, x, u, v, t, m);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      uint32_t g[4] = {kNoGid, kNoGid, kNoGid, kNoGid};
-      uint32_t units = 0;
-      if (i < n && t[i] != JT_EMPTY_TEXTURE && (a.only_tex < 0 || (int)t[i] == a.only_tex)) {
-        LevelInfo L;
-        bool ok = lookup_level(a.tl, t[i], m[i], L);
-        if (ok && ((L.sampling == kSamplingCoef) != (a.coef_mode != 0))) ok = false;
-        if (!ok) {
-          missing = true;
-        } else {
-          units = L.units;
-          if (FILTER == JT_FILTER_NEAREST) {
-            int x, y;
-            nearest_texel(u[i], v[i], L, x, y);
-            g[0] = L.gid_base + x / L.mw + (y / L.mw) * L.mcus_x;
-          } else {
-            int xa, xb, ya, yb;
-            float fx, fy;
-            bilinear_taps(u[i], v[i], L, xa, xb, ya, yb, fx, fy);
-            int mxa = xa / L.mw, mxb = xb / L.mw, mya = ya / L.mw, myb = yb / L.mw;
-            g[0] = L.gid_base + mxa + mya * L.mcus_x;
-            if (mxb != mxa) g[1] = L.gid_base + mxb + mya * L.mcus_x;
-            if (myb != mya) g[2] = L.gid_base + mxa + myb * L.mcus_x;
-            if (mxb != mxa && myb != mya) g[3] = L.gid_base + mxb + myb * L.mcus_x;
-          }
-        }
+      if (i >= n || t[i] == JT_EMPTY_TEXTURE || (a.only_tex >= 0 && (int)t[i] != a.only_tex)) continue;
+      if (!lc.get(a.tl, t[i], m[i]) || ((lc.L.sampling == kSamplingCoef) != (a.coef_mode != 0))) {
+        missing = true;
+        continue;
       }
-      // Store a flag unless this thread just stored the same gid or the neighbouring lane
-      // (the pixels just left of ours) holds it: consecutive pixels mostly share MCUs.
-#pragma unroll
-      for (int j = 0; j < (FILTER == JT_FILTER_NEAREST ? 1 : 4); ++j) {
-        const uint32_t nb = __shfl_up_sync(0xFFFFFFFFu, g[j], 1);
-        if (g[j] != kNoGid) {
-          if (g[j] != last[j] && !(lane > 0 && nb == g[j])) a.flags[g[j]] = (uint8_t)units;
-          last[j] = g[j];
-        }
+      const Lvl& L = lc.L;
+      const uint8_t units = (uint8_t)L.units;
+      if (FILTER == JT_FILTER_NEAREST) {
+        int xx, yy;
+        nearest_texel(u[i], v[i], L, xx, yy);
+        flag(L.gid_base + (xx >> L.shift) + (yy >> L.shift) * L.mcus_x, units);
+      } else {
+        int xa, xb, ya, yb;
+        float fx, fy;
+        bilinear_taps(u[i], v[i], L, xa, xb, ya, yb, fx, fy);
+        const int mxa = xa >> L.shift, mxb = xb >> L.shift;
+        const int mya = ya >> L.shift, myb = yb >> L.shift;
+        flag(L.gid_base + mxa + mya * L.mcus_x, units);
+        if (mxb != mxa) flag(L.gid_base + mxb + mya * L.mcus_x, units);
+        if (myb != mya) flag(L.gid_base + mxa + myb * L.mcus_x, units);
+        if (mxb != mxa && myb != mya) flag(L.gid_base + mxb + myb * L.mcus_x, units);
       }
     }
-  }
+  });
   if (missing) atomicOr(&a.state->err, JT_DEVERR_MISSING);
 }
 
 // ---------------------------------------------------------------------------------------
 // Colourise
 // ---------------------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t fetch_texel(const ColorizeArgs& a, const LevelInfo& L, int x, int y,
-                                                bool& bad) {
-  const uint32_t gid = L.gid_base + x / L.mw + (y / L.mw) * L.mcus_x;
+__device__ __forceinline__ uint32_t slot_of(const ColorizeArgs& a, uint32_t gid, uint32_t units, bool& bad) {
   const uint32_t off = __ldg(&a.slot[gid]);
-  if (off + L.units > a.cap_units) {
+  if (off + units > a.cap_units) {
     bad = true;
-    return 0xFF000000u;
+    return 0xFFFFFFFFu;
   }
-  const uint32_t* tile = reinterpret_cast<const uint32_t*>(a.cache + (size_t)off * kUnitBytes);
-  return __ldg(tile + (y & (L.mw - 1)) * L.mw + (x & (L.mw - 1)));
+  return off;
 }
 
+__device__ __forceinline__ uint32_t texel(const ColorizeArgs& a, uint32_t off, int x, int y, int shift) {
+  if (off == 0xFFFFFFFFu) return 0xFF000000u;
+  const int mwm = (1 << shift) - 1;
+  const uint32_t* tile = reinterpret_cast<const uint32_t*>(a.cache) + (size_t)off * (kUnitBytes / 4);
+  return __ldg(tile + (((y & mwm) << shift) | (x & mwm)));
+}
+
+// Channel `ch` of an RGBA8 texel as float, exactly: the byte is placed under the exponent
+// of 2^23 (PRMT) and the bias subtracted (full-rate ops instead of an int-to-float
+// conversion).
+__device__ __forceinline__ float chan(uint32_t c, int ch) {
+  return __int_as_float((int)__byte_perm(c, 0x4B00u, 0x5440u | (uint32_t)ch)) - 8388608.0f;
+}
+
+// Bilinear blend in fp32 (lerp along x, then y); each channel rounds half up:
+// floor(c + 1/2), computed as the low byte of (c + 1/2) + 2^23 rounded down.
 __device__ __forceinline__ uint32_t blend(uint32_t c00, uint32_t c10, uint32_t c01, uint32_t c11, float fx,
                                           float fy) {
   uint32_t out = 0xFF000000u;
 #pragma unroll
   for (int ch = 0; ch < 3; ++ch) {
-    const int sh = 8 * ch;
-    float a0 = (float)((c00 >> sh) & 255), a1 = (float)((c10 >> sh) & 255);
-    float b0 = (float)((c01 >> sh) & 255), b1 = (float)((c11 >> sh) & 255);
-    float top = fmaf(fx, a1 - a0, a0);
-    float bot = fmaf(fx, b1 - b0, b0);
-    float c = fmaf(fy, bot - top, top);
-    int iv = __float2int_rd(c + 0.5f);
-    iv = min(255, max(0, iv));
-    out |= (uint32_t)iv << sh;
+    const float a0 = chan(c00, ch), a1 = chan(c10, ch), b0 = chan(c01, ch), b1 = chan(c11, ch);
+    const float top = fmaf(fx, a1 - a0, a0);
+    const float bot = fmaf(fx, b1 - b0, b0);
+    const float c = fmaf(fy, bot - top, top);  // in [0, 255] up to rounding
+    const uint32_t iv = (uint32_t)__float_as_int(__fadd_rd(__fadd_rn(c, 0.5f), 8388608.0f)) & 0x1FFu;
+    out |= min(iv, 255u) << (8 * ch);
   }
   return out;
 }
 
 template <int FILTER>
 __global__ void k_colorize(const __grid_constant__ ColorizeArgs a) {
-  const uint32_t stride = gridDim.x * blockDim.x;
-  const uint32_t total = a.views.total_quads;
+  LevelCache lc;
   bool missing = false, bad = false;
-  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += stride) {
-    const int vi = view_of(a.views, q);
-    const View& V = a.views.v[vi];
-    const uint32_t lq = q - V.quad_begin;
+  uint32_t last_gid = kNoGid, last_off = 0xFFFFFFFFu;  // slot of the last MCU looked up
+  for_each_quad(a.views, [&](const View& V, int y, int x) {
     float u[4], v[4];
     uint32_t t[4], m[4];
-    const int n = load_quad(V, lq, u, v, t, m);
+    const int n = load_px4(V, y, x, u, v, t, m);
+    if (n == 0) return;
     uint32_t px[4];
     bool write[4];
 #pragma unroll
@@ -224,33 +261,62 @@ __global__ void k_colorize(const __grid_constant__ ColorizeArgs a) {
       px[i] = 0xFF000000u;
       write[i] = i < n && (a.only_tex < 0 || (int)t[i] == a.only_tex);
       if (!write[i] || t[i] == JT_EMPTY_TEXTURE) continue;
-      LevelInfo L;
-      if (!lookup_level(a.tl, t[i], m[i], L) || L.sampling == kSamplingCoef) {
+      if (!lc.get(a.tl, t[i], m[i]) || lc.L.sampling == kSamplingCoef) {
         missing = true;
         continue;
       }
+      const Lvl& L = lc.L;
       if (FILTER == JT_FILTER_NEAREST) {
-        int x, y;
-        nearest_texel(u[i], v[i], L, x, y);
-        px[i] = fetch_texel(a, L, x, y, bad);
+        int xx, yy;
+        nearest_texel(u[i], v[i], L, xx, yy);
+        const uint32_t g = L.gid_base + (xx >> L.shift) + (yy >> L.shift) * L.mcus_x;
+        if (g != last_gid) {
+          last_gid = g;
+          last_off = slot_of(a, g, L.units, bad);
+        }
+        px[i] = texel(a, last_off, xx, yy, L.shift);
       } else {
         int xa, xb, ya, yb;
         float fx, fy;
         bilinear_taps(u[i], v[i], L, xa, xb, ya, yb, fx, fy);
-        uint32_t c00 = fetch_texel(a, L, xa, ya, bad), c10 = fetch_texel(a, L, xb, ya, bad);
-        uint32_t c01 = fetch_texel(a, L, xa, yb, bad), c11 = fetch_texel(a, L, xb, yb, bad);
-        px[i] = blend(c00, c10, c01, c11, fx, fy);
+        const int mxa = xa >> L.shift, mxb = xb >> L.shift;
+        const int mya = ya >> L.shift, myb = yb >> L.shift;
+        const uint32_t g00 = L.gid_base + mxa + mya * L.mcus_x;
+        if (g00 != last_gid) {  // consecutive pixels mostly sample the same MCU
+          last_gid = g00;
+          last_off = slot_of(a, g00, L.units, bad);
+        }
+        const uint32_t o00 = last_off;
+        // footprint inside one MCU and not wrapped around a level narrower than an MCU
+        if (mxb == mxa && myb == mya && xb == xa + 1 && yb == ya + 1 && o00 != 0xFFFFFFFFu) {
+          const int mwm = (1 << L.shift) - 1;
+          const uint32_t* tile = reinterpret_cast<const uint32_t*>(a.cache) + (size_t)o00 * (kUnitBytes / 4);
+          const uint32_t* p00 = tile + (((ya & mwm) << L.shift) | (xa & mwm));
+          px[i] = blend(__ldg(p00), __ldg(p00 + 1), __ldg(p00 + (1 << L.shift)), __ldg(p00 + (1 << L.shift) + 1), fx,
+                        fy);
+        } else {
+          uint32_t o10 = o00, o01 = o00, o11 = o00;
+          if (mxb != mxa) o10 = slot_of(a, L.gid_base + mxb + mya * L.mcus_x, L.units, bad);
+          if (myb != mya) o01 = slot_of(a, L.gid_base + mxa + myb * L.mcus_x, L.units, bad);
+          if (mxb != mxa && myb != mya)
+            o11 = slot_of(a, L.gid_base + mxb + myb * L.mcus_x, L.units, bad);
+          else
+            o11 = mxb != mxa ? o10 : o01;
+          px[i] = blend(texel(a, o00, xa, ya, L.shift), texel(a, o10, xb, ya, L.shift),
+                        texel(a, o01, xa, yb, L.shift), texel(a, o11, xb, yb, L.shift), fx, fy);
+        }
       }
     }
-    if (n == 4 && write[0] && write[1] && write[2] && write[3]) {
-      V.out[lq] = make_uint4(px[0], px[1], px[2], px[3]);
+    const uint32_t p0 = (uint32_t)y * (uint32_t)V.width + (uint32_t)x;
+    if (n == 4 && (V.width & 3) == 0 && write[0] && write[1] && write[2] && write[3]) {
+      V.out[p0 >> 2] = make_uint4(px[0], px[1], px[2], px[3]);
     } else {
-      uint32_t* o = reinterpret_cast<uint32_t*>(V.out) + (size_t)lq * 4;
+      uint32_t* o = reinterpret_cast<uint32_t*>(V.out) + p0;
 #pragma unroll
       for (int i = 0; i < 4; ++i)
         if (write[i]) o[i] = px[i];
     }
-  }
+  });
   if (missing) atomicOr(&a.state->err, JT_DEVERR_MISSING);
   if (bad) atomicOr(&a.state->err, JT_DEVERR_CAPACITY);
 }

@@ -130,3 +130,27 @@ def test_flags_cleared_between_frames(jt):
     np.testing.assert_array_equal(ctx.work_list(), o.compact(o.mark(small, 0)))
     np.testing.assert_array_equal(out, o.colorize(small.uv, small.tex_id, small.mip, 0))
     ctx.close()
+
+
+@pytest.mark.parametrize("filt", [0, 1])
+def test_levels_smaller_than_an_mcu_and_odd_sizes(jt, filt):
+    """Random uv (repeat wrap) over tiny and non-power-of-two levels: taps wrap inside
+    a single MCU and across the last partial MCU."""
+    sizes = [(8, 8), (4, 4), (12, 20), (33, 17), (16, 16), (5, 3)]
+    ts = synth.make_texture_set(41, sizes, [70] * 6, [420, 444, 420, 444, 420, 420], full_chain=False)
+    rng = np.random.default_rng(5)
+    H, W = 96, 128
+    uv = rng.uniform(-3.0, 3.0, (H, W, 2)).astype(np.float32)
+    tex = rng.integers(0, len(sizes), (H, W)).astype(np.uint16)
+    tex[rng.random((H, W)) < 0.05] = 0xFFFF
+    gb = synth.GBuffer(W, H, uv, tex, np.zeros((H, W), np.uint8))
+    ctx = _ctx(jt)
+    ctx.upload_set(ts)
+    o = oracle.texset_from(ts)
+    out = frame(ctx, jt.DeviceGBuffer.from_host(gb), filt, torch).cpu().numpy()
+    ctx.stats()
+    np.testing.assert_array_equal(ctx.work_list(), o.compact(o.mark(gb, filt)))
+    ref = o.colorize(gb.uv, gb.tex_id, gb.mip, filt)
+    d = np.abs(out.astype(np.int32) - ref.astype(np.int32))
+    assert d.max() <= (0 if filt == 0 else 1)
+    ctx.close()
