@@ -9,14 +9,18 @@
 //    never goes to the host. Small M gives many warps for frames with few needed MCUs
 //    (latency hiding); large M amortises per-warp overhead for full decodes;
 //  * entropy phase: lane m < M runs MCU m's serial entropy chain over all its data units —
-//    a 64-bit bit buffer refilled by aligned 32-bit loads, one 10-bit first-level LUT
-//    lookup per symbol in shared memory (codes longer than 10 bits take a short MAXCODE
-//    walk), the value bits extracted together with the code — and writes dequantised
-//    coefficients into a per-warp buffer coef[du][natural k][m] (int16);
-//  * IDCT phase: all 32 lanes share the 8x8 integer IDCTs of the warp's 6M data units,
-//    one column (then one row) of one data unit per lane and step, with even/odd
-//    butterflies (an exact integer factorisation of the matrix product of the decode
-//    spec); rows of pixels go to a per-MCU shared buffer;
+//    a 64-bit bit buffer refilled from a two-word prefetch queue of aligned 32-bit loads,
+//    one 10-bit first-level LUT lookup per symbol in shared memory whose entry usually
+//    carries the decoded value (codes longer than 10 bits take a short MAXCODE walk) —
+//    and writes the quantised coefficients in zig-zag order into a per-warp buffer
+//    coef[du][k][m] (int16). Nothing but the LUT and the stream is read on this serial
+//    chain: dequantisation waits for the IDCT phase;
+//  * IDCT phase: all 32 lanes share the 8x8 integer IDCTs of the warp's 6M data units; for
+//    each column index u (then row index y) in turn, every lane transforms that column of
+//    one or more data units, so all zig-zag positions are compile-time constants. Columns
+//    are dequantised on load with the MCU's quantisation table (staged per warp in shared
+//    memory); even/odd butterflies give an exact integer factorisation of the matrix
+//    product of the decode spec; rows of pixels go to a per-MCU shared buffer;
 //  * colour phase: the warp writes each MCU's RGBA8 tile cooperatively (32 lanes x 32 B =
 //    one 1 KiB 4:2:0 tile per step, coalesced).
 //
@@ -66,118 +70,162 @@ __device__ __forceinline__ void idct8(const int in[8], int out[8]) {
 __device__ __forceinline__ int sat16(int v) { return min(32767, max(-32768, v)); }
 __device__ __forceinline__ uint32_t clamp255(int v) { return (uint32_t)min(255, max(0, v)); }
 
+// Words of an MCU's entropy-coded data copied to shared memory before its serial decode.
+// Random loads from HBM take thousands of cycles and would otherwise sit on the serial
+// chain once per refill; staging issues them all at once (one latency per work chunk).
+constexpr int kStageWords = 64;  // 256 B per MCU; longer MCUs read their tail from global memory
+
 constexpr int kPixStride = 97;  // words per MCU: Y 64 + Cb 16 + Cr 16, +1 pad
 
-// Shared memory of one warp: coefficients [6][64][M] int16 (natural order), pixels
-// [M][97] words, per-MCU cache offset and descriptor bits.
-__host__ __device__ constexpr size_t warp_smem(int M) { return (size_t)6 * 64 * M * 2 + (size_t)M * kPixStride * 4 + (size_t)M * 8; }
+// Shared memory of one warp: coefficients [6][64][M] int16 (zig-zag order), pixels
+// [M][97] words, quantisation tables [M][2][64] uint16 (zig-zag order), per-MCU cache
+// offset and descriptor bits, staged entropy-coded words [M][kStageWords].
+__host__ __device__ constexpr size_t warp_smem(int M) {
+  return (size_t)6 * 64 * M * 2 + (size_t)M * kPixStride * 4 + (size_t)M * 256 + (size_t)M * 8 +
+         (size_t)M * kStageWords * 4;
+}
 
+__device__ __forceinline__ uint32_t lds_u32(uint32_t saddr) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(saddr));
+  return v;
+}
+
+// Bit reader: a 64-bit window (hi:lo, big-endian words) read at bit `pos` of hi with one
+// funnel shift, and a queue of the next three raw words. Words come from the lane's staged
+// copy in shared memory (words [base, base + nstage)), else from global memory.
 struct BitReader {
-  uint64_t buf;  // valid bits MSB-aligned
-  int cnt;
-  uint32_t wp;   // next word to load
+  uint32_t hi, lo;
+  uint32_t pos;         // bit offset into hi, < 32 after refill()
+  uint32_t q0, q1, q2;  // raw (as loaded) next words
+  uint32_t wp;          // next word to request
   const uint32_t* words;
   uint32_t nwords;
+  uint32_t base, nstage, stage_sa;
 
-  __device__ __forceinline__ void load_word() {
-    const uint32_t w = wp < nwords ? __ldg(words + wp) : 0u;
+  __device__ __forceinline__ uint32_t fetch() {
+    const uint32_t i = wp - base;
+    uint32_t w;
+    if (i < nstage)
+      w = lds_u32(stage_sa + i * 4u);
+    else
+      w = wp < nwords ? __ldg(words + wp) : 0u;
     ++wp;
-    buf |= (uint64_t)__byte_perm(w, 0, 0x0123) << (32 - cnt);
-    cnt += 32;
+    return w;
   }
+  __device__ __forceinline__ static uint32_t be(uint32_t w) { return __byte_perm(w, 0, 0x0123); }
   __device__ __forceinline__ void init(uint32_t bitpos) {
     wp = bitpos >> 5;
-    buf = 0;
-    cnt = 0;
-    load_word();
-    load_word();
-    const int skip = bitpos & 31;
-    buf <<= skip;
-    cnt -= skip;
+    hi = be(fetch());
+    lo = be(fetch());
+    q0 = fetch();
+    q1 = fetch();
+    q2 = fetch();
+    pos = bitpos & 31;
   }
-  // afterwards at least 32 bits are buffered (a symbol needs at most 16 + 11)
+  // afterwards the window holds at least 33 unread bits (a symbol needs at most 16 + 11)
   __device__ __forceinline__ void refill() {
-    if (cnt <= 32) load_word();
+    if (pos >= 32) {
+      hi = lo;
+      lo = be(q0);
+      q0 = q1;
+      q1 = q2;
+      q2 = fetch();
+      pos -= 32;
+    }
   }
-  __device__ __forceinline__ uint64_t position() const { return (uint64_t)wp * 32 - (uint64_t)cnt; }
+  // the next 32 bits
+  __device__ __forceinline__ uint32_t peek() const { return __funnelshift_l(lo, hi, pos); }
+  // bit position of the next unread bit in the stream
+  __device__ __forceinline__ uint64_t position() const { return (uint64_t)(wp - 5) * 32 + pos; }
 };
 
-constexpr uint32_t kBadEntry = 0xFFFFFFFFu;
-
-// Entry for a code longer than kLutBits (MAXCODE walk over lengths kLutBits+1..16), in the
-// LUT's format; kBadEntry when no code matches or the symbol is invalid for the class.
-__device__ __noinline__ uint32_t long_code_entry(const HuffTable* t, uint32_t top, bool dc) {
+// Slow path of a symbol (slow LUT entry): a code longer than kLutBits (found by the
+// MAXCODE walk) or value bits beyond the LUT window. Cuts code and value bits from the
+// 32-bit window w (at most 16 + 11 bits) and returns the equivalent fast entry, or
+// kLutSlow for a code that matches nothing or a symbol invalid for the table's class.
+__device__ __noinline__ uint32_t slow_symbol(const HuffTable* t, uint32_t w, uint32_t e, bool dc) {
+  uint32_t L = e & 31, sym = (e >> 20) & 255;
+  if (L == 0) {
+    const uint32_t top = w >> 16;
 #pragma unroll 1
-  for (int l = kLutBits + 1; l <= 16; ++l) {
-    const int code = (int)(top >> (16 - l));
-    if (code <= t->maxcode[l]) {
-      const int vi = code + t->valoff[l];
-      if (vi < 0 || vi > 255) return kBadEntry;
-      const uint32_t sym = t->vals[vi];
-      const uint32_t r = dc ? 0 : sym >> 4, s = dc ? sym : sym & 15;
-      if (s > (dc ? 11u : 10u)) return kBadEntry;
-      if (s == 0) {
-        if (dc) return lut_entry(l, 0, 0, kLutKindValue, 0);
-        return (r == 0 || r == 15) ? lut_entry(l, r, 0, kLutKindEnd, 0) : kBadEntry;
+    for (int l = kLutBits + 1; l <= 16; ++l) {
+      const int code = (int)(top >> (16 - l));
+      if (code <= t->maxcode[l]) {
+        const int vi = code + t->valoff[l];
+        if (vi < 0 || vi > 255) return kLutSlow;
+        sym = t->vals[vi];
+        L = (uint32_t)l;
+        break;
       }
-      return lut_entry(l, r, s, kLutKindBits, 0);
     }
+    if (L == 0) return kLutSlow;
   }
-  return kBadEntry;
+  const uint32_t r = dc ? 0 : sym >> 4, s = dc ? sym : sym & 15;
+  if (s > (dc ? 11u : 10u)) return kLutSlow;
+  if (!dc && s == 0) {
+    if (r == 0) return lut_fast(L, 64, 63, false, 0);   // end of block
+    if (r == 15) return lut_fast(L, 16, 15, false, 0);  // zero run of 16
+    return kLutSlow;
+  }
+  const uint32_t bits = s ? (w << L) >> (32 - s) : 0u;
+  const int v = s ? ((int)bits - ((bits < (1u << (s - 1))) ? (int)((1u << s) - 1u) : 0)) : 0;
+  return dc ? lut_fast(L + s, 1, 0, false, v) : lut_fast(L + s, r + 1, r, true, v);
 }
 
-// Decodes the next symbol's entry and consumes its code (and, for kind 1, its value bits);
-// for kind 2 the value bits are read here too. Returns false on an invalid code.
-__device__ __forceinline__ bool next_symbol(BitReader& br, const HuffTable* t, bool dc, uint32_t& e, int& v) {
-  br.refill();
-  const uint32_t top = (uint32_t)(br.buf >> 48);
-  e = t->lut[top >> (16 - kLutBits)];
-  if (e == 0) {
-    e = long_code_entry(t, top, dc);
-    if (e == kBadEntry) return false;
-  }
-  const uint32_t nb = e & 31;
-  br.buf <<= nb;
-  br.cnt -= (int)nb;
-  v = (int)e >> 16;
-  if (((e >> 13) & 3) == kLutKindBits) {
-    const uint32_t s = (e >> 9) & 15;
-    const uint32_t bits = (uint32_t)(br.buf >> (64 - s));
-    br.buf <<= s;
-    br.cnt -= (int)s;
-    v = (int)bits - ((bits < (1u << (s - 1))) ? (int)((1u << s) - 1u) : 0);
-  }
-  return true;
-}
-
-// Decodes one data unit into col[nat[k] * M] (dequantised, saturated to int16; col must
-// be zero on entry). Returns false on an invalid coding.
+// Entropy-decodes all data units of one MCU into coef[(du * 64 + k) * M] (quantised, zig-zag
+// k; the buffer must be zero on entry). One symbol per loop iteration. The common symbol —
+// an AC value, end of block, zero run or DC difference whose code and value bits fit the
+// 10-bit window — is one LUT read and a fixed straight sequence: consume, (DC: add the
+// component's predictor), store at k + offset, advance k. hs: the lane's table set; hs_sa:
+// its shared-memory address when it is the staged set, else 0 (generic reads).
+// Returns false on an invalid coding.
 template <int M>
-__device__ __forceinline__ bool decode_du(BitReader& br, const HuffTable* dct, const HuffTable* act,
-                                          const uint16_t* __restrict__ qz, const uint8_t* nat, int16_t& pred,
-                                          int16_t* col) {
-  uint32_t e;
-  int v;
-  if (!next_symbol(br, dct, true, e, v)) return false;  // DC difference
-  pred = (int16_t)(uint16_t)((int)pred + v);
-  col[0] = (int16_t)sat16((int)pred * (int)__ldg(qz));
-  int k = 1;
+__device__ __forceinline__ bool decode_mcu(BitReader& br, const HuffTable* hs, uint32_t hs_sa, int ndu, int16_t& p0,
+                                           int16_t& p1, int16_t& p2, int16_t* coef) {
+  int du = 0, k = 0, comp = 0;
+  int pc = p0;  // DC predictor of the current data unit's component
+  uint32_t dct = 0;  // table index of the component's DC table (0 luma, 2 chroma)
+  bool bad = false;
+  int16_t* blk = coef;
 #pragma unroll 1
-  while (k < 64) {  // AC: at most 63 symbols
-    if (!next_symbol(br, act, false, e, v)) return false;
-    const int r = (int)((e >> 5) & 15);
-    if (((e >> 13) & 3) == kLutKindEnd) {
-      if (r != 15) break;  // end of block
-      k += 16;             // zero run of 16
-      if (k > 63) return false;
-      continue;
+  for (int it = 0; it < 64 * 6; ++it) {  // at most 64 symbols per data unit
+    br.refill();
+    const uint32_t w = br.peek();
+    const bool dc = k == 0;
+    const uint32_t ti = dct + (dc ? 0u : 1u);
+    const uint32_t li = w >> (32 - kLutBits);
+    uint32_t e = hs_sa ? lds_u32(hs_sa + ti * (uint32_t)sizeof(HuffTable) + li * 4u) : hs[ti].lut[li];
+    if (e & kLutSlow) {
+      e = slow_symbol(hs + ti, w, e, dc);
+      if (e & kLutSlow) return false;
     }
-    k += r;
-    if (k > 63) return false;
-    col[nat[k] * M] = (int16_t)sat16(v * (int)__ldg(qz + k));
-    ++k;
+    const uint32_t nb = e & 31, adv = (e >> 5) & 127, sofs = (e >> 12) & 63;
+    const bool chk = (e >> 18) & 1;
+    int v = (int)e >> 20;
+    br.pos += nb;
+    if (dc) {
+      pc = (int16_t)(uint16_t)(pc + v);  // DC values wrap modulo 2^16
+      v = pc;
+    }
+    const int kst = k + (int)sofs;
+    bad |= chk && kst > 63;
+    blk[min(kst, 63) * M] = (int16_t)v;
+    k += (int)adv;
+    if (k >= 64) {  // data unit done
+      if (bad) return false;
+      if (comp == 0) p0 = (int16_t)pc;
+      if (comp == 1) p1 = (int16_t)pc;
+      if (comp == 2) p2 = (int16_t)pc;
+      if (++du == ndu) return true;
+      comp = du < ndu - 2 ? 0 : (du == ndu - 2 ? 1 : 2);
+      pc = comp == 0 ? p0 : (comp == 1 ? p1 : p2);
+      dct = comp == 0 ? 0u : 2u;
+      blk += 64 * M;
+      k = 0;
+    }
   }
-  return true;
+  return false;
 }
 
 __device__ __forceinline__ uint32_t ycc_pixel(uint32_t Y, int ro, int go, int bo) {
@@ -214,22 +262,19 @@ template <int M>
 __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   HuffSet* sh = reinterpret_cast<HuffSet*>(smem);
-  uint8_t* nat = smem + sizeof(HuffSet);  // natural index of zig-zag position k
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint8_t* wbase = smem + sizeof(HuffSet) + 64 + (size_t)warp * warp_smem(M);
   int16_t* coef = reinterpret_cast<int16_t*>(wbase);                       // [6][64][M]
   uint32_t* pix = reinterpret_cast<uint32_t*>(wbase + 6 * 64 * M * 2);     // [M][97]
-  uint32_t* moff = pix + M * kPixStride;                                   // [M] cache unit offset
-  uint32_t* minfo = moff + M;                                              // [M] ndu | 420 << 4 | store << 5
+  uint16_t* qtab = reinterpret_cast<uint16_t*>(pix + M * kPixStride);      // [M][2][64] zig-zag
+  uint32_t* moff = reinterpret_cast<uint32_t*>(qtab + M * 128);            // [M] cache unit offset
+  uint32_t* minfo = moff + M;  // [M] ndu | 420 << 4 | store << 5 | qset << 8
+  uint32_t* stage = minfo + M;  // [M][kStageWords] entropy-coded words
 
-  {  // stage Huffman set 0 and the zig-zag table
+  {  // stage Huffman set 0
     const uint4* src = reinterpret_cast<const uint4*>(a.huff);
     uint4* dst = reinterpret_cast<uint4*>(sh);
     for (int i = threadIdx.x; i < (int)(sizeof(HuffSet) / 16); i += blockDim.x) dst[i] = __ldg(src + i);
-    if (threadIdx.x < 64) {
-      const int r = threadIdx.x >> 3, c = threadIdx.x & 7;
-      nat[zz_pos(r, c)] = (uint8_t)threadIdx.x;
-    }
   }
   __syncthreads();
 
@@ -252,11 +297,10 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
     d0 = __shfl_sync(0xFFFFFFFFu, d0, 0);
     int ndu = 0;
     bool s420 = true, store = false, bad = false;
-    uint32_t off = 0, nbits = 0;
+    uint32_t off = 0, nbits = 0, qset = 0;
     BitReader br;
     int16_t pr0 = 0, pr1 = 0, pr2 = 0;
     const HuffTable* hs = sh->t;
-    const uint16_t* qz = a.quant;
     if (act) {
       int di = d0;
       const uint32_t b0 = __ldg(&a.descs[d0].gid_base);
@@ -278,14 +322,35 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
         br.words = d.stream;
         br.nwords = d.nwords;
         nbits = d.nbits;
+        // stage the MCU's words (from its first word, 16 B aligned, to the next MCU's start
+        // plus the reader's look-ahead) with independent vector loads
+        const uint32_t endbit = mcu + 1 < d.nmcu ? ((uint32_t)__ldg(ix + 5) | ((uint32_t)__ldg(ix + 6) << 16)) : d.nbits;
+        const uint32_t w0 = (bitpos >> 5) & ~3u;
+        uint32_t want = (max(endbit, bitpos) >> 5) + 6 - w0;
+        want = min((want + 3) & ~3u, (uint32_t)kStageWords);
+        if (w0 + want > d.nwords) want = d.nwords > w0 ? (d.nwords - w0) & ~3u : 0u;
+        br.base = w0;
+        br.nstage = want;
+        br.stage_sa = (uint32_t)__cvta_generic_to_shared(stage + lane * kStageWords);
+        const uint4* src4 = reinterpret_cast<const uint4*>(d.stream + w0);
+        uint4* dst4 = reinterpret_cast<uint4*>(stage + lane * kStageWords);
+#pragma unroll 1
+        for (uint32_t j = 0; j < want / 4; j += 4) {
+          uint4 r[4];
+#pragma unroll
+          for (int t = 0; t < 4; ++t) r[t] = j + t < want / 4 ? __ldg(src4 + j + t) : make_uint4(0, 0, 0, 0);
+#pragma unroll
+          for (int t = 0; t < 4; ++t)
+            if (j + t < want / 4) dst4[j + t] = r[t];
+        }
         br.init(bitpos);
         if (d.hset != 0) hs = a.huff[d.hset].t;
-        qz = a.quant + (size_t)d.qset * 128;
+        qset = d.qset;
       }
     }
     if (lane < M) {
       moff[lane] = off;
-      minfo[lane] = act ? ((uint32_t)ndu | (s420 ? 16u : 0u) | (store ? 32u : 0u)) : 0u;
+      minfo[lane] = act ? ((uint32_t)ndu | (s420 ? 16u : 0u) | (store ? 32u : 0u) | (qset << 8)) : 0u;
     }
     {  // clear the coefficient buffer (768 M bytes)
       uint4* z = reinterpret_cast<uint4*>(coef);
@@ -293,67 +358,74 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
       for (int i = lane; i < 48 * M; i += 32) z[i] = make_uint4(0, 0, 0, 0);
     }
     __syncwarp();
+    {  // stage each MCU's quantisation tables (256 B = 16 x 16 B per MCU)
+      const uint4* qsrc = reinterpret_cast<const uint4*>(a.quant);
+      uint4* qdst = reinterpret_cast<uint4*>(qtab);
+#pragma unroll
+      for (int i = lane; i < 16 * M; i += 32) qdst[i] = __ldg(qsrc + (size_t)(minfo[i >> 4] >> 8) * 16 + (i & 15));
+    }
 
     // ---- entropy phase: each active lane decodes all data units of its MCU ----
     if (act) {
-#pragma unroll 1
-      for (int du = 0; du < ndu && !bad; ++du) {
-        const int comp = du < ndu - 2 ? 0 : (du == ndu - 2 ? 1 : 2);
-        const int tb = comp == 0 ? 0 : 2;
-        int16_t pred = comp == 0 ? pr0 : (comp == 1 ? pr1 : pr2);
-        if (!decode_du<M>(br, hs + tb, hs + tb + 1, qz + (comp == 0 ? 0 : 64), nat, pred,
-                          coef + (size_t)du * 64 * M + lane))
-          bad = true;
-        if (comp == 0)
-          pr0 = pred;
-        else if (comp == 1)
-          pr1 = pred;
-        else
-          pr2 = pred;
-      }
+      const uint32_t hs_sa = hs == sh->t ? (uint32_t)__cvta_generic_to_shared(sh->t) : 0u;
+      if (!decode_mcu<M>(br, hs, hs_sa, ndu, pr0, pr1, pr2, coef + lane)) bad = true;
       if (!bad && br.position() > nbits) bad = true;
       any_bad |= bad;
     }
     __syncwarp();
 
-    // ---- IDCT column pass: 48M columns (6 data units x 8 columns per MCU) ----
+    // ---- IDCT column pass: for each column u, the 6M data units spread over the lanes.
+    // Dequantise on load: d = clamp16(q * Q[k]); t = clamp16(floor((sum + 2^8) / 2^9)),
+    // written back in place (column u of t occupies the zig-zag slots of column u).
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
 #pragma unroll 1
-    for (int c = lane; c < 48 * M; c += 32) {
-      const int du_idx = c >> 3, u = c & 7;
-      const int d = du_idx / M, m = du_idx % M;
-      if (d >= (int)(minfo[m] & 7)) continue;
-      int16_t* col = coef + ((size_t)d * 64 + u) * M + m;
-      int in[8], out[8];
+      for (int j = lane; j < 6 * M; j += 32) {
+        const int d = j / M, m = j % M;
+        const uint32_t info = minfo[m];
+        if (d >= (int)(info & 7)) continue;
+        int16_t* blk = coef + (size_t)d * 64 * M + m;
+        const uint16_t* Q = qtab + m * 128 + (d < (int)(info & 7) - 2 ? 0 : 64);
+        int in[8], out[8];
+        int any = 0;
 #pragma unroll
-      for (int v = 0; v < 8; ++v) in[v] = col[v * 8 * M];
-      if ((in[0] | in[1] | in[2] | in[3] | in[4] | in[5] | in[6] | in[7]) == 0) continue;  // stays zero
-      idct8(in, out);
+        for (int v = 0; v < 8; ++v) {
+          const int k = zz_pos(v, u);
+          const int q = blk[k * M];
+          any |= q;
+          in[v] = sat16(q * (int)Q[k]);
+        }
+        if (any == 0) continue;  // an all-zero column stays zero
+        idct8(in, out);
 #pragma unroll
-      for (int y = 0; y < 8; ++y) col[y * 8 * M] = (int16_t)sat16((out[y] + 256) >> 9);
+        for (int y = 0; y < 8; ++y) blk[zz_pos(y, u) * M] = (int16_t)sat16((out[y] + 256) >> 9);
+      }
     }
     __syncwarp();
 
-    // ---- IDCT row pass: 48M rows -> pixels ----
+    // ---- IDCT row pass: for each row y, the 6M data units spread over the lanes -> pixels
+#pragma unroll
+    for (int y = 0; y < 8; ++y) {
 #pragma unroll 1
-    for (int r = lane; r < 48 * M; r += 32) {
-      const int du_idx = r >> 3, y = r & 7;
-      const int d = du_idx / M, m = du_idx % M;
-      const uint32_t info = minfo[m];
-      if (d >= (int)(info & 7)) continue;
-      const int16_t* row = coef + ((size_t)d * 64 + y * 8) * M + m;
-      int in[8], out[8];
+      for (int j = lane; j < 6 * M; j += 32) {
+        const int d = j / M, m = j % M;
+        const uint32_t info = minfo[m];
+        if (d >= (int)(info & 7)) continue;
+        const int16_t* blk = coef + (size_t)d * 64 * M + m;
+        int in[8], out[8];
 #pragma unroll
-      for (int x = 0; x < 8; ++x) in[x] = row[x * M];
-      idct8(in, out);
-      uint32_t w0 = 0, w1 = 0;
+        for (int x = 0; x < 8; ++x) in[x] = blk[zz_pos(y, x) * M];
+        idct8(in, out);
+        uint32_t w0 = 0, w1 = 0;
 #pragma unroll
-      for (int x = 0; x < 4; ++x) {
-        w0 |= clamp255(((out[x] + (1 << 18)) >> 19) + 128) << (8 * x);
-        w1 |= clamp255(((out[x + 4] + (1 << 18)) >> 19) + 128) << (8 * x);
+        for (int x = 0; x < 4; ++x) {
+          w0 |= clamp255(((out[x] + (1 << 18)) >> 19) + 128) << (8 * x);
+          w1 |= clamp255(((out[x + 4] + (1 << 18)) >> 19) + 128) << (8 * x);
+        }
+        uint32_t* dst = pix + m * kPixStride + pix_row(d, y, (info & 16) != 0);
+        dst[0] = w0;
+        dst[1] = w1;
       }
-      uint32_t* dst = pix + m * kPixStride + pix_row(d, y, (info & 16) != 0);
-      dst[0] = w0;
-      dst[1] = w1;
     }
     __syncwarp();
 

@@ -153,17 +153,15 @@ int extend_value(uint32_t bits, int s) {  // T.81 EXTEND
 }
 
 // First-level LUT entry for symbol `sym` with a code of length l, followed in the peeked
-// window by the bits `tail` (kLutBits - l bits). 0 = not decodable from the LUT.
+// window by the bits `tail` (kLutBits - l bits).
 uint32_t fused_entry(bool dc, int l, uint8_t sym, uint32_t tail) {
   const int r = dc ? 0 : sym >> 4, s = dc ? sym : sym & 15;
-  if (dc && s > 11) return 0;
-  if (!dc && s > 10) return 0;
-  if (!dc && s == 0) return (r == 0 || r == 15) ? lut_entry(l, r, 0, kLutKindEnd, 0) : 0;
-  if (l + s <= kLutBits) {
-    const uint32_t bits = (tail >> (kLutBits - l - s)) & ((1u << s) - 1u);
-    return lut_entry(l + s, r, 0, kLutKindValue, extend_value(bits, s));
-  }
-  return lut_entry(l, r, s, kLutKindBits, 0);
+  if ((dc && s > 11) || (!dc && s > 10) || (!dc && s == 0 && r != 0 && r != 15)) return lut_slow(l, sym);
+  if (!dc && s == 0) return r == 0 ? lut_fast(l, 64, 63, false, 0) : lut_fast(l, 16, 15, false, 0);
+  if (l + s > kLutBits) return lut_slow(l, sym);
+  const uint32_t bits = s ? (tail >> (kLutBits - l - s)) & ((1u << s) - 1u) : 0u;
+  const int v = extend_value(bits, s);
+  return dc ? lut_fast(l + s, 1, 0, false, v) : lut_fast(l + s, r + 1, r, true, v);
 }
 
 // Canonical decode tables of one Huffman spec (T.81 Annex C code assignment).
@@ -184,6 +182,7 @@ bool build_table(const jt_huff_spec& spec, bool dc, HuffTable& t, std::string& w
     return false;
   }
   std::memcpy(t.vals, spec.vals, n);
+  for (int i = 0; i < kLutSize; ++i) t.lut[i] = lut_slow(0, 0);  // longer codes: MAXCODE walk
   int code = 0, k = 0;
   for (int l = 1; l <= 16; ++l) {
     const int nl = spec.bits[l - 1];

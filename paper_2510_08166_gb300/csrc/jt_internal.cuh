@@ -17,7 +17,7 @@
 
 #include <cstdint>
 
-#include "../../include/jt.h"
+#include "jt.h"
 
 namespace jt {
 
@@ -28,20 +28,27 @@ constexpr uint32_t kUnitBytes = 256;         // cache unit
 constexpr int kSampling420 = 0, kSampling444 = 1, kSamplingCoef = 2;
 
 // Decode tables of one Huffman spec. lut[i] describes the symbol whose code starts the
-// next kLutBits bits i (0 when that code is longer than kLutBits, or its symbol is not
-// valid for the table's class; such codes take the MAXCODE walk, which also rejects
-// invalid symbols):
-//   bits  0..4   bits to consume now: code length + value bits (kind 1) or code length
-//   bits  5..8   run (AC zero run; 15 with kind 3 is ZRL)
-//   bits  9..12  size (value bits still to read, kind 2)
-//   bits 13..14  kind: 1 value decoded in the entry, 2 value bits follow, 3 EOB / ZRL
-//   bits 16..31  the decoded (sign-extended) value for kind 1
-// Longer codes use maxcode[l] / valoff[l] (index of the symbol = code + valoff[l]).
-constexpr uint32_t kLutKindValue = 1, kLutKindBits = 2, kLutKindEnd = 3;
-__host__ __device__ constexpr uint32_t lut_entry(uint32_t nbits, uint32_t run, uint32_t size, uint32_t kind,
-                                                 int value) {
-  return nbits | (run << 5) | (size << 9) | (kind << 13) | ((uint32_t)(value & 0xFFFF) << 16);
+// next kLutBits bits i. Fast entries (code + value bits fit the window):
+//   bits  0..4   bits to consume (code length + value bits)
+//   bits  5..11  coefficient index advance: run + 1 (value), 16 (ZRL), 64 (end of block),
+//                1 (DC difference)
+//   bits 12..17  store offset from the current index: run (value), 15 (ZRL), 63 (end of
+//                block, clamped to the last slot), 0 (DC); ZRL and EOB store a zero into a
+//                slot that must be zero anyway
+//   bit  18      value symbol: the store position must not pass 63
+//   bits 20..31  the decoded (sign-extended) value (0 for ZRL / end of block)
+// Slow entries (bit 19 set) hold the code length in bits 0..4 (0: longer than kLutBits) and
+// the symbol in bits 20..27; value bits follow in the stream (or the code is long), and
+// symbols invalid for the table's class are rejected on the slow path.
+constexpr uint32_t kLutSlow = 1u << 19;
+__host__ __device__ constexpr uint32_t lut_fast(uint32_t nbits, uint32_t adv, uint32_t sofs, bool chk, int value) {
+  return nbits | (adv << 5) | (sofs << 12) | ((chk ? 1u : 0u) << 18) | ((uint32_t)(value & 0xFFF) << 20);
 }
+__host__ __device__ constexpr uint32_t lut_slow(uint32_t codelen, uint32_t sym) {
+  return codelen | kLutSlow | (sym << 20);
+}
+static_assert(((lut_fast(31, 64, 63, true, -2048) >> 5) & 127) == 64, "advance field holds 64");
+static_assert(((int)lut_fast(31, 64, 63, true, -2048) >> 20) == -2048, "value field is signed 12 bits");
 struct HuffTable {
   uint32_t lut[kLutSize];
   int32_t maxcode[17];  // -1 when no code of length l

@@ -38,37 +38,60 @@ struct Lvl {
   float wf, hf;
 };
 
-// Cached (texture, level) lookup; returns false when the level does not exist.
-struct LevelCache {
-  uint32_t key = 0xFFFFFFFFu;
-  bool ok = false;
+constexpr uint32_t kNoKey = 0xFFFFFFFFu;
+
+// Key of a pixel's (texture, level) record, or kNoKey for pixels that are absent, empty,
+// filtered out (only_tex) or name a texture id / level beyond the table.
+__device__ __forceinline__ uint32_t level_key(const TexLookup& tl, bool present, uint32_t tex, uint32_t mip,
+                                              int only_tex) {
+  if (!present || tex == JT_EMPTY_TEXTURE || (only_tex >= 0 && (int)tex != only_tex)) return kNoKey;
+  if (tex >= tl.map_ntex || mip >= JT_MAX_LEVELS) return kNoKey - 1;  // missing
+  return tex * JT_MAX_LEVELS + mip;
+}
+
+// Level record for a key (w == 0 when the key is absent or the level was never uploaded).
+__device__ __forceinline__ Lvl load_level(const TexLookup& tl, uint32_t key) {
   Lvl L;
-  __device__ __forceinline__ bool get(const TexLookup& tl, uint32_t tex, uint32_t mip) {
-    const uint32_t k = (tex << 4) | mip;
-    if (k != key) {
-      key = k;
-      ok = false;
-      if (tex < tl.map_ntex && mip < JT_MAX_LEVELS) {
-        const uint4 r = __ldg(tl.levels + (tex * JT_MAX_LEVELS + mip));
-        L.w = (int)(r.y & 0xFFFF);
-        if (L.w != 0) {
-          ok = true;
-          L.gid_base = r.x;
-          L.h = (int)(r.y >> 16);
-          L.mcus_x = (int)(r.z & 0xFFFF);
-          L.shift = (int)((r.z >> 16) & 15);
-          L.units = (r.z >> 20) & 15;
-          L.sampling = (r.z >> 24) & 15;
-          L.wp2 = (r.z >> 28) & 1;
-          L.hp2 = (r.z >> 29) & 1;
-          L.wf = (float)L.w;
-          L.hf = (float)L.h;
-        }
-      }
-    }
-    return ok;
-  }
+  const uint4 r = key < kNoKey - 1 ? __ldg(tl.levels + key) : make_uint4(0, 0, 0, 0);
+  L.gid_base = r.x;
+  L.w = (int)(r.y & 0xFFFF);
+  L.h = (int)(r.y >> 16);
+  L.mcus_x = (int)(r.z & 0xFFFF);
+  L.shift = (int)((r.z >> 16) & 15);
+  L.units = (r.z >> 20) & 15;
+  L.sampling = (r.z >> 24) & 15;
+  L.wp2 = (r.z >> 28) & 1;
+  L.hp2 = (r.z >> 29) & 1;
+  L.wf = (float)L.w;
+  L.hf = (float)L.h;
+  return L;
+}
+
+// Keys of a quad's pixels and whether the whole warp's row segment shares one level
+// (then that level is loaded once for the warp; otherwise per pixel).
+struct QuadLevels {
+  uint32_t key[4];
+  bool uniform;
+  Lvl shared;
 };
+
+__device__ __forceinline__ void quad_levels(const TexLookup& tl, int n, const uint32_t t[4], const uint32_t m[4],
+                                            int only_tex, QuadLevels& q) {
+  uint32_t k0 = kNoKey;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    q.key[i] = level_key(tl, i < n, t[i], m[i], only_tex);
+    if (k0 == kNoKey) k0 = q.key[i];
+  }
+  bool same = true;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) same &= q.key[i] == kNoKey || q.key[i] == k0;
+  // the first lane with a pixel names the candidate
+  const uint32_t have = __ballot_sync(0xFFFFFFFFu, k0 != kNoKey);
+  const uint32_t kw = have ? __shfl_sync(0xFFFFFFFFu, k0, __ffs(have) - 1) : kNoKey;
+  q.uniform = __all_sync(0xFFFFFFFFu, same && (k0 == kNoKey || k0 == kw)) && kw < kNoKey - 1;
+  if (q.uniform) q.shared = load_level(tl, kw);
+}
 
 __device__ __forceinline__ int wrap(int a, int w, bool pow2) { return pow2 ? (a & (w - 1)) : floor_mod_i(a, w); }
 
@@ -159,43 +182,48 @@ __global__ void k_mark(const __grid_constant__ MarkArgs a) {
   __shared__ uint32_t seen[kSeen];
   for (int i = threadIdx.x; i < kSeen; i += blockDim.x) seen[i] = kNoGid;
   __syncthreads();
-  LevelCache lc;
   bool missing = false;
-  auto flag = [&](uint32_t g, uint8_t units) {
-    uint32_t& e = seen[(g ^ (g >> 10)) & (kSeen - 1)];
-    if (e != g) {  // racy by design: a duplicate store writes the same byte
-      e = g;
+  // flags gid g unless this CTA already did (racy by design: a duplicate store writes the
+  // same byte)
+  auto flag = [&](bool on, uint32_t g, uint8_t units) {
+    uint32_t* e = &seen[(g ^ (g >> 10)) & (kSeen - 1)];
+    if (on && *e != g) {
+      *e = g;
       a.flags[g] = units;
+    }
+  };
+  auto pixel = [&](const Lvl& L, uint32_t key, float u, float v) {
+    const bool ok = key < kNoKey - 1 && L.w != 0 && ((L.sampling == kSamplingCoef) == (a.coef_mode != 0));
+    missing |= key != kNoKey && !ok;
+    const uint8_t units = (uint8_t)L.units;
+    if (FILTER == JT_FILTER_NEAREST) {
+      int x, y;
+      nearest_texel(u, v, L, x, y);
+      flag(ok, L.gid_base + (x >> L.shift) + (y >> L.shift) * L.mcus_x, units);
+    } else {
+      int xa, xb, ya, yb;
+      float fx, fy;
+      bilinear_taps(u, v, L, xa, xb, ya, yb, fx, fy);
+      const int mxa = xa >> L.shift, mxb = xb >> L.shift;
+      const int mya = ya >> L.shift, myb = yb >> L.shift;
+      flag(ok, L.gid_base + mxa + mya * L.mcus_x, units);
+      flag(ok && mxb != mxa, L.gid_base + mxb + mya * L.mcus_x, units);  // footprint straddles MCUs
+      flag(ok && myb != mya, L.gid_base + mxa + myb * L.mcus_x, units);
+      flag(ok && mxb != mxa && myb != mya, L.gid_base + mxb + myb * L.mcus_x, units);
     }
   };
   for_each_quad(a.views, [&](const View& V, int y, int x) {
     float u[4], v[4];
     uint32_t t[4], m[4];
     const int n = load_px4(V, y, x, u, v, t, m);
+    QuadLevels q;
+    quad_levels(a.tl, n, t, m, a.only_tex, q);
+    if (q.uniform) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      if (i >= n || t[i] == JT_EMPTY_TEXTURE || (a.only_tex >= 0 && (int)t[i] != a.only_tex)) continue;
-      if (!lc.get(a.tl, t[i], m[i]) || ((lc.L.sampling == kSamplingCoef) != (a.coef_mode != 0))) {
-        missing = true;
-        continue;
-      }
-      const Lvl& L = lc.L;
-      const uint8_t units = (uint8_t)L.units;
-      if (FILTER == JT_FILTER_NEAREST) {
-        int xx, yy;
-        nearest_texel(u[i], v[i], L, xx, yy);
-        flag(L.gid_base + (xx >> L.shift) + (yy >> L.shift) * L.mcus_x, units);
-      } else {
-        int xa, xb, ya, yb;
-        float fx, fy;
-        bilinear_taps(u[i], v[i], L, xa, xb, ya, yb, fx, fy);
-        const int mxa = xa >> L.shift, mxb = xb >> L.shift;
-        const int mya = ya >> L.shift, myb = yb >> L.shift;
-        flag(L.gid_base + mxa + mya * L.mcus_x, units);
-        if (mxb != mxa) flag(L.gid_base + mxb + mya * L.mcus_x, units);
-        if (myb != mya) flag(L.gid_base + mxa + myb * L.mcus_x, units);
-        if (mxb != mxa && myb != mya) flag(L.gid_base + mxb + myb * L.mcus_x, units);
-      }
+      for (int i = 0; i < 4; ++i) pixel(q.shared, q.key[i], u[i], v[i]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) pixel(load_level(a.tl, q.key[i]), q.key[i], u[i], v[i]);
     }
   });
   if (missing) atomicOr(&a.state->err, JT_DEVERR_MISSING);
@@ -204,22 +232,6 @@ __global__ void k_mark(const __grid_constant__ MarkArgs a) {
 // ---------------------------------------------------------------------------------------
 // Colourise
 // ---------------------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t slot_of(const ColorizeArgs& a, uint32_t gid, uint32_t units, bool& bad) {
-  const uint32_t off = __ldg(&a.slot[gid]);
-  if (off + units > a.cap_units) {
-    bad = true;
-    return 0xFFFFFFFFu;
-  }
-  return off;
-}
-
-__device__ __forceinline__ uint32_t texel(const ColorizeArgs& a, uint32_t off, int x, int y, int shift) {
-  if (off == 0xFFFFFFFFu) return 0xFF000000u;
-  const int mwm = (1 << shift) - 1;
-  const uint32_t* tile = reinterpret_cast<const uint32_t*>(a.cache) + (size_t)off * (kUnitBytes / 4);
-  return __ldg(tile + (((y & mwm) << shift) | (x & mwm)));
-}
-
 // Channel `ch` of an RGBA8 texel as float, exactly: the byte is placed under the exponent
 // of 2^23 (PRMT) and the bias subtracted (full-rate ops instead of an int-to-float
 // conversion).
@@ -246,67 +258,81 @@ __device__ __forceinline__ uint32_t blend(uint32_t c00, uint32_t c10, uint32_t c
 
 template <int FILTER>
 __global__ void k_colorize(const __grid_constant__ ColorizeArgs a) {
-  LevelCache lc;
   bool missing = false, bad = false;
-  uint32_t last_gid = kNoGid, last_off = 0xFFFFFFFFu;  // slot of the last MCU looked up
+  uint32_t last_gid = kNoGid, last_off = 0;  // slot of the last MCU looked up
+  const uint32_t* cache = reinterpret_cast<const uint32_t*>(a.cache);
+  // cache-unit offset of gid g (0 and `bad` when it would read past the cache)
+  auto slot = [&](bool on, uint32_t g, uint32_t units) -> uint32_t {
+    uint32_t off = last_off;
+    if (on && g != last_gid) off = __ldg(&a.slot[g]);
+    const bool fits = off + units <= a.cap_units;
+    bad |= on && !fits;
+    return fits ? off : 0u;
+  };
+  auto pixel = [&](const Lvl& L, uint32_t key, float u, float v) -> uint32_t {
+    const bool ok = key < kNoKey - 1 && L.w != 0 && L.sampling != kSamplingCoef;
+    missing |= key != kNoKey && !ok;
+    const int mwm = (1 << L.shift) - 1;
+    if (FILTER == JT_FILTER_NEAREST) {
+      int x, y;
+      nearest_texel(u, v, L, x, y);
+      const uint32_t g = L.gid_base + (x >> L.shift) + (y >> L.shift) * L.mcus_x;
+      const uint32_t off = slot(ok, g, L.units);
+      if (ok) {
+        last_gid = g;
+        last_off = off;
+      }
+      const uint32_t c = ok ? __ldg(cache + (size_t)off * (kUnitBytes / 4) + (((y & mwm) << L.shift) | (x & mwm)))
+                            : 0u;
+      return ok ? c : 0xFF000000u;
+    } else {
+      int xa, xb, ya, yb;
+      float fx, fy;
+      bilinear_taps(u, v, L, xa, xb, ya, yb, fx, fy);
+      const int mxa = xa >> L.shift, mxb = xb >> L.shift;
+      const int mya = ya >> L.shift, myb = yb >> L.shift;
+      const uint32_t g00 = L.gid_base + mxa + mya * L.mcus_x;
+      const uint32_t o00 = slot(ok, g00, L.units);
+      if (ok) {
+        last_gid = g00;
+        last_off = o00;
+      }
+      const bool sx = mxb != mxa, sy = myb != mya;  // footprint straddles MCUs (rare)
+      uint32_t o10 = o00, o01 = o00, o11 = o00;
+      if (ok && sx) o10 = slot(true, L.gid_base + mxb + mya * L.mcus_x, L.units);
+      if (ok && sy) o01 = slot(true, L.gid_base + mxa + myb * L.mcus_x, L.units);
+      if (ok && sx && sy) o11 = slot(true, L.gid_base + mxb + myb * L.mcus_x, L.units);
+      o11 = sx && sy ? o11 : (sx ? o10 : o01);
+      const int ia = (ya & mwm) << L.shift, ib = (yb & mwm) << L.shift;
+      const int ja = xa & mwm, jb = xb & mwm;
+      uint32_t c00 = 0, c10 = 0, c01 = 0, c11 = 0;
+      if (ok) {
+        c00 = __ldg(cache + (size_t)o00 * (kUnitBytes / 4) + (ia | ja));
+        c10 = __ldg(cache + (size_t)o10 * (kUnitBytes / 4) + (ia | jb));
+        c01 = __ldg(cache + (size_t)o01 * (kUnitBytes / 4) + (ib | ja));
+        c11 = __ldg(cache + (size_t)o11 * (kUnitBytes / 4) + (ib | jb));
+      }
+      return ok ? blend(c00, c10, c01, c11, fx, fy) : 0xFF000000u;
+    }
+  };
   for_each_quad(a.views, [&](const View& V, int y, int x) {
     float u[4], v[4];
     uint32_t t[4], m[4];
     const int n = load_px4(V, y, x, u, v, t, m);
-    if (n == 0) return;
+    QuadLevels q;
+    quad_levels(a.tl, n, t, m, a.only_tex, q);
     uint32_t px[4];
+    if (q.uniform) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) px[i] = pixel(q.shared, q.key[i], u[i], v[i]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) px[i] = pixel(load_level(a.tl, q.key[i]), q.key[i], u[i], v[i]);
+    }
+    if (n == 0) return;
     bool write[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      px[i] = 0xFF000000u;
-      write[i] = i < n && (a.only_tex < 0 || (int)t[i] == a.only_tex);
-      if (!write[i] || t[i] == JT_EMPTY_TEXTURE) continue;
-      if (!lc.get(a.tl, t[i], m[i]) || lc.L.sampling == kSamplingCoef) {
-        missing = true;
-        continue;
-      }
-      const Lvl& L = lc.L;
-      if (FILTER == JT_FILTER_NEAREST) {
-        int xx, yy;
-        nearest_texel(u[i], v[i], L, xx, yy);
-        const uint32_t g = L.gid_base + (xx >> L.shift) + (yy >> L.shift) * L.mcus_x;
-        if (g != last_gid) {
-          last_gid = g;
-          last_off = slot_of(a, g, L.units, bad);
-        }
-        px[i] = texel(a, last_off, xx, yy, L.shift);
-      } else {
-        int xa, xb, ya, yb;
-        float fx, fy;
-        bilinear_taps(u[i], v[i], L, xa, xb, ya, yb, fx, fy);
-        const int mxa = xa >> L.shift, mxb = xb >> L.shift;
-        const int mya = ya >> L.shift, myb = yb >> L.shift;
-        const uint32_t g00 = L.gid_base + mxa + mya * L.mcus_x;
-        if (g00 != last_gid) {  // consecutive pixels mostly sample the same MCU
-          last_gid = g00;
-          last_off = slot_of(a, g00, L.units, bad);
-        }
-        const uint32_t o00 = last_off;
-        // footprint inside one MCU and not wrapped around a level narrower than an MCU
-        if (mxb == mxa && myb == mya && xb == xa + 1 && yb == ya + 1 && o00 != 0xFFFFFFFFu) {
-          const int mwm = (1 << L.shift) - 1;
-          const uint32_t* tile = reinterpret_cast<const uint32_t*>(a.cache) + (size_t)o00 * (kUnitBytes / 4);
-          const uint32_t* p00 = tile + (((ya & mwm) << L.shift) | (xa & mwm));
-          px[i] = blend(__ldg(p00), __ldg(p00 + 1), __ldg(p00 + (1 << L.shift)), __ldg(p00 + (1 << L.shift) + 1), fx,
-                        fy);
-        } else {
-          uint32_t o10 = o00, o01 = o00, o11 = o00;
-          if (mxb != mxa) o10 = slot_of(a, L.gid_base + mxb + mya * L.mcus_x, L.units, bad);
-          if (myb != mya) o01 = slot_of(a, L.gid_base + mxa + myb * L.mcus_x, L.units, bad);
-          if (mxb != mxa && myb != mya)
-            o11 = slot_of(a, L.gid_base + mxb + myb * L.mcus_x, L.units, bad);
-          else
-            o11 = mxb != mxa ? o10 : o01;
-          px[i] = blend(texel(a, o00, xa, ya, L.shift), texel(a, o10, xb, ya, L.shift),
-                        texel(a, o01, xa, yb, L.shift), texel(a, o11, xb, yb, L.shift), fx, fy);
-        }
-      }
-    }
+    for (int i = 0; i < 4; ++i) write[i] = i < n && (a.only_tex < 0 || (int)t[i] == a.only_tex);
     const uint32_t p0 = (uint32_t)y * (uint32_t)V.width + (uint32_t)x;
     if (n == 4 && (V.width & 3) == 0 && write[0] && write[1] && write[2] && write[3]) {
       V.out[p0 >> 2] = make_uint4(px[0], px[1], px[2], px[3]);

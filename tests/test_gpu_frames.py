@@ -129,8 +129,8 @@ def test_autotune_keeps_results(jt, scene):
     ctx.close()
 
 
-@pytest.mark.parametrize("mcus,warps,per_sm", [(4, 2, 1), (8, 8, 2), (8, 16, 1), (16, 4, 1), (32, 2, 1),
-                                               (32, 4, 1)])
+@pytest.mark.parametrize("mcus,warps,per_sm", [(4, 2, 1), (8, 8, 2), (4, 16, 1), (16, 4, 1), (32, 2, 1),
+                                               (16, 2, 2)])
 def test_decode_shapes_bit_exact(jt, scene, mcus, warps, per_sm):
     ts, views = scene
     ctx = jt.Context(0, 1 << 15)
