@@ -220,6 +220,35 @@ jt_status jt_read_slots(jt_ctx* ctx, uint64_t gid_begin, uint64_t n, uint32_t* d
  * (16 rows of 16 RGBA8 texels), a 4:4:4 MCU one unit (8 rows of 8). Synchronises. */
 jt_status jt_read_cache(jt_ctx* ctx, uint64_t unit_begin, uint64_t n, uint8_t* dst);
 
+/* ---- compaction without allocation (no counterpart in the paper) ------------------------- */
+
+/* Largest n accepted by jt_compact_static: 4096 scan tiles of 4096 flags. */
+#define JT_STATIC_COMPACT_MAX_FLAGS 16777216u
+
+/* The compaction step of jt_decode (Sec. 4.2's decode queue; flags -> work list and cache
+ * slots), on caller-owned buffers, for callers that must not allocate device memory at the
+ * call: a frame loop that cannot afford the device-wide synchronisation cudaMalloc/cudaFree
+ * may cause, code under memory pressure, or code running inside an allocator. It makes no
+ * allocating call (no cudaMalloc/cudaFree, no library allocator); its scratch is a fixed
+ * array in the library's device image. No context is needed; the current device is used.
+ *
+ *  flags    device uint8[n], 16-byte aligned: cache units each index needs (0 = not needed).
+ *           Zeroed by the call (as jt_decode leaves a context's flags).
+ *  slot     device uint32[n]: slot[i] = sum of flags[j] for j < i, written where flags[i] != 0.
+ *  work     device uint32[work_cap]: the indices i with flags[i] != 0, ascending; entries
+ *           past work_cap are dropped (and JT_DEVERR_CAPACITY is set in totals[2]).
+ *  totals   device uint32[3]: {count of flagged indices, sum of flags, JT_DEVERR_* bits}.
+ *  All four stay caller-owned and must stay valid until the stream reaches the work.
+ * Returns JT_ERR_CAPACITY for n > JT_STATIC_COMPACT_MAX_FLAGS and JT_ERR_INVALID_ARG for a
+ * null or misaligned buffer, both before enqueueing anything; JT_ERR_CUDA if a CUDA call fails
+ * (jt_last_error needs a context and does not apply). Enqueues a memset, one kernel and two
+ * device-to-device copies on `stream`, which stays asynchronous.
+ * The first call on each device looks up the scratch address and must happen outside any
+ * stream capture. Calls share the scratch: two calls in flight at once on one device race
+ * and corrupt each other's results, so order them (one stream, or events). */
+jt_status jt_compact_static(uint8_t* flags, uint32_t n, uint32_t* slot, uint32_t* work, uint32_t work_cap,
+                            uint32_t* totals, jt_stream stream);
+
 /* ---- differentiable colourise (float chain; not in the paper) ---------------------------- */
 
 /* Registers `count` coefficient textures with ids first_tex_id.. first_tex_id+count-1, each

@@ -97,7 +97,10 @@ _SIGS = {
     "jt_register_coeff_textures": [_P, _I, _I, _I, _I],
     "jt_colorize_float": [_P, ctypes.POINTER(jt_gbuffer), _P, _P, _P],
     "jt_colorize_backward": [_P, ctypes.POINTER(jt_gbuffer), _P, _P, _P],
+    "jt_compact_static": [_P, ctypes.c_uint32, _P, _P, ctypes.c_uint32, _P, _P],
 }
+
+STATIC_COMPACT_MAX_FLAGS = 1 << 24  # JT_STATIC_COMPACT_MAX_FLAGS
 
 _lib = None
 
@@ -139,6 +142,24 @@ def _stream(stream=None) -> int:
     if stream is None:
         stream = torch.cuda.current_stream()
     return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def compact_static(flags, slot, work, totals, stream=None) -> None:
+    """jt_compact_static on torch CUDA tensors: flags uint8[n] (zeroed by the call), slot
+    int32/uint32[n], work int32/uint32[cap], totals int32/uint32[3] = {count, units, error
+    bits}. Asynchronous on `stream`; allocates nothing."""
+    n = flags.numel()
+    if n > STATIC_COMPACT_MAX_FLAGS:
+        raise JTError(5, f"jt_compact_static takes at most {STATIC_COMPACT_MAX_FLAGS} flags, got {n}")
+    for name, t, need in (("flags", flags, 1), ("slot", slot, 4), ("work", work, 4), ("totals", totals, 4)):
+        if not t.is_cuda or not t.is_contiguous() or t.element_size() != need:
+            raise JTError(1, f"{name} must be a contiguous CUDA tensor of {need}-byte elements")
+    if slot.numel() < n or totals.numel() < 3:
+        raise JTError(1, "slot needs n entries and totals 3")
+    s = lib().jt_compact_static(flags.data_ptr(), n, slot.data_ptr(), work.data_ptr(), work.numel(),
+                                totals.data_ptr(), _stream(stream))
+    if s != 0:
+        raise JTError(s, "jt_compact_static: " + lib().jt_status_string(s).decode())
 
 
 class DeviceGBuffer:
