@@ -360,3 +360,36 @@ class Context:
         g = gb.c()
         self._check(lib().jt_colorize_backward(self._h, ctypes.byref(g), grad_frame.data_ptr(),
                                                grad_coef.data_ptr(), _stream(stream)))
+
+    def colorize_float_autograd(self, gb: DeviceGBuffer, coef):
+        """F = colorize_float(coef) as a differentiable torch op (backward: jt_colorize_backward)."""
+        return _float_function().apply(coef, self, gb)
+
+
+_FLOAT_FN = None
+
+
+def _float_function():
+    """torch.autograd.Function around jt_colorize_float / jt_colorize_backward (built on first use)."""
+    global _FLOAT_FN
+    if _FLOAT_FN is None:
+        import torch
+
+        class ColorizeFloat(torch.autograd.Function):
+            @staticmethod
+            def forward(fctx, coef, jctx, gb):
+                coef = coef.contiguous()
+                out = torch.empty((gb.height, gb.width, 3), dtype=torch.float32, device=coef.device)
+                jctx.colorize_float(gb, coef, out)
+                fctx.jctx, fctx.gb, fctx.coef_shape = jctx, gb, coef.shape
+                return out
+
+            @staticmethod
+            def backward(fctx, grad):
+                grad = grad.contiguous()
+                gc = torch.empty(fctx.coef_shape, dtype=torch.float32, device=grad.device)
+                fctx.jctx.colorize_backward(fctx.gb, grad, gc)
+                return gc, None, None
+
+        _FLOAT_FN = ColorizeFloat
+    return _FLOAT_FN

@@ -422,6 +422,40 @@ bool valid_tuning(const jt_ctx* c, const jt_tuning& t) {
          t.pixel_ctas_per_sm <= 32;
 }
 
+// Shared set-up of the two float calls: checks, the view, the float-chain arguments.
+jt_status float_setup(jt_ctx* c, const jt_gbuffer* g, const float* in, const float* frame_ptr, FloatArgs& a) {
+  if (c->coef_first < 0) return fail(c, JT_ERR_STATE, "no coefficient textures registered");
+  if (c->phase == Phase::Marked) return fail(c, JT_ERR_STATE, "a marked frame is pending");
+  if (!in || !frame_ptr || !aligned(in, 16) || !aligned(frame_ptr, 16))
+    return fail(c, JT_ERR_INVALID_ARG, "coefficient and frame buffers must be 16-byte aligned device pointers");
+  jt_view v{};
+  if (g) v.g = *g;
+  std::memset(&a, 0, sizeof a);
+  jt_status s = make_views(c, &v, 1, false, a.views);
+  if (s != JT_OK) return s;
+  a.tl = lookup(c);
+  a.slot = c->slot;
+  a.work = c->work;
+  a.coef_gid_base = c->coef_gid_base;
+  a.coef_mcus = (uint32_t)((uint64_t)c->coef_count * (c->coef_w / 16) * (c->coef_h / 16));
+  a.tiles = c->float_tiles;
+  a.tile_cap = c->float_tile_cap;
+  a.state = c->state;
+  // orthonormal 8-point DCT-III basis, A[x][u] = C(u)/2 cos((2x+1) u pi / 16)
+  const double pi = 3.14159265358979323846;
+  for (int x = 0; x < 8; ++x)
+    for (int u = 0; u < 8; ++u)
+      a.basis[x * 8 + u] = (float)((u == 0 ? std::sqrt(0.5) : 1.0) * 0.5 * std::cos((2 * x + 1) * u * pi / 16.0));
+  return JT_OK;
+}
+
+// Needed set of the coefficient textures (bilinear taps) and its compaction.
+jt_status enqueue_float_needed(jt_ctx* c, const FloatArgs& a, cudaStream_t st) {
+  jt_status s;
+  if ((s = enqueue_mark(c, a.views, JT_FILTER_BILINEAR, -1, 1, st)) != JT_OK) return s;
+  return enqueue_scan(c, c->coef_gid_base, (uint64_t)c->coef_gid_base + a.coef_mcus, st);
+}
+
 }  // namespace
 
 extern "C" {
@@ -959,21 +993,83 @@ jt_status jt_read_cache(jt_ctx* c, uint64_t unit_begin, uint64_t n, uint8_t* dst
 
 jt_status jt_register_coeff_textures(jt_ctx* c, int first_tex_id, int count, int width, int height) {
   if (!c) return JT_ERR_INVALID_ARG;
-  (void)first_tex_id; (void)count; (void)width; (void)height;
-  return fail(c, JT_ERR_UNSUPPORTED, "float chain not built yet");
+  if (c->coef_first >= 0) return fail(c, JT_ERR_STATE, "coefficient textures are already registered");
+  if (c->phase == Phase::Marked) return fail(c, JT_ERR_STATE, "registration between jt_mark and jt_decode");
+  if (count <= 0 || first_tex_id < 0 || (int64_t)first_tex_id + count > 0xFFFF)
+    return fail(c, JT_ERR_INVALID_ARG, "texture ids %d..%d out of range", first_tex_id, first_tex_id + count - 1);
+  if (width <= 0 || height <= 0 || width % 16 || height % 16 || width > 65520 || height > 65520)
+    return fail(c, JT_ERR_INVALID_ARG, "coefficient textures must be multiples of 16 texels, got %dx%d", width,
+                height);
+  for (int t = first_tex_id; t < first_tex_id + count; ++t)
+    if ((uint32_t)t < c->map_ntex && c->map[(size_t)t * JT_MAX_LEVELS] >= 0)
+      return fail(c, JT_ERR_INVALID_ARG, "texture %d level 0 already exists", t);
+  const uint64_t mx = width / 16, my = height / 16, per = mx * my;
+  if (c->ngid + per * count > kMaxGids) return fail(c, JT_ERR_UNSUPPORTED, "more than 2^26 MCUs in one context");
+  DeviceGuard dg(c->device);
+  if (!dg.ok) return fail(c, JT_ERR_CUDA, "cannot select device %d", c->device);
+  const uint64_t cap = std::min<uint64_t>(per * count, c->cap_units / 4);
+  jt_status s;
+  if ((s = dev_alloc(c, &c->float_tiles, cap * 256 * sizeof(float4))) != JT_OK) return s;
+  c->float_tile_cap = (uint32_t)cap;
+  c->coef_gid_base = (uint32_t)c->ngid;
+  for (int t = 0; t < count; ++t) {
+    DevDesc d{};
+    d.gid_base = (uint32_t)c->ngid;
+    d.nmcu = (uint32_t)per;
+    d.width = (uint16_t)width;
+    d.height = (uint16_t)height;
+    d.mcus_x = (uint16_t)mx;
+    d.mcus_y = (uint16_t)my;
+    d.sampling = kSamplingCoef;
+    d.units = 1;  // one flag unit per MCU: the compaction's slot is the work position
+    if ((s = add_level(c, first_tex_id + t, 0, d, Level{first_tex_id + t, 0})) != JT_OK) return s;
+  }
+  c->coef_first = first_tex_id;
+  c->coef_count = count;
+  c->coef_w = width;
+  c->coef_h = height;
+  return JT_OK;
 }
 
 jt_status jt_colorize_float(jt_ctx* c, const jt_gbuffer* g, const float* coeffs, float* out_rgb, jt_stream stream) {
   if (!c) return JT_ERR_INVALID_ARG;
-  (void)g; (void)coeffs; (void)out_rgb; (void)stream;
-  return fail(c, JT_ERR_UNSUPPORTED, "float chain not built yet");
+  FloatArgs a;
+  jt_status s = float_setup(c, g, coeffs, out_rgb, a);
+  if (s != JT_OK) return s;
+  a.coef = coeffs;
+  a.frame = out_rgb;
+  DeviceGuard dg(c->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if ((s = enqueue_float_needed(c, a, st)) != JT_OK) return s;
+  launch_float_tiles(a, c->sm_count * 8, st);
+  if ((s = check_launch(c, "float tiles")) != JT_OK) return s;
+  launch_float_colorize(a, c->tuning.pixel_threads, pixel_grid(c, a.views), st);
+  if ((s = check_launch(c, "float colourise")) != JT_OK) return s;
+  c->phase = Phase::Idle;  // the work list now describes coefficient MCUs
+  c->last_stream = st;
+  return JT_OK;
 }
 
 jt_status jt_colorize_backward(jt_ctx* c, const jt_gbuffer* g, const float* grad_frame, float* grad_coeffs,
                                jt_stream stream) {
   if (!c) return JT_ERR_INVALID_ARG;
-  (void)g; (void)grad_frame; (void)grad_coeffs; (void)stream;
-  return fail(c, JT_ERR_UNSUPPORTED, "float chain not built yet");
+  FloatArgs a;
+  jt_status s = float_setup(c, g, grad_coeffs, grad_frame, a);
+  if (s != JT_OK) return s;
+  a.frame = const_cast<float*>(grad_frame);  // read only in the backward kernels
+  a.grad_coef = grad_coeffs;
+  DeviceGuard dg(c->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if ((s = enqueue_float_needed(c, a, st)) != JT_OK) return s;
+  launch_float_zero_tiles(a, c->sm_count * 8, st);
+  if ((s = check_launch(c, "float zero")) != JT_OK) return s;
+  launch_float_scatter(a, c->tuning.pixel_threads, pixel_grid(c, a.views), st);
+  if ((s = check_launch(c, "float scatter")) != JT_OK) return s;
+  launch_float_adjoint(a, c->sm_count * 8, st);
+  if ((s = check_launch(c, "float adjoint")) != JT_OK) return s;
+  c->phase = Phase::Idle;
+  c->last_stream = st;
+  return JT_OK;
 }
 
 }  // extern "C"

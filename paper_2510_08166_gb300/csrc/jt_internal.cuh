@@ -193,25 +193,30 @@ struct ColorizeArgs {
 };
 void launch_colorize(const ColorizeArgs& a, int threads, int grid, cudaStream_t s);
 
-// Float chain (differentiable colourise).
+// Float chain (differentiable colourise; not in the paper). Coefficient textures are
+// 4:2:0 level-0 textures whose MCUs are marked with 1 unit each, so after the compaction
+// slot[gid] is the MCU's position in the work list and the index of its float tile.
 struct FloatArgs {
   ViewSet views;          // one view
   TexLookup tl;
-  const uint32_t* slot;   // gid -> work position (coefficient textures use 1 unit per MCU)
+  const uint32_t* slot;   // gid -> work position = float tile index
   const uint32_t* work;
-  const float* coef;      // [T][my][mx][6][64]
+  const float* coef;      // [T][my][mx][6][64], natural order k = v*8+u
   uint32_t coef_gid_base; // gid of coefficient texture 0, MCU 0
-  float4* tiles;          // [count][16][16] float4 (RGB + pad), scratch
-  uint32_t tile_cap;      // tiles available
-  float* frame;           // [npx][3] forward output or gradient input
-  float* grad_coef;       // [T][my][mx][6][64] backward output
+  uint32_t coef_mcus;     // MCUs of all coefficient textures
+  float4* tiles;          // [tile_cap][16][16] float4 (R, G, B, 0): forward texels or their gradients
+  uint32_t tile_cap;
+  float* frame;           // [npx][3]: forward output, or the gradient input of the backward pass
+  float* grad_coef;       // [T][my][mx][6][64]: backward output
   FrameState* state;
+  float basis[64];        // A[x][u] = C(u)/2 cos((2x+1)u pi/16), C(0) = 1/sqrt(2); x*8+u
 };
+constexpr int kFloatWarps = 8;  // warps per CTA of the per-MCU float kernels
 void launch_float_tiles(const FloatArgs& a, int grid, cudaStream_t s);
-void launch_float_colorize(const FloatArgs& a, int threads, int grid, cudaStream_t s);
 void launch_float_zero_tiles(const FloatArgs& a, int grid, cudaStream_t s);
-void launch_float_scatter(const FloatArgs& a, int threads, int grid, cudaStream_t s);
 void launch_float_adjoint(const FloatArgs& a, int grid, cudaStream_t s);
+void launch_float_colorize(const FloatArgs& a, int threads, int grid, cudaStream_t s);
+void launch_float_scatter(const FloatArgs& a, int threads, int grid, cudaStream_t s);
 
 // The integer IDCT constants the decode kernel is compiled with, for the host-side check
 // against round(8192 cos(k pi / 16)), k = 1..7.

@@ -347,7 +347,124 @@ __global__ void k_colorize(const __grid_constant__ ColorizeArgs a) {
   if (bad) atomicOr(&a.state->err, JT_DEVERR_CAPACITY);
 }
 
+// ---------------------------------------------------------------------------------------
+// Float chain (differentiable colourise, not in the paper): bilinear taps as above over
+// the float tiles of the coefficient textures; weights (1-fx)(1-fy), fx(1-fy), (1-fx)fy, fx fy.
+// The forward pass blends the four texels; the backward pass scatters w * dL/dF into the
+// four texels' gradient tiles (float4 atomics; their order is the only non-determinism).
+// ---------------------------------------------------------------------------------------
+struct FloatTaps {
+  uint32_t idx[4];  // float4 index into the tiles (tile * 256 + texel)
+  float w[4];
+  bool ok;
+};
+
+// Taps of one pixel; ok = false (and `missing`/`over` updated) when the pixel is empty,
+// names a texture that is not a coefficient texture, or a tap's tile is past the capacity.
+__device__ __forceinline__ FloatTaps float_taps(const FloatArgs& a, const Lvl& L, uint32_t key, float u, float v,
+                                                bool& missing, bool& over) {
+  FloatTaps T;
+  T.ok = key < kNoKey - 1 && L.w != 0 && L.sampling == kSamplingCoef;
+  missing |= key != kNoKey && !T.ok;
+  int xa, xb, ya, yb;
+  float fx, fy;
+  bilinear_taps(u, v, L, xa, xb, ya, yb, fx, fy);
+  const int xs[4] = {xa, xb, xa, xb}, ys[4] = {ya, ya, yb, yb};
+  T.w[0] = (1.f - fx) * (1.f - fy);
+  T.w[1] = fx * (1.f - fy);
+  T.w[2] = (1.f - fx) * fy;
+  T.w[3] = fx * fy;
+  bool fit = true;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const uint32_t g = L.gid_base + (xs[i] >> 4) + (ys[i] >> 4) * L.mcus_x;
+    const uint32_t tile = T.ok ? __ldg(a.slot + g) : 0u;
+    fit &= tile < a.tile_cap;
+    T.idx[i] = (tile < a.tile_cap ? tile : 0u) * 256u + (uint32_t)(((ys[i] & 15) << 4) | (xs[i] & 15));
+  }
+  over |= T.ok && !fit;
+  T.ok = T.ok && fit;
+  return T;
+}
+
+template <bool BACKWARD>
+__global__ void k_float_pixels(const __grid_constant__ FloatArgs a) {
+  bool missing = false, over = false;
+  for_each_quad(a.views, [&](const View& V, int y, int x) {
+    float u[4], v[4];
+    uint32_t t[4], m[4];
+    const int n = load_px4(V, y, x, u, v, t, m);
+    QuadLevels q;
+    quad_levels(a.tl, n, t, m, -1, q);
+    if (n == 0) return;
+    const uint32_t p0 = (uint32_t)y * (uint32_t)V.width + (uint32_t)x;
+    float* fr = a.frame + (size_t)p0 * 3;  // 12 floats of the quad, 16-byte aligned when p0 % 4 == 0
+    const bool vec = n == 4 && (V.width & 3) == 0;
+    float rgb[12];
+    if (BACKWARD) {
+      if (vec) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          const float4 g4 = __ldg(reinterpret_cast<const float4*>(fr) + i);
+          rgb[4 * i] = g4.x; rgb[4 * i + 1] = g4.y; rgb[4 * i + 2] = g4.z; rgb[4 * i + 3] = g4.w;
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 12; ++i) rgb[i] = i < 3 * n ? __ldg(fr + i) : 0.f;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const Lvl L = q.uniform ? q.shared : load_level(a.tl, q.key[i]);
+      const FloatTaps T = float_taps(a, L, q.key[i], u[i], v[i], missing, over);
+      if (BACKWARD) {
+        if (T.ok) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            atomicAdd(a.tiles + T.idx[k], make_float4(T.w[k] * rgb[3 * i], T.w[k] * rgb[3 * i + 1],
+                                                      T.w[k] * rgb[3 * i + 2], 0.f));
+        }
+      } else {
+        float r = 0.f, gg = 0.f, b = 0.f;
+        if (T.ok) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const float4 c = __ldg(a.tiles + T.idx[k]);
+            r = fmaf(T.w[k], c.x, r);
+            gg = fmaf(T.w[k], c.y, gg);
+            b = fmaf(T.w[k], c.z, b);
+          }
+        }
+        rgb[3 * i] = r;
+        rgb[3 * i + 1] = gg;
+        rgb[3 * i + 2] = b;
+      }
+    }
+    if (!BACKWARD) {
+      if (vec) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+          reinterpret_cast<float4*>(fr)[i] = make_float4(rgb[4 * i], rgb[4 * i + 1], rgb[4 * i + 2], rgb[4 * i + 3]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 12; ++i)
+          if (i < 3 * n) fr[i] = rgb[i];
+      }
+    }
+  });
+  if (missing) atomicOr(&a.state->err, JT_DEVERR_MISSING);
+  if (over) atomicOr(&a.state->err, JT_DEVERR_CAPACITY);
+}
+
 }  // namespace
+
+void launch_float_colorize(const FloatArgs& a, int threads, int grid, cudaStream_t s) {
+  k_float_pixels<false><<<grid, threads, 0, s>>>(a);
+}
+
+void launch_float_scatter(const FloatArgs& a, int threads, int grid, cudaStream_t s) {
+  k_float_pixels<true><<<grid, threads, 0, s>>>(a);
+}
 
 void launch_mark(const MarkArgs& a, int threads, int grid, cudaStream_t s) {
   if (a.filter == JT_FILTER_NEAREST)
