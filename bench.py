@@ -196,6 +196,91 @@ def run_reference(args, rank, world):
 # GPU arm
 # ---------------------------------------------------------------------------------------
 
+def timed(fn, steps, warmup, stream, flush=None):
+    """Mean ms of fn() over `steps` CUDA-event-timed calls after `warmup` untimed ones."""
+    import torch
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    ms = []
+    for s in range(warmup + steps):
+        if flush is not None:
+            flush.fill_(s & 255)
+        a0.record(stream)
+        fn()
+        a1.record(stream)
+        a1.synchronize()
+        if s >= warmup:
+            ms.append(a0.elapsed_time(a1))
+    return statistics.mean(ms)
+
+
+def run_views(ctx, ts, jt, dev, flush, stream, steps):
+    """Batched views over the same textures: 8 G-buffers (720p .. 4K and two stereo VR
+    pairs) in one graph (one mark over all views into one flag array, one compaction, one
+    persistent decode of the union, one colourise) against the plain per-view, per-texture
+    pipeline."""
+    import torch
+    import synth
+    views = synth.config3_views(ts)
+    dv = [jt.DeviceGBuffer.from_host(v, dev) for v in views]
+    outs = [torch.empty((v.height, v.width, 4), dtype=torch.uint8, device=dev) for v in views]
+    pairs = list(zip(dv, outs))
+    g = ctx.frame_graph(pairs, jt.FILTER_BILINEAR)
+    ms_graph = timed(lambda: ctx.graph_launch(g), steps, 3, stream, flush)
+    st = ctx.stats()
+    union = int(st["needed_blocks"])
+    ref = [o.clone() for o in outs]
+    per_view = []
+    for d, o in pairs:  # needed blocks of each view alone
+        ctx.frame([(d, o)], jt.FILTER_BILINEAR)
+        per_view.append(int(ctx.stats()["needed_blocks"]))
+    ms_plain = timed(lambda: ctx.frame_plain(pairs, jt.FILTER_BILINEAR), max(2, steps // 10), 1, stream, flush)
+    ctx.stats()
+    same = all(bool(torch.equal(a, b)) for a, b in zip(ref, outs))
+    ctx.graph_destroy(g)
+    px = sum(v.width * v.height for v in views)
+    return {"workload": "8 views 1280x720, 1920x1080, 2560x1440, 3840x2160, 2x2 VR 2064x2208 (two stereo poses), "
+                        "same 64 textures, bilinear", "pixels": px, "needed_blocks_union": union,
+            "needed_blocks_per_view": per_view, "batched_graph_ms": ms_graph, "plain_ms": ms_plain,
+            "speedup": ms_plain / ms_graph, "same_output": same,
+            "blocks_per_s": union / (ms_graph * 1e-3)}
+
+
+def run_adjoint(jt, dev, flush, stream, steps, peak):
+    """Differentiable colourise: 16 coefficient textures 2048^2 (float32 dequantised DCT,
+    403 MB), 1920x1080 perspective plane, bilinear; forward F, then the adjoint of
+    L = sum (F - T)^2 to the coefficients."""
+    import torch
+    import synth
+    ts, coef, gb, target = synth.config5()
+    T, my, mx = coef.shape[:3]
+    ctx = jt.Context(dev.index, max_cache_blocks=T * my * mx)  # a float tile for every MCU (4 KiB each)
+    ctx.register_coeff_textures(0, T, mx * 16, my * 16)
+    c = torch.from_numpy(coef).to(dev)
+    tgt = torch.from_numpy(target).to(dev)
+    dgb = jt.DeviceGBuffer.from_host(gb, dev)
+    F = torch.empty((gb.height, gb.width, 3), dtype=torch.float32, device=dev)
+    gc = torch.empty_like(c)
+    ms_fwd = timed(lambda: ctx.colorize_float(dgb, c, F), steps, 3, stream, flush)
+    needed = int(ctx.stats()["needed_blocks"])
+    gF = (2.0 * (F - tgt)).contiguous()
+    ms_bwd = timed(lambda: ctx.colorize_backward(dgb, gF, gc), steps, 3, stream, flush)
+    ctx.stats()
+    npx = gb.width * gb.height
+    # algorithmic HBM bytes: every gradient written once; G-buffer read by mark and scatter,
+    # the frame gradient once; per needed MCU its texel-gradient tile zeroed and read back.
+    # Forward: G-buffer twice, F written, per needed MCU its coefficients read and its float
+    # tile written, four 16-byte texel taps per pixel
+    bwd_bytes = 4.0 * c.numel() + 2 * 11.0 * npx + 12.0 * npx + needed * (2 * 4096.0)
+    fwd_bytes = 2 * 11.0 * npx + 12.0 * npx + needed * (1536.0 + 4096.0) + 4 * 16.0 * npx
+    ctx.close()
+    ach = bwd_bytes / (ms_bwd * 1e-3) / 1e9
+    return {"workload": "16 coefficient textures 2048^2 4:2:0 (float32 [16,128,128,6,64]), 1920x1080 plane, "
+                        "bilinear", "needed_blocks": needed, "forward_ms": ms_fwd, "backward_ms": ms_bwd,
+            "backward_roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                                  "algorithmic_bytes": bwd_bytes},
+            "forward_achieved_gbs": fwd_bytes / (ms_fwd * 1e-3) / 1e9}
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     import paper_2510_08166_gb300 as jt
@@ -342,6 +427,9 @@ def run_gpu(args, rank, world, local_rank):
         }
         if tuned:
             line["tuning"] = tuned
+        if not args.no_extra:
+            line["batched_views"] = run_views(ctx, ts, jt, dev, flush, stream, 20)
+            line["adjoint"] = run_adjoint(jt, dev, flush, stream, 20, peak)
         print(json.dumps(line), flush=True)
     ctx.close()
     return 0
@@ -353,9 +441,11 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="keep the default launch shapes instead of autotuning them first")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--quick", action="store_true", help="timed frames only: no e2e, plain or CPU legs")
+    ap.add_argument("--no-extra", action="store_true", help="skip the batched-views and adjoint measurements")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
