@@ -8,13 +8,14 @@
 //    a time from a device counter, so uneven MCU sizes balance dynamically and the count
 //    never goes to the host. Small M gives many warps for frames with few needed MCUs
 //    (latency hiding); large M amortises per-warp overhead for full decodes;
-//  * entropy phase: lane m < M runs MCU m's serial entropy chain over all its data units —
-//    a 64-bit bit buffer refilled from a two-word prefetch queue of aligned 32-bit loads,
-//    one 10-bit first-level LUT lookup per symbol in shared memory whose entry usually
-//    carries the decoded value (codes longer than 10 bits take a short MAXCODE walk) —
-//    and writes the quantised coefficients in zig-zag order into a per-warp buffer
-//    coef[du][k][m] (int16). Nothing but the LUT and the stream is read on this serial
-//    chain: dequantisation waits for the IDCT phase;
+//  * entropy phase: lane m < M runs MCU m's serial entropy chain over all its data units
+//    from a byte-swapped copy of its words staged in shared memory (a per-warp pool shared
+//    out by a prefix sum). Per symbol: one funnel shift of a two-word window, one 10-bit
+//    LUT read (16-bit entries: code length, value size, run), the value cut from the same
+//    window without a branch, and a select to advance the window; codes longer than 10
+//    bits take a second-level table. The quantised coefficients go in zig-zag order into a
+//    per-warp buffer coef[du][k][m] (int16). Nothing but the LUT and the stream is read on
+//    this serial chain: dequantisation waits for the IDCT phase;
 //  * IDCT phase: all 32 lanes share the 8x8 integer IDCTs of the warp's 6M data units; for
 //    each column index u (then row index y) in turn, every lane transforms that column of
 //    one or more data units, so all zig-zag positions are compile-time constants. Columns
@@ -70,162 +71,125 @@ __device__ __forceinline__ void idct8(const int in[8], int out[8]) {
 __device__ __forceinline__ int sat16(int v) { return min(32767, max(-32768, v)); }
 __device__ __forceinline__ uint32_t clamp255(int v) { return (uint32_t)min(255, max(0, v)); }
 
-// Words of an MCU's entropy-coded data copied to shared memory before its serial decode.
-// Random loads from HBM take thousands of cycles and would otherwise sit on the serial
-// chain once per refill; staging issues them all at once (one latency per work chunk).
-constexpr int kStageWords = 64;  // 256 B per MCU; longer MCUs read their tail from global memory
+// Words of the MCUs' entropy-coded data copied to shared memory before their serial decode
+// (random loads from HBM take thousands of cycles and would otherwise sit on the serial
+// chain once per word). A warp has kStageWords words per MCU as one pool, shared out by a
+// prefix sum over its lanes, so a long MCU can use what short ones leave. Words are stored
+// big-endian-swapped; a lane whose MCU does not fit reads the rest from global memory.
+constexpr int kStageWords = 64;
 
 constexpr int kPixStride = 97;  // words per MCU: Y 64 + Cb 16 + Cr 16, +1 pad
 
 // Shared memory of one warp: coefficients [6][64][M] int16 (zig-zag order), pixels
 // [M][97] words, quantisation tables [M][2][64] uint16 (zig-zag order), per-MCU cache
-// offset and descriptor bits, staged entropy-coded words [M][kStageWords].
+// offset and descriptor bits, staged entropy-coded words [M * kStageWords].
 __host__ __device__ constexpr size_t warp_smem(int M) {
   return (size_t)6 * 64 * M * 2 + (size_t)M * kPixStride * 4 + (size_t)M * 256 + (size_t)M * 8 +
          (size_t)M * kStageWords * 4;
 }
 
-__device__ __forceinline__ uint32_t lds_u32(uint32_t saddr) {
-  uint32_t v;
-  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(saddr));
-  return v;
-}
+__device__ __forceinline__ uint32_t bswap(uint32_t w) { return __byte_perm(w, 0, 0x0123); }
 
-// Bit reader: a 64-bit window (hi:lo, big-endian words) read at bit `pos` of hi with one
-// funnel shift, and a queue of the next three raw words. Words come from the lane's staged
-// copy in shared memory (words [base, base + nstage)), else from global memory.
-struct BitReader {
-  uint32_t hi, lo;
-  uint32_t pos;         // bit offset into hi, < 32 after refill()
-  uint32_t q0, q1, q2;  // raw (as loaded) next words
-  uint32_t wp;          // next word to request
-  const uint32_t* words;
-  uint32_t nwords;
-  uint32_t base, nstage, stage_sa;
-
-  __device__ __forceinline__ uint32_t fetch() {
-    const uint32_t i = wp - base;
-    uint32_t w;
-    if (i < nstage)
-      w = lds_u32(stage_sa + i * 4u);
-    else
-      w = wp < nwords ? __ldg(words + wp) : 0u;
-    ++wp;
-    return w;
+// Stream word i (relative to the lane's first staged word): from the staged copy when it is
+// there, else from global memory (past the end of the stream: 0).
+struct Words {
+  const uint32_t* st;     // staged, byte-swapped
+  uint32_t nst;           // words staged
+  const uint32_t* gw;     // stream words from the first staged word on
+  uint32_t ngw;           // readable words from gw on
+  __device__ __forceinline__ uint32_t operator()(uint32_t i) const {
+    if (i < nst) return st[i];
+    return i < ngw ? bswap(__ldg(gw + i)) : 0u;
   }
-  __device__ __forceinline__ static uint32_t be(uint32_t w) { return __byte_perm(w, 0, 0x0123); }
-  __device__ __forceinline__ void init(uint32_t bitpos) {
-    wp = bitpos >> 5;
-    hi = be(fetch());
-    lo = be(fetch());
-    q0 = fetch();
-    q1 = fetch();
-    q2 = fetch();
-    pos = bitpos & 31;
-  }
-  // afterwards the window holds at least 33 unread bits (a symbol needs at most 16 + 11)
-  __device__ __forceinline__ void refill() {
-    if (pos >= 32) {
-      hi = lo;
-      lo = be(q0);
-      q0 = q1;
-      q1 = q2;
-      q2 = fetch();
-      pos -= 32;
-    }
-  }
-  // the next 32 bits
-  __device__ __forceinline__ uint32_t peek() const { return __funnelshift_l(lo, hi, pos); }
-  // bit position of the next unread bit in the stream
-  __device__ __forceinline__ uint64_t position() const { return (uint64_t)(wp - 5) * 32 + pos; }
 };
 
-// Slow path of a symbol (slow LUT entry): a code longer than kLutBits (found by the
-// MAXCODE walk) or value bits beyond the LUT window. Cuts code and value bits from the
-// 32-bit window w (at most 16 + 11 bits) and returns the equivalent fast entry, or
-// kLutSlow for a code that matches nothing or a symbol invalid for the table's class.
-__device__ __noinline__ uint32_t slow_symbol(const HuffTable* t, uint32_t w, uint32_t e, bool dc) {
-  uint32_t L = e & 31, sym = (e >> 20) & 255;
-  if (L == 0) {
-    const uint32_t top = w >> 16;
+// Symbol entry of a code longer than kLutBits, or 0 for an invalid code or symbol: the
+// second-level table when the table has one, else the MAXCODE walk (T.81 F.2.2.3).
+__device__ __noinline__ uint32_t long_symbol(const HuffTable* t, uint32_t w, bool dc) {
+  const uint32_t top = w >> 16;
+  const uint32_t j = top - t->first16;
+  if (j < t->n2) return t->lut2[j];
 #pragma unroll 1
-    for (int l = kLutBits + 1; l <= 16; ++l) {
-      const int code = (int)(top >> (16 - l));
-      if (code <= t->maxcode[l]) {
-        const int vi = code + t->valoff[l];
-        if (vi < 0 || vi > 255) return kLutSlow;
-        sym = t->vals[vi];
-        L = (uint32_t)l;
-        break;
-      }
+  for (int l = kLutBits + 1; l <= 16; ++l) {
+    const int code = (int)(top >> (16 - l));
+    if (code <= t->maxcode[l]) {
+      const int vi = code + t->valoff[l];
+      if (vi < 0 || vi > 255) return 0;
+      const uint32_t sym = t->vals[vi];
+      const uint32_t r = dc ? 0 : sym >> 4, s = dc ? sym : sym & 15;
+      if (s > (dc ? 11u : 10u)) return 0;
+      if (!dc && s == 0) return r == 0 ? huff_entry(l, 0, kRunEob) : (r == 15 ? huff_entry(l, 0, 15) : 0u);
+      return huff_entry(l, s, r);
     }
-    if (L == 0) return kLutSlow;
   }
-  const uint32_t r = dc ? 0 : sym >> 4, s = dc ? sym : sym & 15;
-  if (s > (dc ? 11u : 10u)) return kLutSlow;
-  if (!dc && s == 0) {
-    if (r == 0) return lut_fast(L, 64, 63, false, 0);   // end of block
-    if (r == 15) return lut_fast(L, 16, 15, false, 0);  // zero run of 16
-    return kLutSlow;
-  }
-  const uint32_t bits = s ? (w << L) >> (32 - s) : 0u;
-  const int v = s ? ((int)bits - ((bits < (1u << (s - 1))) ? (int)((1u << s) - 1u) : 0)) : 0;
-  return dc ? lut_fast(L + s, 1, 0, false, v) : lut_fast(L + s, r + 1, r, true, v);
+  return 0;
 }
 
 // Entropy-decodes all data units of one MCU into coef[(du * 64 + k) * M] (quantised, zig-zag
-// k; the buffer must be zero on entry). One symbol per loop iteration. The common symbol —
-// an AC value, end of block, zero run or DC difference whose code and value bits fit the
-// 10-bit window — is one LUT read and a fixed straight sequence: consume, (DC: add the
-// component's predictor), store at k + offset, advance k. hs: the lane's table set; hs_sa:
-// its shared-memory address when it is the staged set, else 0 (generic reads).
-// Returns false on an invalid coding.
+// k; the buffer must be zero on entry). One symbol per iteration, on a short dependent
+// chain: a funnel shift cuts the next 32 bits from the two-word window (hi:lo), one LUT
+// read gives (l, s, r), the s value bits are cut from the same window (T.81 EXTEND without
+// a branch), and the window advances by a select; the next stream word is read ahead. The
+// move to the next data unit (predictor save/restore, table choice) is also branch-free.
+// hs: the lane's tables (shared or global memory). Returns the bit position after the MCU
+// relative to the first staged word, or 0xFFFFFFFF on an invalid coding.
 template <int M>
-__device__ __forceinline__ bool decode_mcu(BitReader& br, const HuffTable* hs, uint32_t hs_sa, int ndu, int16_t& p0,
-                                           int16_t& p1, int16_t& p2, int16_t* coef) {
-  int du = 0, k = 0, comp = 0;
-  int pc = p0;  // DC predictor of the current data unit's component
-  uint32_t dct = 0;  // table index of the component's DC table (0 luma, 2 chroma)
+__device__ __forceinline__ uint32_t decode_mcu(const Words& W, uint32_t bit0, const HuffTable* hs, int ndu,
+                                               int16_t& p0, int16_t& p1, int16_t& p2, int16_t* coef) {
+  uint32_t widx = bit0 >> 5, pos = bit0 & 31;
+  uint32_t hi = W(widx), lo = W(widx + 1), nx = W(widx + 2);
+  int du = 0, k = 0, comp = 0, pc = p0, q0 = p0, q1 = p1, q2 = p2;
+  uint32_t dct = 0, boff = 0;
   bool bad = false;
-  int16_t* blk = coef;
 #pragma unroll 1
   for (int it = 0; it < 64 * 6; ++it) {  // at most 64 symbols per data unit
-    br.refill();
-    const uint32_t w = br.peek();
+    const uint32_t w = __funnelshift_l(lo, hi, pos);
     const bool dc = k == 0;
-    const uint32_t ti = dct + (dc ? 0u : 1u);
-    const uint32_t li = w >> (32 - kLutBits);
-    uint32_t e = hs_sa ? lds_u32(hs_sa + ti * (uint32_t)sizeof(HuffTable) + li * 4u) : hs[ti].lut[li];
-    if (e & kLutSlow) {
-      e = slow_symbol(hs + ti, w, e, dc);
-      if (e & kLutSlow) return false;
+    const HuffTable* t = hs + dct + (dc ? 0u : 1u);
+    uint32_t e = t->lut[w >> (32 - kLutBits)];
+    if (e == 0) {
+      e = long_symbol(t, w, dc);
+      if (e == 0) {
+        bad = true;
+        break;
+      }
     }
-    const uint32_t nb = e & 31, adv = (e >> 5) & 127, sofs = (e >> 12) & 63;
-    const bool chk = (e >> 18) & 1;
-    int v = (int)e >> 20;
-    br.pos += nb;
+    const uint32_t l = e & 31u, sz = (e >> 5) & 15u, r = e >> 9;
+    const uint32_t tw = w << l;
+    // EXTEND: the s bits after the code; a leading 0 bit makes the value negative
+    int v = (int)__funnelshift_l(tw, 0u, sz) + (int)(~((int)tw >> 31) & (int)(1u - (1u << sz)));
+    pos += l + sz;
+    const bool step = pos >= 32;
+    hi = step ? lo : hi;
+    lo = step ? nx : lo;
+    pos = step ? pos - 32 : pos;
+    widx += step ? 1u : 0u;
+    nx = W(widx + 2);
     if (dc) {
       pc = (int16_t)(uint16_t)(pc + v);  // DC values wrap modulo 2^16
       v = pc;
     }
-    const int kst = k + (int)sofs;
-    bad |= chk && kst > 63;
-    blk[min(kst, 63) * M] = (int16_t)v;
-    k += (int)adv;
-    if (k >= 64) {  // data unit done
-      if (bad) return false;
-      if (comp == 0) p0 = (int16_t)pc;
-      if (comp == 1) p1 = (int16_t)pc;
-      if (comp == 2) p2 = (int16_t)pc;
-      if (++du == ndu) return true;
-      comp = du < ndu - 2 ? 0 : (du == ndu - 2 ? 1 : 2);
-      pc = comp == 0 ? p0 : (comp == 1 ? p1 : p2);
-      dct = comp == 0 ? 0u : 2u;
-      blk += 64 * M;
-      k = 0;
-    }
+    const int kst = k + (int)r;
+    bad |= sz != 0 && kst > 63;
+    coef[(boff + (uint32_t)min(kst, 63)) * M] = (int16_t)v;
+    k += (int)r + 1;
+    const bool done = k >= 64;  // data unit complete
+    q0 = done && comp == 0 ? pc : q0;
+    q1 = done && comp == 1 ? pc : q1;
+    q2 = done && comp == 2 ? pc : q2;
+    du += done ? 1 : 0;
+    const int cn = du < ndu - 2 ? 0 : (du == ndu - 2 ? 1 : 2);
+    pc = done ? (cn == 0 ? q0 : (cn == 1 ? q1 : q2)) : pc;
+    comp = cn;
+    dct = cn ? 2u : 0u;
+    boff += done ? 64u : 0u;
+    k = done ? 0 : k;
+    if (du == ndu || bad) break;
   }
-  return false;
+  p0 = (int16_t)q0;
+  p1 = (int16_t)q1;
+  p2 = (int16_t)q2;
+  return (bad || du != ndu) ? 0xFFFFFFFFu : widx * 32 + pos;
 }
 
 __device__ __forceinline__ uint32_t ycc_pixel(uint32_t Y, int ro, int go, int bo) {
@@ -297,8 +261,9 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
     d0 = __shfl_sync(0xFFFFFFFFu, d0, 0);
     int ndu = 0;
     bool s420 = true, store = false, bad = false;
-    uint32_t off = 0, nbits = 0, qset = 0;
-    BitReader br;
+    uint32_t off = 0, nbits = 0, qset = 0, bitpos = 0, w0 = 0, want = 0;
+    const uint32_t* words = nullptr;
+    uint32_t nwords = 0;
     int16_t pr0 = 0, pr1 = 0, pr2 = 0;
     const HuffTable* hs = sh->t;
     if (act) {
@@ -315,37 +280,46 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
         off = __ldg(a.slot + gid);
         store = off + d.units <= a.cap_units;
         const uint16_t* ix = d.index + (size_t)mcu * 5;
-        const uint32_t bitpos = (uint32_t)__ldg(ix) | ((uint32_t)__ldg(ix + 1) << 16);
+        bitpos = (uint32_t)__ldg(ix) | ((uint32_t)__ldg(ix + 1) << 16);
         pr0 = (int16_t)__ldg(ix + 2);
         pr1 = (int16_t)__ldg(ix + 3);
         pr2 = (int16_t)__ldg(ix + 4);
-        br.words = d.stream;
-        br.nwords = d.nwords;
+        words = d.stream;
+        nwords = d.nwords;
         nbits = d.nbits;
-        // stage the MCU's words (from its first word, 16 B aligned, to the next MCU's start
-        // plus the reader's look-ahead) with independent vector loads
+        // the MCU's words: from its first word (16 B aligned) to the next MCU's start plus
+        // the window's look-ahead (3 words)
         const uint32_t endbit = mcu + 1 < d.nmcu ? ((uint32_t)__ldg(ix + 5) | ((uint32_t)__ldg(ix + 6) << 16)) : d.nbits;
-        const uint32_t w0 = (bitpos >> 5) & ~3u;
-        uint32_t want = (max(endbit, bitpos) >> 5) + 6 - w0;
-        want = min((want + 3) & ~3u, (uint32_t)kStageWords);
-        if (w0 + want > d.nwords) want = d.nwords > w0 ? (d.nwords - w0) & ~3u : 0u;
-        br.base = w0;
-        br.nstage = want;
-        br.stage_sa = (uint32_t)__cvta_generic_to_shared(stage + lane * kStageWords);
-        const uint4* src4 = reinterpret_cast<const uint4*>(d.stream + w0);
-        uint4* dst4 = reinterpret_cast<uint4*>(stage + lane * kStageWords);
-#pragma unroll 1
-        for (uint32_t j = 0; j < want / 4; j += 4) {
-          uint4 r[4];
-#pragma unroll
-          for (int t = 0; t < 4; ++t) r[t] = j + t < want / 4 ? __ldg(src4 + j + t) : make_uint4(0, 0, 0, 0);
-#pragma unroll
-          for (int t = 0; t < 4; ++t)
-            if (j + t < want / 4) dst4[j + t] = r[t];
-        }
-        br.init(bitpos);
+        w0 = (bitpos >> 5) & ~3u;
+        want = (max(endbit, bitpos) >> 5) + 3 - w0;
+        want = (want + 3) & ~3u;
+        if (w0 + want > nwords) want = nwords > w0 ? (nwords - w0) & ~3u : 0u;
         if (d.hset != 0) hs = a.huff[d.hset].t;
         qset = d.qset;
+      }
+    }
+    // share the warp's stage pool out by a prefix sum of the lanes' word counts
+    uint32_t sbeg = want;
+#pragma unroll
+    for (int dlt = 1; dlt < 32; dlt <<= 1) {
+      const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, sbeg, dlt);
+      if (lane >= dlt) sbeg += o;
+    }
+    sbeg -= want;  // exclusive
+    constexpr uint32_t kPool = (uint32_t)kStageWords * M;
+    const uint32_t nst = sbeg >= kPool ? 0u : min(want, kPool - sbeg);
+    if (act) {
+      const uint4* src4 = reinterpret_cast<const uint4*>(words + w0);
+      uint4* dst4 = reinterpret_cast<uint4*>(stage + sbeg);
+#pragma unroll 1
+      for (uint32_t j = 0; j < nst / 4; j += 4) {
+        uint4 r[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) r[t] = j + t < nst / 4 ? __ldg(src4 + j + t) : make_uint4(0, 0, 0, 0);
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if (j + t < nst / 4)
+            dst4[j + t] = make_uint4(bswap(r[t].x), bswap(r[t].y), bswap(r[t].z), bswap(r[t].w));
       }
     }
     if (lane < M) {
@@ -367,9 +341,9 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
 
     // ---- entropy phase: each active lane decodes all data units of its MCU ----
     if (act) {
-      const uint32_t hs_sa = hs == sh->t ? (uint32_t)__cvta_generic_to_shared(sh->t) : 0u;
-      if (!decode_mcu<M>(br, hs, hs_sa, ndu, pr0, pr1, pr2, coef + lane)) bad = true;
-      if (!bad && br.position() > nbits) bad = true;
+      const Words W{stage + sbeg, nst, words + w0, nwords > w0 ? nwords - w0 : 0u};
+      const uint32_t end = decode_mcu<M>(W, bitpos - w0 * 32, hs, ndu, pr0, pr1, pr2, coef + lane);
+      if (end == 0xFFFFFFFFu || (uint64_t)w0 * 32 + end > nbits) bad = true;
       any_bad |= bad;
     }
     __syncwarp();

@@ -147,21 +147,13 @@ void zigzag_natural(int nat[64]) {
     }
 }
 
-int extend_value(uint32_t bits, int s) {  // T.81 EXTEND
-  if (s == 0) return 0;
-  return bits < (1u << (s - 1)) ? (int)bits - (1 << s) + 1 : (int)bits;
-}
-
-// First-level LUT entry for symbol `sym` with a code of length l, followed in the peeked
-// window by the bits `tail` (kLutBits - l bits).
-uint32_t fused_entry(bool dc, int l, uint8_t sym, uint32_t tail) {
+// Table entry of symbol `sym` with a code of length l (0 when the symbol is invalid for the
+// table's class; the decoder's MAXCODE walk then rejects it).
+uint16_t symbol_entry(bool dc, int l, uint8_t sym) {
   const int r = dc ? 0 : sym >> 4, s = dc ? sym : sym & 15;
-  if ((dc && s > 11) || (!dc && s > 10) || (!dc && s == 0 && r != 0 && r != 15)) return lut_slow(l, sym);
-  if (!dc && s == 0) return r == 0 ? lut_fast(l, 64, 63, false, 0) : lut_fast(l, 16, 15, false, 0);
-  if (l + s > kLutBits) return lut_slow(l, sym);
-  const uint32_t bits = s ? (tail >> (kLutBits - l - s)) & ((1u << s) - 1u) : 0u;
-  const int v = extend_value(bits, s);
-  return dc ? lut_fast(l + s, 1, 0, false, v) : lut_fast(l + s, r + 1, r, true, v);
+  if ((dc && s > 11) || (!dc && s > 10) || (!dc && s == 0 && r != 0 && r != 15)) return 0;
+  if (!dc && s == 0) return huff_entry((uint32_t)l, 0, r == 0 ? kRunEob : 15u);
+  return huff_entry((uint32_t)l, (uint32_t)s, (uint32_t)r);
 }
 
 // Canonical decode tables of one Huffman spec (T.81 Annex C code assignment).
@@ -182,7 +174,11 @@ bool build_table(const jt_huff_spec& spec, bool dc, HuffTable& t, std::string& w
     return false;
   }
   std::memcpy(t.vals, spec.vals, n);
-  for (int i = 0; i < kLutSize; ++i) t.lut[i] = lut_slow(0, 0);  // longer codes: MAXCODE walk
+  // left-aligned start of the codes longer than kLutBits = Kraft mass of the shorter ones
+  uint32_t first16 = 0;
+  for (int l = 1; l <= kLutBits; ++l) first16 += (uint32_t)spec.bits[l - 1] << (16 - l);
+  t.first16 = first16;
+  t.n2 = (65536u - first16 <= (uint32_t)kLut2Size && first16 < 65536u) ? 65536u - first16 : 0u;
   int code = 0, k = 0;
   for (int l = 1; l <= 16; ++l) {
     const int nl = spec.bits[l - 1];
@@ -192,9 +188,13 @@ bool build_table(const jt_huff_spec& spec, bool dc, HuffTable& t, std::string& w
     } else {
       t.valoff[l] = k - code;
       for (int i = 0; i < nl; ++i, ++k, ++code) {
+        const uint16_t e = symbol_entry(dc, l, spec.vals[k]);
         if (l <= kLutBits) {
           const int first = code << (kLutBits - l), cnt = 1 << (kLutBits - l);
-          for (int j = 0; j < cnt; ++j) t.lut[first + j] = fused_entry(dc, l, spec.vals[k], (uint32_t)j);
+          for (int j = 0; j < cnt; ++j) t.lut[first + j] = e;
+        } else if (t.n2) {
+          const uint32_t first = ((uint32_t)code << (16 - l)) - first16, cnt = 1u << (16 - l);
+          for (uint32_t j = 0; j < cnt; ++j) t.lut2[first + j] = e;
         }
       }
       t.maxcode[l] = code - 1;

@@ -23,34 +23,35 @@ namespace jt {
 
 constexpr int kLutBits = 10;                 // first-level Huffman LUT: next 10 bits
 constexpr int kLutSize = 1 << kLutBits;
+constexpr int kLut2Size = 1024;              // second-level LUT for longer codes
 constexpr int kStreamPadBytes = 64;          // zero padding after each entropy stream
 constexpr uint32_t kUnitBytes = 256;         // cache unit
 constexpr int kSampling420 = 0, kSampling444 = 1, kSamplingCoef = 2;
 
-// Decode tables of one Huffman spec. lut[i] describes the symbol whose code starts the
-// next kLutBits bits i. Fast entries (code + value bits fit the window):
-//   bits  0..4   bits to consume (code length + value bits)
-//   bits  5..11  coefficient index advance: run + 1 (value), 16 (ZRL), 64 (end of block),
-//                1 (DC difference)
-//   bits 12..17  store offset from the current index: run (value), 15 (ZRL), 63 (end of
-//                block, clamped to the last slot), 0 (DC); ZRL and EOB store a zero into a
-//                slot that must be zero anyway
-//   bit  18      value symbol: the store position must not pass 63
-//   bits 20..31  the decoded (sign-extended) value (0 for ZRL / end of block)
-// Slow entries (bit 19 set) hold the code length in bits 0..4 (0: longer than kLutBits) and
-// the symbol in bits 20..27; value bits follow in the stream (or the code is long), and
-// symbols invalid for the table's class are rejected on the slow path.
-constexpr uint32_t kLutSlow = 1u << 19;
-__host__ __device__ constexpr uint32_t lut_fast(uint32_t nbits, uint32_t adv, uint32_t sofs, bool chk, int value) {
-  return nbits | (adv << 5) | (sofs << 12) | ((chk ? 1u : 0u) << 18) | ((uint32_t)(value & 0xFFF) << 20);
+// Decode tables of one Huffman spec (T.81 Annex C canonical codes). A symbol entry is 16
+// bits: code length l (bits 0..4), value-bit count s (bits 5..8), run r (bits 9..14):
+//   AC value  (r, s)   -> store at k + r, advance k by r + 1
+//   ZRL       (15, 0)  -> advance 16 (the skipped slots are zero)
+//   EOB       (63, 0)  -> advance 64 (store a zero at slot 63, which is zero already)
+//   DC        (0, s)   -> difference, advance 1
+// The s value bits follow the code in the stream; the decoder cuts them from its 32-bit
+// window itself (T.81 EXTEND), so an entry depends on the code alone. 0 = no entry.
+//   lut[i]   entry of the code that starts the next kLutBits bits i (codes up to kLutBits)
+//   lut2[j]  entry of the longer code whose 16-bit left-aligned prefix is first16 + j: in
+//            canonical order the longer codes are the numerically largest, so they occupy
+//            the top n2 of the 65536 16-bit prefixes (n2 <= kLut2Size, else 0 and the
+//            MAXCODE walk of T.81 F.2.2.3 decodes them)
+// Symbols invalid for the table's class (DC category > 11, AC size > 10, AC size 0 with a
+// run other than 0 or 15) get no entry; the MAXCODE walk then rejects them.
+__host__ __device__ constexpr uint16_t huff_entry(uint32_t l, uint32_t s, uint32_t r) {
+  return (uint16_t)(l | (s << 5) | (r << 9));
 }
-__host__ __device__ constexpr uint32_t lut_slow(uint32_t codelen, uint32_t sym) {
-  return codelen | kLutSlow | (sym << 20);
-}
-static_assert(((lut_fast(31, 64, 63, true, -2048) >> 5) & 127) == 64, "advance field holds 64");
-static_assert(((int)lut_fast(31, 64, 63, true, -2048) >> 20) == -2048, "value field is signed 12 bits");
+constexpr uint32_t kRunEob = 63;
 struct HuffTable {
-  uint32_t lut[kLutSize];
+  uint16_t lut[kLutSize];
+  uint16_t lut2[kLut2Size];
+  uint32_t first16;     // 16-bit left-aligned value of the first code longer than kLutBits
+  uint32_t n2;          // entries of lut2 in use (0: no longer codes, or too many)
   int32_t maxcode[17];  // -1 when no code of length l
   int32_t valoff[17];
   uint8_t vals[256];
