@@ -12,9 +12,10 @@
 // launches and copies three words out, all asynchronously on the caller's stream.
 //
 // Scratch: one fixed array per device image, 256 B of frame state then one 64-bit status
-// word per 4096-flag tile, for at most kMaxTiles tiles (16,777,216 flags, 33 KB). Its
-// device address is looked up once per device (cudaGetSymbolAddress, which may load the
-// module lazily and so must first run outside any stream capture) and cached. Because
+// word per scan tile (16384 flags), for at most kMaxTiles = 1024 tiles (16,777,216 flags,
+// 8.4 KB). Its device address is looked up once per device (cudaGetSymbolAddress, which
+// may load the module lazily and so must first run outside any stream capture) and cached.
+// Because
 // the array is shared, two calls in flight at once on one device (two streams, or two
 // host threads without ordering) race on it and give wrong results: callers serialise.
 #include <cuda_runtime.h>
@@ -26,9 +27,9 @@
 namespace jt {
 namespace {
 
-constexpr uint32_t kMaxTiles = 4096;
-constexpr uint32_t kMaxFlags = kMaxTiles * (uint32_t)kScanTile;
-static_assert(kMaxFlags == JT_STATIC_COMPACT_MAX_FLAGS, "header limit matches the scratch size");
+constexpr uint32_t kMaxFlags = JT_STATIC_COMPACT_MAX_FLAGS;
+constexpr uint32_t kMaxTiles = kMaxFlags / (uint32_t)kScanTile;
+static_assert(kMaxTiles * (uint32_t)kScanTile == kMaxFlags, "the limit is a whole number of scan tiles");
 constexpr size_t kStateBytes = 256;  // FrameState, padded so the status words stay 256-B aligned
 static_assert(sizeof(FrameState) <= kStateBytes, "frame state fits its slot");
 
@@ -38,7 +39,7 @@ __device__ __align__(256) uint64_t g_compact_scratch[kStateBytes / 8 + kMaxTiles
 constexpr int kMaxDevices = 64;
 struct DeviceSlot {
   uint8_t* scratch = nullptr;
-  int sm_count = 0;
+  int sm_count = 0;  // resident scan CTAs (SMs x CTAs per SM)
 };
 DeviceSlot g_slots[kMaxDevices];
 std::mutex g_slots_mutex;
@@ -55,7 +56,7 @@ jt_status device_slot(DeviceSlot& out) {
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
       return JT_ERR_CUDA;
-    s.sm_count = sms;
+    s.sm_count = sms * scan_max_ctas_per_sm();  // resident scan CTAs on the device
     s.scratch = static_cast<uint8_t*>(p);
   }
   out = s;
@@ -90,7 +91,7 @@ extern "C" jt_status jt_compact_static(uint8_t* flags, uint32_t n, uint32_t* slo
   a.tile_status = reinterpret_cast<uint64_t*>(d.scratch + kStateBytes);
   a.state = state;
   a.cap_units = 0xFFFFFFFFu;  // no cache behind these slots: only the work list can overflow
-  const int grid = (int)(ntiles < (uint32_t)d.sm_count * 4 ? (ntiles ? ntiles : 1) : (uint32_t)d.sm_count * 4);
+  const int grid = (int)(ntiles < (uint32_t)d.sm_count ? (ntiles ? ntiles : 1) : (uint32_t)d.sm_count);
   launch_scan(a, grid, s);
   if (cudaGetLastError() != cudaSuccess) return JT_ERR_CUDA;
   // totals = {count, units, error bits}: FrameState holds count, units at words 0, 1 and err at word 3

@@ -37,6 +37,7 @@ struct jt_ctx {
   Phase phase = Phase::Idle;
   jt_tuning tuning{};
   int decode_occ[33][17] = {};  // resident decode CTAs per SM by [MCUs per warp][warps per CTA]
+  int scan_per_sm = 1;          // resident compaction CTAs per SM
 
   // textures
   std::vector<DevDesc> descs;
@@ -263,11 +264,14 @@ jt_status sync_tables(jt_ctx* c) {
   return JT_OK;
 }
 
+bool pow2(uint32_t v) { return v && !(v & (v - 1)); }
+
 TexLookup lookup(const jt_ctx* c) {
-  return TexLookup{c->d_descs, c->d_map, reinterpret_cast<const uint4*>(c->d_lrec), c->map_ntex};
+  bool all_p2 = true;
+  for (const DevDesc& d : c->descs) all_p2 &= pow2(d.width) && pow2(d.height);
+  return TexLookup{c->d_descs, c->d_map, reinterpret_cast<const uint4*>(c->d_lrec), c->map_ntex, all_p2 ? 1u : 0u};
 }
 
-bool pow2(uint32_t v) { return v && !(v & (v - 1)); }
 
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
@@ -349,7 +353,7 @@ jt_status enqueue_scan(jt_ctx* c, uint64_t gid_lo, uint64_t gid_hi, cudaStream_t
   a.state = c->state;
   a.cap_units = (uint32_t)c->cap_units;
   const uint32_t ntiles = (a.n + kScanTile - 1) / kScanTile;
-  const int grid = (int)std::max<uint32_t>(1, std::min<uint32_t>(ntiles, (uint32_t)c->sm_count * 4));
+  const int grid = (int)std::max<uint32_t>(1, std::min<uint32_t>(ntiles, (uint32_t)(c->sm_count * c->scan_per_sm)));
   launch_scan(a, grid, s);
   return check_launch(c, "scan");
 }
@@ -505,10 +509,11 @@ jt_status jt_create(jt_ctx** out, int device, uint64_t max_cache_blocks) {
     }
   for (int M : kMcusPerWarp)
     for (int W : kDecodeWarps) c->decode_occ[M][W] = decode_max_ctas_per_sm(W, M);
+  c->scan_per_sm = scan_max_ctas_per_sm();
   cudaGetLastError();
-  c->tuning.decode_mcus_per_warp = 8;
+  c->tuning.decode_mcus_per_warp = 4;  // the autotuner's usual pick for frames of ~10^4 MCUs
   c->tuning.decode_warps = 8;
-  c->tuning.decode_ctas_per_sm = std::max(1, c->decode_occ[8][8]);
+  c->tuning.decode_ctas_per_sm = std::max(1, c->decode_occ[4][8]);
   c->tuning.pixel_threads = 256;
   c->tuning.pixel_ctas_per_sm = 8;
   c->cap_units = max_cache_blocks * 4;

@@ -135,6 +135,7 @@ struct TexLookup {
   const int32_t* desc_map;
   const uint4* levels;  // LevelRec per (tex, level), same indexing as desc_map
   uint32_t map_ntex;
+  uint32_t all_p2;      // every level has power-of-two sides
 };
 
 // ---- launchers (defined in the kernel translation units) ----
@@ -161,9 +162,10 @@ struct ScanArgs {
   uint32_t cap_units;
 };
 constexpr int kScanThreads = 256;
-constexpr int kScanPerThread = 16;
+constexpr int kScanPerThread = 64;  // 4 x 16-byte loads
 constexpr int kScanTile = kScanThreads * kScanPerThread;
 void launch_scan(const ScanArgs& a, int grid, cudaStream_t s);
+int scan_max_ctas_per_sm();  // resident CTAs per SM (the grid must not exceed SMs x this)
 
 struct DecodeArgs {
   const DevDesc* descs;

@@ -18,6 +18,8 @@
 // gid_base + MCU (Sec. 4.6).
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "jt_internal.cuh"
 
 namespace jt {
@@ -75,6 +77,7 @@ struct QuadLevels {
   Lvl shared;
 };
 
+// Warp-collective: all 32 lanes must call it.
 __device__ __forceinline__ void quad_levels(const TexLookup& tl, int n, const uint32_t t[4], const uint32_t m[4],
                                             int only_tex, QuadLevels& q) {
   uint32_t k0 = kNoKey;
@@ -93,24 +96,66 @@ __device__ __forceinline__ void quad_levels(const TexLookup& tl, int n, const ui
   if (q.uniform) q.shared = load_level(tl, kw);
 }
 
-__device__ __forceinline__ int wrap(int a, int w, bool pow2) { return pow2 ? (a & (w - 1)) : floor_mod_i(a, w); }
-
-__device__ __forceinline__ void nearest_texel(float u, float v, const Lvl& L, int& x, int& y) {
-  x = wrap(__float2int_rd(__fmul_rn(u, L.wf)), L.w, L.wp2);  // cvt.rmi saturates out-of-range values
-  y = wrap(__float2int_rd(__fmul_rn(v, L.hf)), L.h, L.hp2);
+// Floor-mod of a texel coordinate; P2: the side is a power of two (a mask). The choice is
+// made once per quad (warp-uniform), so the division-free path costs nothing extra.
+template <bool P2>
+__device__ __forceinline__ int wrap(int a, int w) {
+  if (P2) return a & (w - 1);
+  return floor_mod_i(a, w);
 }
 
+template <bool P2>
+__device__ __forceinline__ void nearest_texel(float u, float v, const Lvl& L, int& x, int& y) {
+  x = wrap<P2>(__float2int_rd(__fmul_rn(u, L.wf)), L.w);  // cvt.rmi saturates out-of-range values
+  y = wrap<P2>(__float2int_rd(__fmul_rn(v, L.hf)), L.h);
+}
+
+template <bool P2>
 __device__ __forceinline__ void bilinear_taps(float u, float v, const Lvl& L, int& xa, int& xb, int& ya, int& yb,
                                               float& fx, float& fy) {
   const float xs = __fsub_rn(__fmul_rn(u, L.wf), 0.5f);
   const float ys = __fsub_rn(__fmul_rn(v, L.hf), 0.5f);
-  const float x0 = floorf(xs), y0 = floorf(ys);
-  fx = __fsub_rn(xs, x0);
-  fy = __fsub_rn(ys, y0);
-  xa = wrap(__float2int_rd(x0), L.w, L.wp2);
-  ya = wrap(__float2int_rd(y0), L.h, L.hp2);
+  fx = __fsub_rn(xs, floorf(xs));
+  fy = __fsub_rn(ys, floorf(ys));
+  xa = wrap<P2>(__float2int_rd(xs), L.w);  // = floor(xs), saturated like floor then convert
+  ya = wrap<P2>(__float2int_rd(ys), L.h);
   xb = xa + 1 == L.w ? 0 : xa + 1;
   yb = ya + 1 == L.h ? 0 : ya + 1;
+}
+
+// Calls f(P2, L, i) for the quad's pixels i = 0..3 with the level record of each, P2 a
+// std::integral_constant telling whether both sides may be wrapped with a mask: loaded once
+// when the warp's row segment shares one level (the common case), else per pixel. P2 is
+// decided per warp, so only one of the two instantiations runs. Warp-collective: all 32
+// lanes must call it (lanes without pixels have empty keys).
+template <typename F>
+__device__ __forceinline__ void for_quad_pixels(const TexLookup& tl, const QuadLevels& q, F&& f) {
+  if (q.uniform) {
+    if (q.shared.wp2 && q.shared.hp2) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) f(std::true_type{}, q.shared, i);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) f(std::false_type{}, q.shared, i);
+    }
+  } else {
+    // levels differ within the row segment: the mask wrap still applies when every pixel's
+    // level has power-of-two sides (known for the whole context, else one info word per
+    // pixel and a vote)
+    bool p2 = true;
+    if (!tl.all_p2) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (q.key[i] < kNoKey - 1) p2 &= ((__ldg(&tl.levels[q.key[i]].z) >> 28) & 3u) == 3u;
+    }
+    if (__all_sync(0xFFFFFFFFu, p2)) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) f(std::true_type{}, load_level(tl, q.key[i]), i);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) f(std::false_type{}, load_level(tl, q.key[i]), i);
+    }
+  }
 }
 
 // Locates the view of global tile `tile` (views are few and sorted by tile_begin).
@@ -185,31 +230,11 @@ __global__ void k_mark(const __grid_constant__ MarkArgs a) {
   bool missing = false;
   // flags gid g unless this CTA already did (racy by design: a duplicate store writes the
   // same byte)
-  auto flag = [&](bool on, uint32_t g, uint8_t units) {
+  auto flag = [&](uint32_t g, uint32_t units) {
     uint32_t* e = &seen[(g ^ (g >> 10)) & (kSeen - 1)];
-    if (on && *e != g) {
+    if (*e != g) {
       *e = g;
-      a.flags[g] = units;
-    }
-  };
-  auto pixel = [&](const Lvl& L, uint32_t key, float u, float v) {
-    const bool ok = key < kNoKey - 1 && L.w != 0 && ((L.sampling == kSamplingCoef) == (a.coef_mode != 0));
-    missing |= key != kNoKey && !ok;
-    const uint8_t units = (uint8_t)L.units;
-    if (FILTER == JT_FILTER_NEAREST) {
-      int x, y;
-      nearest_texel(u, v, L, x, y);
-      flag(ok, L.gid_base + (x >> L.shift) + (y >> L.shift) * L.mcus_x, units);
-    } else {
-      int xa, xb, ya, yb;
-      float fx, fy;
-      bilinear_taps(u, v, L, xa, xb, ya, yb, fx, fy);
-      const int mxa = xa >> L.shift, mxb = xb >> L.shift;
-      const int mya = ya >> L.shift, myb = yb >> L.shift;
-      flag(ok, L.gid_base + mxa + mya * L.mcus_x, units);
-      flag(ok && mxb != mxa, L.gid_base + mxb + mya * L.mcus_x, units);  // footprint straddles MCUs
-      flag(ok && myb != mya, L.gid_base + mxa + myb * L.mcus_x, units);
-      flag(ok && mxb != mxa && myb != mya, L.gid_base + mxb + myb * L.mcus_x, units);
+      a.flags[g] = (uint8_t)units;
     }
   };
   for_each_quad(a.views, [&](const View& V, int y, int x) {
@@ -218,13 +243,32 @@ __global__ void k_mark(const __grid_constant__ MarkArgs a) {
     const int n = load_px4(V, y, x, u, v, t, m);
     QuadLevels q;
     quad_levels(a.tl, n, t, m, a.only_tex, q);
-    if (q.uniform) {
-#pragma unroll
-      for (int i = 0; i < 4; ++i) pixel(q.shared, q.key[i], u[i], v[i]);
-    } else {
-#pragma unroll
-      for (int i = 0; i < 4; ++i) pixel(load_level(a.tl, q.key[i]), q.key[i], u[i], v[i]);
-    }
+    for_quad_pixels(a.tl, q, [&](auto p2, const Lvl& L, int i) {
+      constexpr bool P2 = decltype(p2)::value;
+      const uint32_t key = q.key[i];
+      const bool ok = key < kNoKey - 1 && L.w != 0 && ((L.sampling == kSamplingCoef) == (a.coef_mode != 0));
+      missing |= key != kNoKey && !ok;
+      if (!ok) return;
+      if (FILTER == JT_FILTER_NEAREST) {
+        int tx, ty;
+        nearest_texel<P2>(u[i], v[i], L, tx, ty);
+        flag(L.gid_base + (tx >> L.shift) + (ty >> L.shift) * L.mcus_x, L.units);
+      } else {
+        int xa, xb, ya, yb;
+        float fx, fy;
+        bilinear_taps<P2>(u[i], v[i], L, xa, xb, ya, yb, fx, fy);
+        const int mxa = xa >> L.shift, mxb = xb >> L.shift;
+        const int mya = ya >> L.shift, myb = yb >> L.shift;
+        const uint32_t row_a = L.gid_base + mya * L.mcus_x;
+        flag(row_a + mxa, L.units);
+        if (mxb != mxa) flag(row_a + mxb, L.units);  // the footprint straddles MCUs (rare)
+        if (myb != mya) {
+          const uint32_t row_b = L.gid_base + myb * L.mcus_x;
+          flag(row_b + mxa, L.units);
+          if (mxb != mxa) flag(row_b + mxb, L.units);
+        }
+      }
+    });
   });
   if (missing) atomicOr(&a.state->err, JT_DEVERR_MISSING);
 }
@@ -262,58 +306,14 @@ __global__ void k_colorize(const __grid_constant__ ColorizeArgs a) {
   uint32_t last_gid = kNoGid, last_off = 0;  // slot of the last MCU looked up
   const uint32_t* cache = reinterpret_cast<const uint32_t*>(a.cache);
   // cache-unit offset of gid g (0 and `bad` when it would read past the cache)
-  auto slot = [&](bool on, uint32_t g, uint32_t units) -> uint32_t {
-    uint32_t off = last_off;
-    if (on && g != last_gid) off = __ldg(&a.slot[g]);
-    const bool fits = off + units <= a.cap_units;
-    bad |= on && !fits;
-    return fits ? off : 0u;
-  };
-  auto pixel = [&](const Lvl& L, uint32_t key, float u, float v) -> uint32_t {
-    const bool ok = key < kNoKey - 1 && L.w != 0 && L.sampling != kSamplingCoef;
-    missing |= key != kNoKey && !ok;
-    const int mwm = (1 << L.shift) - 1;
-    if (FILTER == JT_FILTER_NEAREST) {
-      int x, y;
-      nearest_texel(u, v, L, x, y);
-      const uint32_t g = L.gid_base + (x >> L.shift) + (y >> L.shift) * L.mcus_x;
-      const uint32_t off = slot(ok, g, L.units);
-      if (ok) {
-        last_gid = g;
-        last_off = off;
-      }
-      const uint32_t c = ok ? __ldg(cache + (size_t)off * (kUnitBytes / 4) + (((y & mwm) << L.shift) | (x & mwm)))
-                            : 0u;
-      return ok ? c : 0xFF000000u;
-    } else {
-      int xa, xb, ya, yb;
-      float fx, fy;
-      bilinear_taps(u, v, L, xa, xb, ya, yb, fx, fy);
-      const int mxa = xa >> L.shift, mxb = xb >> L.shift;
-      const int mya = ya >> L.shift, myb = yb >> L.shift;
-      const uint32_t g00 = L.gid_base + mxa + mya * L.mcus_x;
-      const uint32_t o00 = slot(ok, g00, L.units);
-      if (ok) {
-        last_gid = g00;
-        last_off = o00;
-      }
-      const bool sx = mxb != mxa, sy = myb != mya;  // footprint straddles MCUs (rare)
-      uint32_t o10 = o00, o01 = o00, o11 = o00;
-      if (ok && sx) o10 = slot(true, L.gid_base + mxb + mya * L.mcus_x, L.units);
-      if (ok && sy) o01 = slot(true, L.gid_base + mxa + myb * L.mcus_x, L.units);
-      if (ok && sx && sy) o11 = slot(true, L.gid_base + mxb + myb * L.mcus_x, L.units);
-      o11 = sx && sy ? o11 : (sx ? o10 : o01);
-      const int ia = (ya & mwm) << L.shift, ib = (yb & mwm) << L.shift;
-      const int ja = xa & mwm, jb = xb & mwm;
-      uint32_t c00 = 0, c10 = 0, c01 = 0, c11 = 0;
-      if (ok) {
-        c00 = __ldg(cache + (size_t)o00 * (kUnitBytes / 4) + (ia | ja));
-        c10 = __ldg(cache + (size_t)o10 * (kUnitBytes / 4) + (ia | jb));
-        c01 = __ldg(cache + (size_t)o01 * (kUnitBytes / 4) + (ib | ja));
-        c11 = __ldg(cache + (size_t)o11 * (kUnitBytes / 4) + (ib | jb));
-      }
-      return ok ? blend(c00, c10, c01, c11, fx, fy) : 0xFF000000u;
+  auto slot = [&](uint32_t g, uint32_t units) -> uint32_t {
+    if (g != last_gid) {
+      last_gid = g;
+      last_off = __ldg(&a.slot[g]);
     }
+    const bool fits = last_off + units <= a.cap_units;
+    bad |= !fits;
+    return fits ? last_off : 0u;
   };
   for_each_quad(a.views, [&](const View& V, int y, int x) {
     float u[4], v[4];
@@ -322,13 +322,43 @@ __global__ void k_colorize(const __grid_constant__ ColorizeArgs a) {
     QuadLevels q;
     quad_levels(a.tl, n, t, m, a.only_tex, q);
     uint32_t px[4];
-    if (q.uniform) {
-#pragma unroll
-      for (int i = 0; i < 4; ++i) px[i] = pixel(q.shared, q.key[i], u[i], v[i]);
-    } else {
-#pragma unroll
-      for (int i = 0; i < 4; ++i) px[i] = pixel(load_level(a.tl, q.key[i]), q.key[i], u[i], v[i]);
-    }
+    for_quad_pixels(a.tl, q, [&](auto p2, const Lvl& L, int i) {
+      constexpr bool P2 = decltype(p2)::value;
+      const uint32_t key = q.key[i];
+      const bool ok = key < kNoKey - 1 && L.w != 0 && L.sampling != kSamplingCoef;
+      missing |= key != kNoKey && !ok;
+      px[i] = 0xFF000000u;  // empty pixel
+      if (!ok) return;
+      const int mwm = (1 << L.shift) - 1;
+      if (FILTER == JT_FILTER_NEAREST) {
+        int tx, ty;
+        nearest_texel<P2>(u[i], v[i], L, tx, ty);
+        const uint32_t off = slot(L.gid_base + (tx >> L.shift) + (ty >> L.shift) * L.mcus_x, L.units);
+        px[i] = __ldg(cache + (size_t)off * (kUnitBytes / 4) + (((ty & mwm) << L.shift) | (tx & mwm)));
+      } else {
+        int xa, xb, ya, yb;
+        float fx, fy;
+        bilinear_taps<P2>(u[i], v[i], L, xa, xb, ya, yb, fx, fy);
+        const int mxa = xa >> L.shift, mxb = xb >> L.shift;
+        const int mya = ya >> L.shift, myb = yb >> L.shift;
+        const uint32_t row_a = L.gid_base + mya * L.mcus_x;
+        const uint32_t o00 = slot(row_a + mxa, L.units);
+        uint32_t o10 = o00, o01 = o00, o11 = o00;
+        if (mxb != mxa || myb != mya) {  // the footprint straddles MCUs (rare)
+          const uint32_t row_b = L.gid_base + myb * L.mcus_x;
+          o10 = slot(row_a + mxb, L.units);
+          o01 = slot(row_b + mxa, L.units);
+          o11 = slot(row_b + mxb, L.units);
+        }
+        const int ia = (ya & mwm) << L.shift, ib = (yb & mwm) << L.shift;
+        const int ja = xa & mwm, jb = xb & mwm;
+        const uint32_t c00 = __ldg(cache + (size_t)o00 * (kUnitBytes / 4) + (ia | ja));
+        const uint32_t c10 = __ldg(cache + (size_t)o10 * (kUnitBytes / 4) + (ia | jb));
+        const uint32_t c01 = __ldg(cache + (size_t)o01 * (kUnitBytes / 4) + (ib | ja));
+        const uint32_t c11 = __ldg(cache + (size_t)o11 * (kUnitBytes / 4) + (ib | jb));
+        px[i] = blend(c00, c10, c01, c11, fx, fy);
+      }
+    });
     if (n == 0) return;
     bool write[4];
 #pragma unroll
@@ -361,6 +391,7 @@ struct FloatTaps {
 
 // Taps of one pixel; ok = false (and `missing`/`over` updated) when the pixel is empty,
 // names a texture that is not a coefficient texture, or a tap's tile is past the capacity.
+template <bool P2>
 __device__ __forceinline__ FloatTaps float_taps(const FloatArgs& a, const Lvl& L, uint32_t key, float u, float v,
                                                 bool& missing, bool& over) {
   FloatTaps T;
@@ -368,7 +399,7 @@ __device__ __forceinline__ FloatTaps float_taps(const FloatArgs& a, const Lvl& L
   missing |= key != kNoKey && !T.ok;
   int xa, xb, ya, yb;
   float fx, fy;
-  bilinear_taps(u, v, L, xa, xb, ya, yb, fx, fy);
+  bilinear_taps<P2>(u, v, L, xa, xb, ya, yb, fx, fy);
   const int xs[4] = {xa, xb, xa, xb}, ys[4] = {ya, ya, yb, yb};
   T.w[0] = (1.f - fx) * (1.f - fy);
   T.w[1] = fx * (1.f - fy);
@@ -396,12 +427,14 @@ __global__ void k_float_pixels(const __grid_constant__ FloatArgs a) {
     const int n = load_px4(V, y, x, u, v, t, m);
     QuadLevels q;
     quad_levels(a.tl, n, t, m, -1, q);
-    if (n == 0) return;
+    // every lane goes on to for_quad_pixels (it may vote); lanes without pixels touch no memory
     const uint32_t p0 = (uint32_t)y * (uint32_t)V.width + (uint32_t)x;
     float* fr = a.frame + (size_t)p0 * 3;  // 12 floats of the quad, 16-byte aligned when p0 % 4 == 0
     const bool vec = n == 4 && (V.width & 3) == 0;
     float rgb[12];
-    if (BACKWARD) {
+#pragma unroll
+    for (int i = 0; i < 12; ++i) rgb[i] = 0.f;
+    if (BACKWARD && n > 0) {
       if (vec) {
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
@@ -413,10 +446,8 @@ __global__ void k_float_pixels(const __grid_constant__ FloatArgs a) {
         for (int i = 0; i < 12; ++i) rgb[i] = i < 3 * n ? __ldg(fr + i) : 0.f;
       }
     }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const Lvl L = q.uniform ? q.shared : load_level(a.tl, q.key[i]);
-      const FloatTaps T = float_taps(a, L, q.key[i], u[i], v[i], missing, over);
+    for_quad_pixels(a.tl, q, [&](auto p2, const Lvl& L, int i) {
+      const FloatTaps T = float_taps<decltype(p2)::value>(a, L, q.key[i], u[i], v[i], missing, over);
       if (BACKWARD) {
         if (T.ok) {
 #pragma unroll
@@ -439,8 +470,8 @@ __global__ void k_float_pixels(const __grid_constant__ FloatArgs a) {
         rgb[3 * i + 1] = gg;
         rgb[3 * i + 2] = b;
       }
-    }
-    if (!BACKWARD) {
+    });
+    if (!BACKWARD && n > 0) {
       if (vec) {
 #pragma unroll
         for (int i = 0; i < 3; ++i)

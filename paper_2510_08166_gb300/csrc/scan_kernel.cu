@@ -7,7 +7,7 @@
 // prefix): work[count_prefix] = gid, slot[gid] = units_prefix. The list is therefore in
 // ascending gid order and deterministic. The same pass clears the flags for the next frame.
 //
-// Single pass: decoupled look-back (Merrill & Garland 2016). Each 4096-flag tile
+// Single pass: decoupled look-back (Merrill & Garland 2016). Each 16384-flag tile
 // publishes its aggregate, then a warp of the tile looks back over up to 32 predecessor
 // tiles at a time until it meets an inclusive prefix. The grid is persistent (every CTA
 // resident) and CTAs take tiles in increasing order, so every awaited predecessor is being
@@ -48,24 +48,30 @@ __device__ __forceinline__ void word_stats(uint32_t w, uint32_t& cnt, uint32_t& 
   sum += (w & 255) + ((w >> 8) & 255) + ((w >> 16) & 255) + (w >> 24);
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan(const __grid_constant__ ScanArgs a) {
+__global__ void __launch_bounds__(kScanThreads, 4) k_scan(const __grid_constant__ ScanArgs a) {
   __shared__ uint32_t s_cnt[kScanThreads / 32], s_sum[kScanThreads / 32];
   __shared__ uint32_t s_pre_cnt, s_pre_sum;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t ntiles = (a.n + kScanTile - 1) / kScanTile;
   for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const uint32_t first = tile * kScanTile + tid * kScanPerThread;  // relative to gid_lo
-    uint32_t w[4] = {0, 0, 0, 0};
+    constexpr int kWords = kScanPerThread / 4;
+    uint32_t w[kWords];
     if (first + kScanPerThread <= a.n) {
-      uint4 v = *reinterpret_cast<const uint4*>(a.flags + first);
-      w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+#pragma unroll
+      for (int j = 0; j < kWords / 4; ++j) {
+        const uint4 v = reinterpret_cast<const uint4*>(a.flags + first)[j];
+        w[4 * j] = v.x; w[4 * j + 1] = v.y; w[4 * j + 2] = v.z; w[4 * j + 3] = v.w;
+      }
     } else {
+#pragma unroll
+      for (int j = 0; j < kWords; ++j) w[j] = 0;
       for (int i = 0; i < kScanPerThread; ++i)
         if (first + i < a.n) w[i >> 2] |= (uint32_t)a.flags[first + i] << (8 * (i & 3));
     }
     uint32_t cnt = 0, sum = 0;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) word_stats(w[i], cnt, sum);
+    for (int i = 0; i < kWords; ++i) word_stats(w[i], cnt, sum);
     // block-wide exclusive scan of (cnt, sum)
     uint32_t ic = cnt, is = sum;
 #pragma unroll
@@ -155,7 +161,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const __grid_constant__ S
       }
       // clear for the next frame
       if (first + kScanPerThread <= a.n) {
-        *reinterpret_cast<uint4*>(a.flags + first) = make_uint4(0, 0, 0, 0);
+#pragma unroll
+        for (int j = 0; j < kWords / 4; ++j) reinterpret_cast<uint4*>(a.flags + first)[j] = make_uint4(0, 0, 0, 0);
       } else {
         for (int i = 0; i < kScanPerThread; ++i)
           if (first + i < a.n) a.flags[first + i] = 0;
@@ -192,5 +199,15 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const __grid_constant__ S
 }  // namespace
 
 void launch_scan(const ScanArgs& a, int grid, cudaStream_t s) { k_scan<<<grid, kScanThreads, 0, s>>>(a); }
+
+// Resident scan CTAs per SM: the look-back needs every CTA of the grid running at once.
+int scan_max_ctas_per_sm() {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_scan, kScanThreads, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return n > 0 ? n : 1;
+}
 
 }  // namespace jt
