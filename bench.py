@@ -196,6 +196,22 @@ def run_reference(args, rank, world):
 # GPU arm
 # ---------------------------------------------------------------------------------------
 
+def max_over_ranks(value: float, world: int, device) -> float:
+    """The largest `value` over the replicas (the whole job's time is the slowest rank's)."""
+    if world <= 1:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(units_per_rank: float, world: int, total_ms: float) -> float:
+    """Whole-job throughput of `world` replicas that each processed `units_per_rank` units in
+    at most `total_ms` (weak scaling)."""
+    return world * units_per_rank / (total_ms * 1e-3)
+
+
 def timed(fn, steps, warmup, stream, flush=None):
     """Mean ms of fn() over `steps` CUDA-event-timed calls after `warmup` untimed ones."""
     import torch
@@ -332,11 +348,7 @@ def run_gpu(args, rank, world, local_rank):
     wall = time.perf_counter() - wall0
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in zip(e0, e1)]
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(sum(step_ms)), world, dev)
     ctx.stats()
 
     if args.quick:  # timed frames only (used under the profiler)
@@ -398,7 +410,7 @@ def run_gpu(args, rank, world, local_rank):
     peak, peak_kind = peaks()
     achieved = alg[dom] / (mean[dom] * 1e-3) / 1e9
     frame_ms = total_ms / args.steps
-    value = world * nblocks * args.steps / (total_ms * 1e-3)
+    value = replica_value(nblocks * args.steps, world, total_ms)
     e2e_value = world * nblocks / (statistics.mean(e2e_ms) * 1e-3)
 
     if rank == 0:
