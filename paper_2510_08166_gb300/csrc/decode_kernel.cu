@@ -4,26 +4,26 @@
 //
 // GB300 design (the paper's one 64-thread block per MCU with a 32-lane code compare,
 // Sec. 5.2, is prior art here):
-//  * persistent grid; each warp fetches M work items (M = 4, 8, 16 or 32 MCUs per warp) at
-//    a time from a device counter, so uneven MCU sizes balance dynamically and the count
-//    never goes to the host. Small M gives many warps for frames with few needed MCUs
-//    (latency hiding); large M amortises per-warp overhead for full decodes;
+//  * persistent grid; each warp fetches M work items (M = 4, 8, 16 or 32 MCUs per warp, one
+//    per lane) at a time from a device counter, so uneven MCU sizes balance dynamically and
+//    the count never goes to the host;
 //  * entropy phase: lane m < M runs MCU m's serial entropy chain over all its data units
 //    from a byte-swapped copy of its words staged in shared memory (a per-warp pool shared
 //    out by a prefix sum). Per symbol: one funnel shift of a two-word window, one 10-bit
 //    LUT read (16-bit entries: code length, value size, run), the value cut from the same
 //    window without a branch, and a select to advance the window; codes longer than 10
-//    bits take a second-level table. The quantised coefficients go in zig-zag order into a
+//    bits take one more read in their prefix's 64-entry subtable. The quantised coefficients go in zig-zag order into a
 //    per-warp buffer coef[du][k][m] (int16). Nothing but the LUT and the stream is read on
 //    this serial chain: dequantisation waits for the IDCT phase;
-//  * IDCT phase: all 32 lanes share the 8x8 integer IDCTs of the warp's 6M data units; for
-//    each column index u (then row index y) in turn, every lane transforms that column of
-//    one or more data units, so all zig-zag positions are compile-time constants. Columns
-//    are dequantised on load with the MCU's quantisation table (staged per warp in shared
-//    memory); even/odd butterflies give an exact integer factorisation of the matrix
-//    product of the decode spec; rows of pixels go to a per-MCU shared buffer;
-//  * colour phase: the warp writes each MCU's RGBA8 tile cooperatively (32 lanes x 32 B =
-//    one 1 KiB 4:2:0 tile per step, coalesced).
+//  * IDCT phase: each lane transforms its own MCU, column then row, over the warp's
+//    buffer coef[du][k][m] (lane m at column m, so the warp's accesses are consecutive and
+//    conflict-free); all zig-zag positions are compile-time constants. Columns are
+//    dequantised on load with the MCU's quantisation table (read through L1); even/odd
+//    butterflies give an exact integer factorisation of the matrix product of the decode
+//    spec; the row pass writes each row's pixels in place over the slots it just read;
+//  * colour phase: each lane converts its MCU and writes its tile with 16-byte stores.
+//    The buffers per MCU are 768 B of coefficients plus 128 B of staged words, so up to
+//    seven 32-MCU warps fit on an SM.
 //
 // Decode spec (identical in the oracle): dequantised d = clamp16(q * Q); column pass
 // t = clamp16(floor((sum_v K[y][v] d[v][u] + 2^8) / 2^9)); row pass
@@ -74,18 +74,16 @@ __device__ __forceinline__ uint32_t clamp255(int v) { return (uint32_t)min(255, 
 // Words of the MCUs' entropy-coded data copied to shared memory before their serial decode
 // (random loads from HBM take thousands of cycles and would otherwise sit on the serial
 // chain once per word). A warp has kStageWords words per MCU as one pool, shared out by a
-// prefix sum over its lanes, so a long MCU can use what short ones leave. Words are stored
-// big-endian-swapped; a lane whose MCU does not fit reads the rest from global memory.
-constexpr int kStageWords = 64;
+// prefix sum over its lanes, so a long MCU can use what short ones leave (the mean MCU of a
+// scene needs about a quarter). Words are stored big-endian-swapped; a lane whose MCU does
+// not fit reads the rest from global memory.
+constexpr int kStageWords = 32;
 
-constexpr int kPixStride = 97;  // words per MCU: Y 64 + Cb 16 + Cr 16, +1 pad
-
-// Shared memory of one warp: coefficients [6][64][M] int16 (zig-zag order), pixels
-// [M][97] words, quantisation tables [M][2][64] uint16 (zig-zag order), per-MCU cache
-// offset and descriptor bits, staged entropy-coded words [M * kStageWords].
+// Shared memory of one warp: coefficients [6][64][M] int16 (zig-zag order k, lane m at
+// column m; after the row pass each data unit's slots hold its pixels, see below) and the
+// staged entropy-coded words [M * kStageWords].
 __host__ __device__ constexpr size_t warp_smem(int M) {
-  return (size_t)6 * 64 * M * 2 + (size_t)M * kPixStride * 4 + (size_t)M * 256 + (size_t)M * 8 +
-         (size_t)M * kStageWords * 4;
+  return (size_t)6 * 64 * M * 2 + (size_t)M * kStageWords * 4;
 }
 
 __device__ __forceinline__ uint32_t bswap(uint32_t w) { return __byte_perm(w, 0, 0x0123); }
@@ -103,14 +101,12 @@ struct Words {
   }
 };
 
-// Symbol entry of a code longer than kLutBits, or 0 for an invalid code or symbol: the
-// second-level table when the table has one, else the MAXCODE walk (T.81 F.2.2.3).
-__device__ __noinline__ uint32_t long_symbol(const HuffTable* t, uint32_t w, bool dc) {
+// Symbol entry by the MAXCODE walk (T.81 F.2.2.3), or 0 for an invalid code or a symbol
+// invalid for the table's class. Only codes without a LUT entry come here.
+__device__ __noinline__ uint32_t walk_symbol(const HuffTable* t, uint32_t w, bool dc) {
   const uint32_t top = w >> 16;
-  const uint32_t j = top - t->first16;
-  if (j < t->n2) return t->lut2[j];
 #pragma unroll 1
-  for (int l = kLutBits + 1; l <= 16; ++l) {
+  for (int l = 1; l <= 16; ++l) {
     const int code = (int)(top >> (16 - l));
     if (code <= t->maxcode[l]) {
       const int vi = code + t->valoff[l];
@@ -147,8 +143,10 @@ __device__ __forceinline__ uint32_t decode_mcu(const Words& W, uint32_t bit0, co
     const bool dc = k == 0;
     const HuffTable* t = hs + dct + (dc ? 0u : 1u);
     uint32_t e = t->lut[w >> (32 - kLutBits)];
-    if (e == 0) {
-      e = long_symbol(t, w, dc);
+    if ((e & 31u) == 0) {  // a longer code: its prefix's subtable, else the walk
+      const uint32_t sub = e >> 5;
+      e = sub ? (uint32_t)t->lut2[(sub - 1) * kSubSize + ((w >> (32 - kLutBits - kSubBits)) & (kSubSize - 1))] : 0u;
+      if (e == 0) e = walk_symbol(t, w, dc);
       if (e == 0) {
         bad = true;
         break;
@@ -203,23 +201,13 @@ __device__ __forceinline__ void chroma_offsets(uint32_t cb8, uint32_t cr8, int& 
   bo = (116130 * cb + 32768) >> 16;
 }
 
-__device__ __forceinline__ int find_desc(const DevDesc* descs, int n, uint32_t gid) {
-  int lo = 0, hi = n - 1;
-#pragma unroll 1
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (__ldg(&descs[mid].gid_base) <= gid)
-      lo = mid;
-    else
-      hi = mid - 1;
-  }
-  return lo;
-}
 
-// Word offset of row y of data unit d inside an MCU's pixel buffer, and the row pitch.
-__device__ __forceinline__ int pix_row(int d, int y, bool s420) {
-  if (s420) return d < 4 ? ((d >> 1) * 8 + y) * 4 + (d & 1) * 2 : 64 + (d - 4) * 16 + y * 2;
-  return (d == 0 ? 0 : (d == 1 ? 64 : 80)) + y * 2;
+// Pixels after the row pass, in place: the row pass of data unit d, row y has just read
+// the 8 slots zz_pos(y, 0..7) (no other row reads them) and writes pixels x = 2i, 2i+1 as the
+// low and high byte of slot zz_pos(y, i), i < 4. pixel2(d, y, i) reads that pair.
+template <int M>
+__device__ __forceinline__ uint32_t pixel2(const int16_t* col, int d, int y, int i) {
+  return (uint16_t)col[(d * 64 + zz_pos(y, i)) * M];
 }
 
 template <int M>
@@ -228,12 +216,9 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
   HuffSet* sh = reinterpret_cast<HuffSet*>(smem);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint8_t* wbase = smem + sizeof(HuffSet) + 64 + (size_t)warp * warp_smem(M);
-  int16_t* coef = reinterpret_cast<int16_t*>(wbase);                       // [6][64][M]
-  uint32_t* pix = reinterpret_cast<uint32_t*>(wbase + 6 * 64 * M * 2);     // [M][97]
-  uint16_t* qtab = reinterpret_cast<uint16_t*>(pix + M * kPixStride);      // [M][2][64] zig-zag
-  uint32_t* moff = reinterpret_cast<uint32_t*>(qtab + M * 128);            // [M] cache unit offset
-  uint32_t* minfo = moff + M;  // [M] ndu | 420 << 4 | store << 5 | qset << 8
-  uint32_t* stage = minfo + M;  // [M][kStageWords] entropy-coded words
+  int16_t* coef = reinterpret_cast<int16_t*>(wbase);                    // [6][64][M]
+  uint32_t* stage = reinterpret_cast<uint32_t*>(wbase + 6 * 64 * M * 2);  // [M * kStageWords]
+  int16_t* col = coef + (lane < M ? lane : 0);                          // this lane's MCU
 
   {  // stage Huffman set 0
     const uint4* src = reinterpret_cast<const uint4*>(a.huff);
@@ -252,24 +237,25 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
     base = __shfl_sync(0xFFFFFFFFu, base, 0);
     if (base >= count) break;
 
+    {  // clear the coefficient buffer (768 M bytes)
+      uint4* z = reinterpret_cast<uint4*>(coef);
+#pragma unroll
+      for (int i = lane; i < 48 * M; i += 32) z[i] = make_uint4(0, 0, 0, 0);
+    }
+
     // ---- set-up: lane m < M takes item base + m ----
     const uint32_t item = base + lane;
     bool act = lane < M && item < count;
     const uint32_t gid = act ? __ldg(a.work + item) : 0u;
-    int d0 = 0;  // the first item's level is shared by nearly all lanes (the list is sorted)
-    if (lane == 0) d0 = find_desc(a.descs, (int)a.ndesc, gid);
-    d0 = __shfl_sync(0xFFFFFFFFu, d0, 0);
+    const uint32_t di = act ? __ldg(a.desc_of_gid + gid) : 0u;
     int ndu = 0;
-    bool s420 = true, store = false, bad = false;
-    uint32_t off = 0, nbits = 0, qset = 0, bitpos = 0, w0 = 0, want = 0;
+    bool s420 = true, store = false;
+    uint32_t off = 0, nbits = 0, bitpos = 0, w0 = 0, want = 0, nwords = 0;
     const uint32_t* words = nullptr;
-    uint32_t nwords = 0;
+    const uint16_t* Q = a.quant;  // the MCU's quantisation tables (zig-zag), read through L1
     int16_t pr0 = 0, pr1 = 0, pr2 = 0;
     const HuffTable* hs = sh->t;
-    if (act) {
-      int di = d0;
-      const uint32_t b0 = __ldg(&a.descs[d0].gid_base);
-      if (gid < b0 || gid - b0 >= __ldg(&a.descs[d0].nmcu)) di = find_desc(a.descs, (int)a.ndesc, gid);
+    if (act && di < a.ndesc) {
       const DevDesc d = a.descs[di];
       const uint32_t mcu = gid - d.gid_base;
       if (d.sampling == kSamplingCoef || mcu >= d.nmcu) {
@@ -289,14 +275,17 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
         nbits = d.nbits;
         // the MCU's words: from its first word (16 B aligned) to the next MCU's start plus
         // the window's look-ahead (3 words)
-        const uint32_t endbit = mcu + 1 < d.nmcu ? ((uint32_t)__ldg(ix + 5) | ((uint32_t)__ldg(ix + 6) << 16)) : d.nbits;
+        const uint32_t endbit =
+            mcu + 1 < d.nmcu ? ((uint32_t)__ldg(ix + 5) | ((uint32_t)__ldg(ix + 6) << 16)) : d.nbits;
         w0 = (bitpos >> 5) & ~3u;
         want = (max(endbit, bitpos) >> 5) + 3 - w0;
         want = (want + 3) & ~3u;
         if (w0 + want > nwords) want = nwords > w0 ? (nwords - w0) & ~3u : 0u;
         if (d.hset != 0) hs = a.huff[d.hset].t;
-        qset = d.qset;
+        Q = a.quant + (size_t)d.qset * 128;
       }
+    } else {
+      act = false;
     }
     // share the warp's stage pool out by a prefix sum of the lanes' word counts
     uint32_t sbeg = want;
@@ -318,130 +307,111 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
         for (int t = 0; t < 4; ++t) r[t] = j + t < nst / 4 ? __ldg(src4 + j + t) : make_uint4(0, 0, 0, 0);
 #pragma unroll
         for (int t = 0; t < 4; ++t)
-          if (j + t < nst / 4)
-            dst4[j + t] = make_uint4(bswap(r[t].x), bswap(r[t].y), bswap(r[t].z), bswap(r[t].w));
+          if (j + t < nst / 4) dst4[j + t] = make_uint4(bswap(r[t].x), bswap(r[t].y), bswap(r[t].z), bswap(r[t].w));
       }
     }
-    if (lane < M) {
-      moff[lane] = off;
-      minfo[lane] = act ? ((uint32_t)ndu | (s420 ? 16u : 0u) | (store ? 32u : 0u) | (qset << 8)) : 0u;
-    }
-    {  // clear the coefficient buffer (768 M bytes)
-      uint4* z = reinterpret_cast<uint4*>(coef);
-#pragma unroll
-      for (int i = lane; i < 48 * M; i += 32) z[i] = make_uint4(0, 0, 0, 0);
-    }
     __syncwarp();
-    {  // stage each MCU's quantisation tables (256 B = 16 x 16 B per MCU)
-      const uint4* qsrc = reinterpret_cast<const uint4*>(a.quant);
-      uint4* qdst = reinterpret_cast<uint4*>(qtab);
-#pragma unroll
-      for (int i = lane; i < 16 * M; i += 32) qdst[i] = __ldg(qsrc + (size_t)(minfo[i >> 4] >> 8) * 16 + (i & 15));
-    }
 
     // ---- entropy phase: each active lane decodes all data units of its MCU ----
     if (act) {
       const Words W{stage + sbeg, nst, words + w0, nwords > w0 ? nwords - w0 : 0u};
-      const uint32_t end = decode_mcu<M>(W, bitpos - w0 * 32, hs, ndu, pr0, pr1, pr2, coef + lane);
-      if (end == 0xFFFFFFFFu || (uint64_t)w0 * 32 + end > nbits) bad = true;
-      any_bad |= bad;
+      const uint32_t end = decode_mcu<M>(W, bitpos - w0 * 32, hs, ndu, pr0, pr1, pr2, col);
+      if (end == 0xFFFFFFFFu || (uint64_t)w0 * 32 + end > nbits) any_bad = true;
     }
-    __syncwarp();
 
-    // ---- IDCT column pass: for each column u, the 6M data units spread over the lanes.
-    // Dequantise on load: d = clamp16(q * Q[k]); t = clamp16(floor((sum + 2^8) / 2^9)),
-    // written back in place (column u of t occupies the zig-zag slots of column u).
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    // ---- IDCT: each active lane transforms its own MCU (column m of the buffer, so the
+    // warp's accesses are consecutive). Column pass with dequantisation on load:
+    // t = clamp16(floor((sum_v K[y][v] clamp16(q Q) + 2^8) / 2^9)), written back in place.
+    if (act) {
 #pragma unroll 1
-      for (int j = lane; j < 6 * M; j += 32) {
-        const int d = j / M, m = j % M;
-        const uint32_t info = minfo[m];
-        if (d >= (int)(info & 7)) continue;
-        int16_t* blk = coef + (size_t)d * 64 * M + m;
-        const uint16_t* Q = qtab + m * 128 + (d < (int)(info & 7) - 2 ? 0 : 64);
-        int in[8], out[8];
-        int any = 0;
+      for (int d = 0; d < ndu; ++d) {
+        const uint16_t* Qd = Q + (d < ndu - 2 ? 0 : 64);
+        int16_t* blk = col + d * 64 * M;
 #pragma unroll
-        for (int v = 0; v < 8; ++v) {
-          const int k = zz_pos(v, u);
-          const int q = blk[k * M];
-          any |= q;
-          in[v] = sat16(q * (int)Q[k]);
+        for (int u = 0; u < 8; ++u) {
+          int in[8], out[8];
+          int any = 0;
+#pragma unroll
+          for (int v = 0; v < 8; ++v) {
+            const int k = zz_pos(v, u);
+            const int q = blk[k * M];
+            any |= q;
+            in[v] = sat16(q * (int)__ldg(Qd + k));
+          }
+          if (any == 0) continue;  // an all-zero column stays zero
+          idct8(in, out);
+#pragma unroll
+          for (int y = 0; y < 8; ++y) blk[zz_pos(y, u) * M] = (int16_t)sat16((out[y] + 256) >> 9);
         }
-        if (any == 0) continue;  // an all-zero column stays zero
-        idct8(in, out);
+      }
+      // row pass -> pixels p = clamp(floor((sum + 2^18) / 2^19) + 128), stored in place
+#pragma unroll 1
+      for (int d = 0; d < ndu; ++d) {
+        int16_t* blk = col + d * 64 * M;
 #pragma unroll
-        for (int y = 0; y < 8; ++y) blk[zz_pos(y, u) * M] = (int16_t)sat16((out[y] + 256) >> 9);
+        for (int y = 0; y < 8; ++y) {
+          int in[8], out[8];
+#pragma unroll
+          for (int x = 0; x < 8; ++x) in[x] = blk[zz_pos(y, x) * M];
+          idct8(in, out);
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            blk[zz_pos(y, i) * M] = (int16_t)(clamp255(((out[2 * i] + (1 << 18)) >> 19) + 128) |
+                                              (clamp255(((out[2 * i + 1] + (1 << 18)) >> 19) + 128) << 8));
+        }
       }
     }
-    __syncwarp();
 
-    // ---- IDCT row pass: for each row y, the 6M data units spread over the lanes -> pixels
-#pragma unroll
-    for (int y = 0; y < 8; ++y) {
+    // ---- colour conversion + tile stores: each active lane writes its own MCU's tile,
+    // four texels (16 B) per store ----
+    if (act && store) {
+      uint8_t* tile = a.cache + (size_t)off * kUnitBytes;
+      if (s420) {  // 16x16 texels; chroma sample (cx, cy) covers texels 2cx..2cx+1, 2cy..2cy+1
 #pragma unroll 1
-      for (int j = lane; j < 6 * M; j += 32) {
-        const int d = j / M, m = j % M;
-        const uint32_t info = minfo[m];
-        if (d >= (int)(info & 7)) continue;
-        const int16_t* blk = coef + (size_t)d * 64 * M + m;
-        int in[8], out[8];
+        for (int cy = 0; cy < 8; ++cy) {
 #pragma unroll
-        for (int x = 0; x < 8; ++x) in[x] = blk[zz_pos(y, x) * M];
-        idct8(in, out);
-        uint32_t w0 = 0, w1 = 0;
+          for (int c2 = 0; c2 < 4; ++c2) {  // texels x = 4 c2 .. 4 c2 + 3
+            const uint32_t cb2 = pixel2<M>(col, 4, cy, c2), cr2 = pixel2<M>(col, 5, cy, c2);
+            int ro[2], go[2], bo[2];
+            chroma_offsets(cb2 & 255, cr2 & 255, ro[0], go[0], bo[0]);
+            chroma_offsets(cb2 >> 8, cr2 >> 8, ro[1], go[1], bo[1]);
 #pragma unroll
-        for (int x = 0; x < 4; ++x) {
-          w0 |= clamp255(((out[x] + (1 << 18)) >> 19) + 128) << (8 * x);
-          w1 |= clamp255(((out[x + 4] + (1 << 18)) >> 19) + 128) << (8 * x);
+            for (int dy = 0; dy < 2; ++dy) {
+              const int ty = 2 * cy + dy;
+              const int du = (ty >> 3) * 2 + (c2 >> 1), ry = ty & 7, ci = (c2 & 1) * 2;
+              const uint32_t ya = pixel2<M>(col, du, ry, ci), yb = pixel2<M>(col, du, ry, ci + 1);
+              uint4 o;
+              o.x = ycc_pixel(ya & 255, ro[0], go[0], bo[0]);
+              o.y = ycc_pixel(ya >> 8, ro[0], go[0], bo[0]);
+              o.z = ycc_pixel(yb & 255, ro[1], go[1], bo[1]);
+              o.w = ycc_pixel(yb >> 8, ro[1], go[1], bo[1]);
+              *reinterpret_cast<uint4*>(tile + (ty * 16 + 4 * c2) * 4) = o;
+            }
+          }
         }
-        uint32_t* dst = pix + m * kPixStride + pix_row(d, y, (info & 16) != 0);
-        dst[0] = w0;
-        dst[1] = w1;
+      } else {  // 4:4:4, 8x8 texels, Y Cb Cr data units 0 1 2
+#pragma unroll 1
+        for (int ty = 0; ty < 8; ++ty) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {  // texels x = 4h .. 4h + 3
+            uint32_t o[4];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+              const uint32_t y2 = pixel2<M>(col, 0, ty, 2 * h + j), b2 = pixel2<M>(col, 1, ty, 2 * h + j),
+                             r2 = pixel2<M>(col, 2, ty, 2 * h + j);
+#pragma unroll
+              for (int e = 0; e < 2; ++e) {
+                int ro, go, bo;
+                chroma_offsets((b2 >> (8 * e)) & 255, (r2 >> (8 * e)) & 255, ro, go, bo);
+                o[2 * j + e] = ycc_pixel((y2 >> (8 * e)) & 255, ro, go, bo);
+              }
+            }
+            *reinterpret_cast<uint4*>(tile + (ty * 8 + 4 * h) * 4) = make_uint4(o[0], o[1], o[2], o[3]);
+          }
+        }
       }
     }
-    __syncwarp();
-
-    // ---- colour conversion + coalesced tile stores, one MCU at a time ----
-#pragma unroll 1
-    for (int m = 0; m < M; ++m) {
-      const uint32_t info = minfo[m];
-      if (!(info & 32)) continue;
-      const uint32_t* P = pix + m * kPixStride;
-      uint8_t* tile = a.cache + (size_t)moff[m] * kUnitBytes;
-      if (info & 16) {  // 4:2:0, 16x16: lane = (row r, half h)
-        const int r = lane >> 1, h = lane & 1;
-        const uint32_t y0 = P[r * 4 + h * 2], y1 = P[r * 4 + h * 2 + 1];
-        const uint32_t cbw = P[64 + (r >> 1) * 2 + h], crw = P[80 + (r >> 1) * 2 + h];
-        uint32_t o[8];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          int ro, go, bo;
-          chroma_offsets((cbw >> (8 * j)) & 255, (crw >> (8 * j)) & 255, ro, go, bo);
-          const uint32_t yw = j < 2 ? y0 : y1;
-          const int sh0 = 16 * (j & 1);
-          o[2 * j] = ycc_pixel((yw >> sh0) & 255, ro, go, bo);
-          o[2 * j + 1] = ycc_pixel((yw >> (sh0 + 8)) & 255, ro, go, bo);
-        }
-        uint4* dst = reinterpret_cast<uint4*>(tile + r * 64 + h * 32);
-        dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
-        dst[1] = make_uint4(o[4], o[5], o[6], o[7]);
-      } else {  // 4:4:4, 8x8: lane = (row r, quarter q)
-        const int r = lane >> 2, q = lane & 3;
-        const int wi = r * 2 + (q >> 1), sh0 = 16 * (q & 1);
-        const uint32_t yw = P[wi], cbw = P[64 + wi], crw = P[80 + wi];
-        uint32_t o[2];
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-          int ro, go, bo;
-          chroma_offsets((cbw >> (sh0 + 8 * i)) & 255, (crw >> (sh0 + 8 * i)) & 255, ro, go, bo);
-          o[i] = ycc_pixel((yw >> (sh0 + 8 * i)) & 255, ro, go, bo);
-        }
-        *reinterpret_cast<uint2*>(tile + r * 32 + q * 8) = make_uint2(o[0], o[1]);
-      }
-    }
-    __syncwarp();
+    __syncwarp();  // the buffers are cleared for the next items
   }
   if (any_bad) atomicOr(&a.state->err, JT_DEVERR_CORRUPT);
 }

@@ -44,6 +44,8 @@ struct jt_ctx {
   std::vector<Level> levels;
   DevDesc* d_descs = nullptr;
   size_t d_descs_cap = 0;
+  uint32_t* d_desc_of_gid = nullptr;  // descriptor index of every gid (the decoder's lookup)
+  uint64_t desc_of_gid_cap = 0;
   std::vector<int32_t> map;  // [map_ntex * 16]
   std::vector<LevelRec> lrec;  // [map_ntex * 16]
   uint32_t map_ntex = 0;
@@ -175,11 +177,7 @@ bool build_table(const jt_huff_spec& spec, bool dc, HuffTable& t, std::string& w
     return false;
   }
   std::memcpy(t.vals, spec.vals, n);
-  // left-aligned start of the codes longer than kLutBits = Kraft mass of the shorter ones
-  uint32_t first16 = 0;
-  for (int l = 1; l <= kLutBits; ++l) first16 += (uint32_t)spec.bits[l - 1] << (16 - l);
-  t.first16 = first16;
-  t.n2 = (65536u - first16 <= (uint32_t)kLut2Size && first16 < 65536u) ? 65536u - first16 : 0u;
+  int nsub = 0;
   int code = 0, k = 0;
   for (int l = 1; l <= 16; ++l) {
     const int nl = spec.bits[l - 1];
@@ -193,9 +191,18 @@ bool build_table(const jt_huff_spec& spec, bool dc, HuffTable& t, std::string& w
         if (l <= kLutBits) {
           const int first = code << (kLutBits - l), cnt = 1 << (kLutBits - l);
           for (int j = 0; j < cnt; ++j) t.lut[first + j] = e;
-        } else if (t.n2) {
-          const uint32_t first = ((uint32_t)code << (16 - l)) - first16, cnt = 1u << (16 - l);
-          for (uint32_t j = 0; j < cnt; ++j) t.lut2[first + j] = e;
+        } else {
+          // subtable of the code's kLutBits-bit prefix (allocated on first use)
+          const int prefix = code >> (l - kLutBits);
+          int sub = (t.lut[prefix] & 31) == 0 ? (int)(t.lut[prefix] >> 5) - 1 : -2;
+          if (sub == -1 && nsub < kLut2Size / kSubSize) {
+            sub = nsub++;
+            t.lut[prefix] = (uint16_t)((sub + 1) << 5);
+          }
+          if (sub >= 0) {
+            const int first = (code << (16 - l)) & (kSubSize - 1), cnt = 1 << (16 - l);
+            for (int j = 0; j < cnt; ++j) t.lut2[sub * kSubSize + first + j] = e;
+          }
         }
       }
       t.maxcode[l] = code - 1;
@@ -362,6 +369,7 @@ jt_status enqueue_decode(jt_ctx* c, cudaStream_t s) {
   DecodeArgs a{};
   a.descs = c->d_descs;
   a.ndesc = (uint32_t)c->descs.size();
+  a.desc_of_gid = c->d_desc_of_gid;
   a.mcus_per_warp = c->tuning.decode_mcus_per_warp;
   a.huff = c->d_huff;
   a.quant = c->d_quant;
@@ -511,9 +519,9 @@ jt_status jt_create(jt_ctx** out, int device, uint64_t max_cache_blocks) {
     for (int W : kDecodeWarps) c->decode_occ[M][W] = decode_max_ctas_per_sm(W, M);
   c->scan_per_sm = scan_max_ctas_per_sm();
   cudaGetLastError();
-  c->tuning.decode_mcus_per_warp = 4;  // the autotuner's usual pick for frames of ~10^4 MCUs
-  c->tuning.decode_warps = 8;
-  c->tuning.decode_ctas_per_sm = std::max(1, c->decode_occ[4][8]);
+  c->tuning.decode_mcus_per_warp = 32;
+  c->tuning.decode_warps = 4;
+  c->tuning.decode_ctas_per_sm = std::max(1, c->decode_occ[32][4]);
   c->tuning.pixel_threads = 256;
   c->tuning.pixel_ctas_per_sm = 8;
   c->cap_units = max_cache_blocks * 4;
@@ -550,6 +558,7 @@ jt_status jt_destroy(jt_ctx* c) {
   dev_free(c->work);
   dev_free(c->tile_status);
   dev_free(c->cache);
+  dev_free(c->d_desc_of_gid);
   dev_free(c->state);
   dev_free(c->float_tiles);
   if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
@@ -594,9 +603,24 @@ static jt_status add_level(jt_ctx* c, int tex_id, int level, DevDesc d, Level L)
   r.pad = 0;
   c->descs.push_back(d);
   c->levels.push_back(L);
+  const uint64_t g0 = c->ngid;
   c->ngid += d.nmcu;
   jt_status s = grow_frame_buffers(c, c->ngid);
   if (s != JT_OK) return s;
+  // gid -> descriptor index for the new level's MCUs
+  if (c->ngid > c->desc_of_gid_cap) {
+    const uint64_t cap = std::max<uint64_t>(c->ngid, c->desc_of_gid_cap * 2);
+    uint32_t* nb = nullptr;
+    if ((s = dev_alloc(c, &nb, cap * 4)) != JT_OK) return s;
+    if (g0) JT_CUDA(c, cudaMemcpy(nb, c->d_desc_of_gid, g0 * 4, cudaMemcpyDeviceToDevice));
+    dev_free(c->d_desc_of_gid);
+    c->d_desc_of_gid = nb;
+    c->desc_of_gid_cap = cap;
+  }
+  {
+    const std::vector<uint32_t> di(d.nmcu, (uint32_t)(c->descs.size() - 1));
+    JT_CUDA(c, cudaMemcpy(c->d_desc_of_gid + g0, di.data(), (size_t)d.nmcu * 4, cudaMemcpyHostToDevice));
+  }
   return sync_descs(c);
 }
 
