@@ -10,9 +10,9 @@
 //  * entropy phase: lane m < M runs MCU m's serial entropy chain over all its data units
 //    from a byte-swapped copy of its words staged in shared memory (a per-warp pool shared
 //    out by a prefix sum). Per symbol: one funnel shift of a two-word window, one 10-bit
-//    LUT read (16-bit entries: code length, value size, run), the value cut from the same
-//    window without a branch, and a select to advance the window; codes longer than 10
-//    bits take one more read in their prefix's 64-entry subtable. The quantised coefficients go in zig-zag order into a
+//    LUT read (16-bit entries: code length, value size, run) together with an independent
+//    read of the second-level entry for codes longer than 10 bits, the value cut from the
+//    same window without a branch, and a select to advance the window. The quantised coefficients go in zig-zag order into a
 //    per-warp buffer coef[du][k][m] (int16). Nothing but the LUT and the stream is read on
 //    this serial chain: dequantisation waits for the IDCT phase;
 //  * IDCT phase: each lane transforms its own MCU, column then row, over the warp's
@@ -31,6 +31,8 @@
 // K[x][u] = round(2^14 c_u cos((2x+1) u pi / 16)); JFIF colour in 16-bit fixed point;
 // 4:2:0 chroma replicated within the MCU; DC values wrap modulo 2^16.
 #include <cuda_runtime.h>
+
+#include <cstddef>
 
 #include "jt_internal.cuh"
 
@@ -77,7 +79,7 @@ __device__ __forceinline__ uint32_t clamp255(int v) { return (uint32_t)min(255, 
 // prefix sum over its lanes, so a long MCU can use what short ones leave (the mean MCU of a
 // scene needs about a quarter). Words are stored big-endian-swapped; a lane whose MCU does
 // not fit reads the rest from global memory.
-constexpr int kStageWords = 32;
+constexpr int kStageWords = 36;  // also the colour phase's 144 B batch buffer per MCU
 
 // Shared memory of one warp: coefficients [6][64][M] int16 (zig-zag order k, lane m at
 // column m; after the row pass each data unit's slots hold its pixels, see below) and the
@@ -90,14 +92,49 @@ __device__ __forceinline__ uint32_t bswap(uint32_t w) { return __byte_perm(w, 0,
 
 // Stream word i (relative to the lane's first staged word): from the staged copy when it is
 // there, else from global memory (past the end of the stream: 0).
+__device__ __forceinline__ uint32_t lds_u32(uint32_t saddr) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(saddr));
+  return v;
+}
+__device__ __forceinline__ uint32_t lds_u16(uint32_t saddr) {
+  uint16_t v;
+  asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(saddr));
+  return v;
+}
+
+// Stream word i (relative to the lane's first staged word): from the staged copy (shared
+// memory address st) when it is there, else from global memory (past the end: 0).
 struct Words {
-  const uint32_t* st;     // staged, byte-swapped
+  uint32_t st;            // shared-memory address of the staged, byte-swapped words
   uint32_t nst;           // words staged
   const uint32_t* gw;     // stream words from the first staged word on
   uint32_t ngw;           // readable words from gw on
   __device__ __forceinline__ uint32_t operator()(uint32_t i) const {
-    if (i < nst) return st[i];
+    if (i < nst) return lds_u32(st + 4 * i);
     return i < ngw ? bswap(__ldg(gw + i)) : 0u;
+  }
+};
+
+// Reads of the table set on the serial chain: explicit shared-memory loads for the staged
+// set (address hs_sa), generic loads through hs otherwise.
+template <bool SH>
+struct Tables {
+  const HuffTable* hs;
+  uint32_t hs_sa;
+  __device__ __forceinline__ uint32_t lut(uint32_t ti, uint32_t i) const {
+    return SH ? lds_u16(hs_sa + ti * (uint32_t)sizeof(HuffTable) + i * 2) : (uint32_t)hs[ti].lut[i];
+  }
+  __device__ __forceinline__ uint32_t lut2(uint32_t ti, uint32_t j) const {
+    return SH ? lds_u16(hs_sa + ti * (uint32_t)sizeof(HuffTable) + (uint32_t)offsetof(HuffTable, lut2) + j * 2)
+              : (uint32_t)hs[ti].lut2[j];
+  }
+  __device__ __forceinline__ uint32_t first16(uint32_t ti) const {
+    return SH ? lds_u32(hs_sa + ti * (uint32_t)sizeof(HuffTable) + (uint32_t)offsetof(HuffTable, first16))
+              : hs[ti].first16;
+  }
+  __device__ __forceinline__ uint32_t n2(uint32_t ti) const {
+    return SH ? lds_u32(hs_sa + ti * (uint32_t)sizeof(HuffTable) + (uint32_t)offsetof(HuffTable, n2)) : hs[ti].n2;
   }
 };
 
@@ -129,24 +166,32 @@ __device__ __noinline__ uint32_t walk_symbol(const HuffTable* t, uint32_t w, boo
 // move to the next data unit (predictor save/restore, table choice) is also branch-free.
 // hs: the lane's tables (shared or global memory). Returns the bit position after the MCU
 // relative to the first staged word, or 0xFFFFFFFF on an invalid coding.
-template <int M>
-__device__ __forceinline__ uint32_t decode_mcu(const Words& W, uint32_t bit0, const HuffTable* hs, int ndu,
+template <int M, bool SH>
+__device__ __forceinline__ uint32_t decode_mcu(const Words& W, uint32_t bit0, const Tables<SH>& T, int ndu,
                                                int16_t& p0, int16_t& p1, int16_t& p2, int16_t* coef) {
   uint32_t widx = bit0 >> 5, pos = bit0 & 31;
   uint32_t hi = W(widx), lo = W(widx + 1), nx = W(widx + 2);
+  // second-level ranges of the four tables, held in registers so that no table read other
+  // than the two LUT entries sits on the chain
+  const uint32_t F0 = T.first16(0), F1 = T.first16(1), F2 = T.first16(2), F3 = T.first16(3);
+  const uint32_t N0 = T.n2(0), N1 = T.n2(1), N2 = T.n2(2), N3 = T.n2(3);
   int du = 0, k = 0, comp = 0, pc = p0, q0 = p0, q1 = p1, q2 = p2;
-  uint32_t dct = 0, boff = 0;
+  uint32_t ti = 0, boff = 0;  // ti: table of the next symbol (0 DC luma, 1 AC luma, 2 DC chroma, 3 AC chroma)
   bool bad = false;
 #pragma unroll 1
   for (int it = 0; it < 64 * 6; ++it) {  // at most 64 symbols per data unit
     const uint32_t w = __funnelshift_l(lo, hi, pos);
     const bool dc = k == 0;
-    const HuffTable* t = hs + dct + (dc ? 0u : 1u);
-    uint32_t e = t->lut[w >> (32 - kLutBits)];
-    if ((e & 31u) == 0) {  // a longer code: its prefix's subtable, else the walk
-      const uint32_t sub = e >> 5;
-      e = sub ? (uint32_t)t->lut2[(sub - 1) * kSubSize + ((w >> (32 - kLutBits - kSubBits)) & (kSubSize - 1))] : 0u;
-      if (e == 0) e = walk_symbol(t, w, dc);
+    // both levels read at once (independent loads): the first-level entry when the code is
+    // short, else the second-level entry of the 16-bit prefix
+    const uint32_t f16 = (ti & 2) ? ((ti & 1) ? F3 : F2) : ((ti & 1) ? F1 : F0);
+    const uint32_t n2 = (ti & 2) ? ((ti & 1) ? N3 : N2) : ((ti & 1) ? N1 : N0);
+    const uint32_t e1 = T.lut(ti, w >> (32 - kLutBits));
+    const uint32_t j = (w >> 16) - f16;
+    const uint32_t e2 = T.lut2(ti, min(j, (uint32_t)kLut2Size - 1u));
+    uint32_t e = (e1 & 31u) ? e1 : (j < n2 ? e2 : 0u);
+    if (e == 0) {  // no table entry: the MAXCODE walk decodes or rejects it
+      e = walk_symbol(T.hs + ti, w, dc);
       if (e == 0) {
         bad = true;
         break;
@@ -179,7 +224,8 @@ __device__ __forceinline__ uint32_t decode_mcu(const Words& W, uint32_t bit0, co
     const int cn = du < ndu - 2 ? 0 : (du == ndu - 2 ? 1 : 2);
     pc = done ? (cn == 0 ? q0 : (cn == 1 ? q1 : q2)) : pc;
     comp = cn;
-    dct = cn ? 2u : 0u;
+    // next symbol: the DC table of the next data unit's component, else this one's AC table
+    ti = (cn ? 2u : 0u) + (done ? 0u : 1u);
     boff += done ? 64u : 0u;
     k = done ? 0 : k;
     if (du == ndu || bad) break;
@@ -314,8 +360,13 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
 
     // ---- entropy phase: each active lane decodes all data units of its MCU ----
     if (act) {
-      const Words W{stage + sbeg, nst, words + w0, nwords > w0 ? nwords - w0 : 0u};
-      const uint32_t end = decode_mcu<M>(W, bitpos - w0 * 32, hs, ndu, pr0, pr1, pr2, col);
+      const Words W{(uint32_t)__cvta_generic_to_shared(stage + sbeg), nst, words + w0,
+                    nwords > w0 ? nwords - w0 : 0u};
+      const uint32_t end =
+          hs == sh->t
+              ? decode_mcu<M, true>(W, bitpos - w0 * 32, Tables<true>{hs, (uint32_t)__cvta_generic_to_shared(sh->t)},
+                                    ndu, pr0, pr1, pr2, col)
+              : decode_mcu<M, false>(W, bitpos - w0 * 32, Tables<false>{hs, 0u}, ndu, pr0, pr1, pr2, col);
       if (end == 0xFFFFFFFFu || (uint64_t)w0 * 32 + end > nbits) any_bad = true;
     }
 
@@ -330,15 +381,11 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           int in[8], out[8];
-          int any = 0;
 #pragma unroll
           for (int v = 0; v < 8; ++v) {
             const int k = zz_pos(v, u);
-            const int q = blk[k * M];
-            any |= q;
-            in[v] = sat16(q * (int)__ldg(Qd + k));
+            in[v] = sat16(blk[k * M] * (int)__ldg(Qd + k));
           }
-          if (any == 0) continue;  // an all-zero column stays zero
           idct8(in, out);
 #pragma unroll
           for (int y = 0; y < 8; ++y) blk[zz_pos(y, u) * M] = (int16_t)sat16((out[y] + 256) >> 9);
@@ -362,53 +409,69 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
       }
     }
 
-    // ---- colour conversion + tile stores: each active lane writes its own MCU's tile,
-    // four texels (16 B) per store ----
-    if (act && store) {
-      uint8_t* tile = a.cache + (size_t)off * kUnitBytes;
-      if (s420) {  // 16x16 texels; chroma sample (cx, cy) covers texels 2cx..2cx+1, 2cy..2cy+1
+    // ---- colour conversion + tile stores. A tile is written in batches of 128 B (two
+    // texel rows at 4:2:0, four at 4:4:4): each lane converts its MCU's batch into the
+    // stage area (row m at 144 m bytes; the staged words are no longer needed), then the
+    // warp stores the batches of 4 MCUs per instruction as 128 B runs (coalesced).
+    const bool put = act && store;
+    uint8_t* obuf = reinterpret_cast<uint8_t*>(stage);
+    const int nbatch = __reduce_max_sync(0xFFFFFFFFu, put ? (s420 ? 8 : 2) : 0);
 #pragma unroll 1
-        for (int cy = 0; cy < 8; ++cy) {
+    for (int b = 0; b < nbatch; ++b) {
+      __syncwarp();
+      if (put && (s420 || b < 2)) {
+        uint4* ob = reinterpret_cast<uint4*>(obuf + lane * 144);
+        if (s420) {  // texel rows 2b, 2b + 1 = chroma row b; chroma sample x covers texels 2x, 2x+1
 #pragma unroll
           for (int c2 = 0; c2 < 4; ++c2) {  // texels x = 4 c2 .. 4 c2 + 3
-            const uint32_t cb2 = pixel2<M>(col, 4, cy, c2), cr2 = pixel2<M>(col, 5, cy, c2);
+            const uint32_t cb2 = pixel2<M>(col, 4, b, c2), cr2 = pixel2<M>(col, 5, b, c2);
             int ro[2], go[2], bo[2];
             chroma_offsets(cb2 & 255, cr2 & 255, ro[0], go[0], bo[0]);
             chroma_offsets(cb2 >> 8, cr2 >> 8, ro[1], go[1], bo[1]);
 #pragma unroll
             for (int dy = 0; dy < 2; ++dy) {
-              const int ty = 2 * cy + dy;
+              const int ty = 2 * b + dy;
               const int du = (ty >> 3) * 2 + (c2 >> 1), ry = ty & 7, ci = (c2 & 1) * 2;
               const uint32_t ya = pixel2<M>(col, du, ry, ci), yb = pixel2<M>(col, du, ry, ci + 1);
-              uint4 o;
-              o.x = ycc_pixel(ya & 255, ro[0], go[0], bo[0]);
-              o.y = ycc_pixel(ya >> 8, ro[0], go[0], bo[0]);
-              o.z = ycc_pixel(yb & 255, ro[1], go[1], bo[1]);
-              o.w = ycc_pixel(yb >> 8, ro[1], go[1], bo[1]);
-              *reinterpret_cast<uint4*>(tile + (ty * 16 + 4 * c2) * 4) = o;
+              ob[dy * 4 + c2] = make_uint4(ycc_pixel(ya & 255, ro[0], go[0], bo[0]),
+                                           ycc_pixel(ya >> 8, ro[0], go[0], bo[0]),
+                                           ycc_pixel(yb & 255, ro[1], go[1], bo[1]),
+                                           ycc_pixel(yb >> 8, ro[1], go[1], bo[1]));
             }
           }
-        }
-      } else {  // 4:4:4, 8x8 texels, Y Cb Cr data units 0 1 2
-#pragma unroll 1
-        for (int ty = 0; ty < 8; ++ty) {
+        } else {  // 4:4:4: texel rows 4b .. 4b + 3 of 8 texels; Y Cb Cr data units 0 1 2
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {  // texels x = 4h .. 4h + 3
-            uint32_t o[4];
+          for (int r = 0; r < 4; ++r) {
+            const int ty = 4 * b + r;
 #pragma unroll
-            for (int j = 0; j < 2; ++j) {
-              const uint32_t y2 = pixel2<M>(col, 0, ty, 2 * h + j), b2 = pixel2<M>(col, 1, ty, 2 * h + j),
-                             r2 = pixel2<M>(col, 2, ty, 2 * h + j);
+            for (int h = 0; h < 2; ++h) {  // texels x = 4h .. 4h + 3
+              uint32_t o[4];
 #pragma unroll
-              for (int e = 0; e < 2; ++e) {
-                int ro, go, bo;
-                chroma_offsets((b2 >> (8 * e)) & 255, (r2 >> (8 * e)) & 255, ro, go, bo);
-                o[2 * j + e] = ycc_pixel((y2 >> (8 * e)) & 255, ro, go, bo);
+              for (int j = 0; j < 2; ++j) {
+                const uint32_t y2 = pixel2<M>(col, 0, ty, 2 * h + j), b2 = pixel2<M>(col, 1, ty, 2 * h + j),
+                               r2 = pixel2<M>(col, 2, ty, 2 * h + j);
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                  int ro, go, bo;
+                  chroma_offsets((b2 >> (8 * e)) & 255, (r2 >> (8 * e)) & 255, ro, go, bo);
+                  o[2 * j + e] = ycc_pixel((y2 >> (8 * e)) & 255, ro, go, bo);
+                }
               }
+              ob[r * 2 + h] = make_uint4(o[0], o[1], o[2], o[3]);
             }
-            *reinterpret_cast<uint4*>(tile + (ty * 8 + 4 * h) * 4) = make_uint4(o[0], o[1], o[2], o[3]);
           }
         }
+      }
+      __syncwarp();
+      // chunk j of MCU m: lanes 8q .. 8q + 7 store the 8 chunks of MCU 4 i + q
+#pragma unroll
+      for (int i = 0; i < M / 4; ++i) {
+        const int m = 4 * i + (lane >> 3), j = lane & 7;
+        const uint32_t om = __shfl_sync(0xFFFFFFFFu, off, m);
+        const bool pm = __shfl_sync(0xFFFFFFFFu, put && (s420 || b < 2), m);
+        if (pm)
+          *reinterpret_cast<uint4*>(a.cache + (size_t)om * kUnitBytes + b * 128 + j * 16) =
+              *reinterpret_cast<const uint4*>(obuf + m * 144 + j * 16);
       }
     }
     __syncwarp();  // the buffers are cleared for the next items

@@ -177,7 +177,11 @@ bool build_table(const jt_huff_spec& spec, bool dc, HuffTable& t, std::string& w
     return false;
   }
   std::memcpy(t.vals, spec.vals, n);
-  int nsub = 0;
+  // left-aligned start of the codes longer than kLutBits = Kraft mass of the shorter ones
+  uint32_t first16 = 0;
+  for (int l = 1; l <= kLutBits; ++l) first16 += (uint32_t)spec.bits[l - 1] << (16 - l);
+  t.first16 = first16;
+  t.n2 = (first16 < 65536u && 65536u - first16 <= (uint32_t)kLut2Size) ? 65536u - first16 : 0u;
   int code = 0, k = 0;
   for (int l = 1; l <= 16; ++l) {
     const int nl = spec.bits[l - 1];
@@ -191,18 +195,9 @@ bool build_table(const jt_huff_spec& spec, bool dc, HuffTable& t, std::string& w
         if (l <= kLutBits) {
           const int first = code << (kLutBits - l), cnt = 1 << (kLutBits - l);
           for (int j = 0; j < cnt; ++j) t.lut[first + j] = e;
-        } else {
-          // subtable of the code's kLutBits-bit prefix (allocated on first use)
-          const int prefix = code >> (l - kLutBits);
-          int sub = (t.lut[prefix] & 31) == 0 ? (int)(t.lut[prefix] >> 5) - 1 : -2;
-          if (sub == -1 && nsub < kLut2Size / kSubSize) {
-            sub = nsub++;
-            t.lut[prefix] = (uint16_t)((sub + 1) << 5);
-          }
-          if (sub >= 0) {
-            const int first = (code << (16 - l)) & (kSubSize - 1), cnt = 1 << (16 - l);
-            for (int j = 0; j < cnt; ++j) t.lut2[sub * kSubSize + first + j] = e;
-          }
+        } else if (t.n2) {
+          const uint32_t first = ((uint32_t)code << (16 - l)) - first16, cnt = 1u << (16 - l);
+          for (uint32_t j = 0; j < cnt; ++j) t.lut2[first + j] = e;
         }
       }
       t.maxcode[l] = code - 1;

@@ -35,23 +35,25 @@ constexpr int kSampling420 = 0, kSampling444 = 1, kSamplingCoef = 2;
 //   EOB       (63, 0)  -> advance 64 (store a zero at slot 63, which is zero already)
 //   DC        (0, s)   -> difference, advance 1
 // The s value bits follow the code in the stream; the decoder cuts them from its 32-bit
-// window itself (T.81 EXTEND), so an entry depends on the code alone.
-//   lut[i]   indexed by the next kLutBits bits: the entry of the code they start with when
-//            it is at most kLutBits long; for a prefix of longer codes l = 0 and bits 5..9
-//            hold 1 + the index of its 64-entry subtable in lut2; 0 = no entry
-//   lut2[64 sub + j]  entry of the longer code that continues the prefix with the 6 bits j
-// Prefixes beyond kLut2Size / 64 subtables, invalid codes, and symbols invalid for the
-// table's class (DC category > 11, AC size > 10, AC size 0 with a run other than 0 or 15)
-// have no entry; the MAXCODE walk of T.81 F.2.2.3 then decodes or rejects them.
+// window itself (T.81 EXTEND), so an entry depends on the code alone. 0 = no entry.
+//   lut[i]   entry of the code that starts the next kLutBits bits i (codes up to kLutBits)
+//   lut2[j]  entry of the longer code whose 16-bit left-aligned prefix is first16 + j: in
+//            canonical order the longer codes are the numerically largest, so they occupy
+//            the top n2 of the 65536 16-bit prefixes (n2 <= kLut2Size, else 0)
+// The decoder reads both entries for every symbol (the two reads are independent), so a
+// long code costs no branch. Codes without an entry (invalid codes, long codes of tables
+// whose range exceeds kLut2Size) and symbols invalid for the table's class (DC category >
+// 11, AC size > 10, AC size 0 with a run other than 0 or 15) go to the MAXCODE walk of
+// T.81 F.2.2.3, which decodes or rejects them.
 __host__ __device__ constexpr uint16_t huff_entry(uint32_t l, uint32_t s, uint32_t r) {
   return (uint16_t)(l | (s << 5) | (r << 9));
 }
 constexpr uint32_t kRunEob = 63;
-constexpr int kSubBits = 16 - kLutBits;  // 6: a subtable covers the bits up to length 16
-constexpr int kSubSize = 1 << kSubBits;
 struct HuffTable {
   uint16_t lut[kLutSize];
   uint16_t lut2[kLut2Size];
+  uint32_t first16;     // 16-bit left-aligned value of the first code longer than kLutBits
+  uint32_t n2;          // entries of lut2 in use (0: no longer codes, or too many)
   int32_t maxcode[17];  // -1 when no code of length l
   int32_t valoff[17];
   uint8_t vals[256];
