@@ -222,7 +222,7 @@ jt_status jt_read_cache(jt_ctx* ctx, uint64_t unit_begin, uint64_t n, uint8_t* d
 
 /* ---- compaction without allocation (no counterpart in the paper) ------------------------- */
 
-/* Largest n accepted by jt_compact_static: 1024 scan tiles of 16384 flags. */
+/* Largest n accepted by jt_compact_static: 256 scan tiles of 65536 flags. */
 #define JT_STATIC_COMPACT_MAX_FLAGS 16777216u
 
 /* The compaction step of jt_decode (Sec. 4.2's decode queue; flags -> work list and cache

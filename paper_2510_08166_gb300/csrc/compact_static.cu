@@ -12,8 +12,8 @@
 // launches and copies three words out, all asynchronously on the caller's stream.
 //
 // Scratch: one fixed array per device image, 256 B of frame state then one 64-bit status
-// word per scan tile (16384 flags), for at most kMaxTiles = 1024 tiles (16,777,216 flags,
-// 8.4 KB). Its device address is looked up once per device (cudaGetSymbolAddress, which
+// word per scan tile (65536 flags), for at most kMaxTiles = 256 tiles (16,777,216 flags,
+// 2.3 KB). Its device address is looked up once per device (cudaGetSymbolAddress, which
 // may load the module lazily and so must first run outside any stream capture) and cached.
 // Because
 // the array is shared, two calls in flight at once on one device (two streams, or two

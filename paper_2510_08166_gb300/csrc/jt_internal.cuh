@@ -163,7 +163,7 @@ struct ScanArgs {
   FrameState* state;
   uint32_t cap_units;
 };
-constexpr int kScanThreads = 256;
+constexpr int kScanThreads = 1024;
 constexpr int kScanPerThread = 64;  // 4 x 16-byte loads
 constexpr int kScanTile = kScanThreads * kScanPerThread;
 void launch_scan(const ScanArgs& a, int grid, cudaStream_t s);

@@ -69,31 +69,15 @@ __device__ __forceinline__ Lvl load_level(const TexLookup& tl, uint32_t key) {
   return L;
 }
 
-// Keys of a quad's pixels and whether the whole warp's row segment shares one level
-// (then that level is loaded once for the warp; otherwise per pixel).
+// Keys of a quad's pixels.
 struct QuadLevels {
   uint32_t key[4];
-  bool uniform;
-  Lvl shared;
 };
 
-// Warp-collective: all 32 lanes must call it.
 __device__ __forceinline__ void quad_levels(const TexLookup& tl, int n, const uint32_t t[4], const uint32_t m[4],
                                             int only_tex, QuadLevels& q) {
-  uint32_t k0 = kNoKey;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    q.key[i] = level_key(tl, i < n, t[i], m[i], only_tex);
-    if (k0 == kNoKey) k0 = q.key[i];
-  }
-  bool same = true;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) same &= q.key[i] == kNoKey || q.key[i] == k0;
-  // the first lane with a pixel names the candidate
-  const uint32_t have = __ballot_sync(0xFFFFFFFFu, k0 != kNoKey);
-  const uint32_t kw = have ? __shfl_sync(0xFFFFFFFFu, k0, __ffs(have) - 1) : kNoKey;
-  q.uniform = __all_sync(0xFFFFFFFFu, same && (k0 == kNoKey || k0 == kw)) && kw < kNoKey - 1;
-  if (q.uniform) q.shared = load_level(tl, kw);
+  for (int i = 0; i < 4; ++i) q.key[i] = level_key(tl, i < n, t[i], m[i], only_tex);
 }
 
 // Floor-mod of a texel coordinate; P2: the side is a power of two (a mask). The choice is
@@ -124,38 +108,38 @@ __device__ __forceinline__ void bilinear_taps(float u, float v, const Lvl& L, in
 }
 
 // Calls f(P2, L, i) for the quad's pixels i = 0..3 with the level record of each, P2 a
-// std::integral_constant telling whether both sides may be wrapped with a mask: loaded once
-// when the warp's row segment shares one level (the common case), else per pixel. P2 is
-// decided per warp, so only one of the two instantiations runs. Warp-collective: all 32
-// lanes must call it (lanes without pixels have empty keys).
+// std::integral_constant telling whether the levels may be wrapped with a mask: known for
+// the whole context, else decided per warp by a vote (so only one instantiation runs). A
+// lane loads a level record only when its key differs from the previous pixel's (the
+// pixels of a quad nearly always share one). Warp-collective: all 32 lanes must call it
+// (lanes without pixels have empty keys).
+template <bool P2, typename F>
+__device__ __forceinline__ void quad_pixels_with(const TexLookup& tl, const QuadLevels& q, F&& f) {
+  Lvl L = load_level(tl, kNoKey);
+  uint32_t lk = kNoKey;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    if (q.key[i] != lk) {
+      L = load_level(tl, q.key[i]);
+      lk = q.key[i];
+    }
+    f(std::integral_constant<bool, P2>{}, L, i);
+  }
+}
+
 template <typename F>
 __device__ __forceinline__ void for_quad_pixels(const TexLookup& tl, const QuadLevels& q, F&& f) {
-  if (q.uniform) {
-    if (q.shared.wp2 && q.shared.hp2) {
+  bool p2 = true;
+  if (!tl.all_p2) {
 #pragma unroll
-      for (int i = 0; i < 4; ++i) f(std::true_type{}, q.shared, i);
-    } else {
-#pragma unroll
-      for (int i = 0; i < 4; ++i) f(std::false_type{}, q.shared, i);
-    }
-  } else {
-    // levels differ within the row segment: the mask wrap still applies when every pixel's
-    // level has power-of-two sides (known for the whole context, else one info word per
-    // pixel and a vote)
-    bool p2 = true;
-    if (!tl.all_p2) {
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-        if (q.key[i] < kNoKey - 1) p2 &= ((__ldg(&tl.levels[q.key[i]].z) >> 28) & 3u) == 3u;
-    }
-    if (__all_sync(0xFFFFFFFFu, p2)) {
-#pragma unroll
-      for (int i = 0; i < 4; ++i) f(std::true_type{}, load_level(tl, q.key[i]), i);
-    } else {
-#pragma unroll
-      for (int i = 0; i < 4; ++i) f(std::false_type{}, load_level(tl, q.key[i]), i);
-    }
+    for (int i = 0; i < 4; ++i)
+      if (q.key[i] < kNoKey - 1) p2 &= ((__ldg(&tl.levels[q.key[i]].z) >> 28) & 3u) == 3u;
+    p2 = __all_sync(0xFFFFFFFFu, p2);
   }
+  if (p2)
+    quad_pixels_with<true>(tl, q, f);
+  else
+    quad_pixels_with<false>(tl, q, f);
 }
 
 // Locates the view of global tile `tile` (views are few and sorted by tile_begin).

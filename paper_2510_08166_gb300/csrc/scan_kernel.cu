@@ -7,7 +7,7 @@
 // prefix): work[count_prefix] = gid, slot[gid] = units_prefix. The list is therefore in
 // ascending gid order and deterministic. The same pass clears the flags for the next frame.
 //
-// Single pass: decoupled look-back (Merrill & Garland 2016). Each 16384-flag tile
+// Single pass: decoupled look-back (Merrill & Garland 2016). Each 65536-flag tile
 // publishes its aggregate, then a warp of the tile looks back over up to 32 predecessor
 // tiles at a time until it meets an inclusive prefix. The grid is persistent (every CTA
 // resident) and CTAs take tiles in increasing order, so every awaited predecessor is being
@@ -48,7 +48,7 @@ __device__ __forceinline__ void word_stats(uint32_t w, uint32_t& cnt, uint32_t& 
   sum += (w & 255) + ((w >> 8) & 255) + ((w >> 16) & 255) + (w >> 24);
 }
 
-__global__ void __launch_bounds__(kScanThreads, 4) k_scan(const __grid_constant__ ScanArgs a) {
+__global__ void __launch_bounds__(kScanThreads, 1) k_scan(const __grid_constant__ ScanArgs a) {
   __shared__ uint32_t s_cnt[kScanThreads / 32], s_sum[kScanThreads / 32];
   __shared__ uint32_t s_pre_cnt, s_pre_sum;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
