@@ -79,7 +79,7 @@ __device__ __forceinline__ uint32_t clamp255(int v) { return (uint32_t)min(255, 
 // prefix sum over its lanes, so a long MCU can use what short ones leave (the mean MCU of a
 // scene needs about a quarter). Words are stored big-endian-swapped; a lane whose MCU does
 // not fit reads the rest from global memory.
-constexpr int kStageWords = 36;  // also the colour phase's 144 B batch buffer per MCU
+constexpr int kStageWords = 32;
 
 // Shared memory of one warp: coefficients [6][64][M] int16 (zig-zag order k, lane m at
 // column m; after the row pass each data unit's slots hold its pixels, see below) and the
@@ -409,69 +409,53 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
       }
     }
 
-    // ---- colour conversion + tile stores. A tile is written in batches of 128 B (two
-    // texel rows at 4:2:0, four at 4:4:4): each lane converts its MCU's batch into the
-    // stage area (row m at 144 m bytes; the staged words are no longer needed), then the
-    // warp stores the batches of 4 MCUs per instruction as 128 B runs (coalesced).
-    const bool put = act && store;
-    uint8_t* obuf = reinterpret_cast<uint8_t*>(stage);
-    const int nbatch = __reduce_max_sync(0xFFFFFFFFu, put ? (s420 ? 8 : 2) : 0);
+    // ---- colour conversion + tile stores: each active lane writes its own MCU's tile,
+    // four texels (16 B) per store ----
+    if (act && store) {
+      uint8_t* tile = a.cache + (size_t)off * kUnitBytes;
+      if (s420) {  // 16x16 texels; chroma sample (cx, cy) covers texels 2cx..2cx+1, 2cy..2cy+1
 #pragma unroll 1
-    for (int b = 0; b < nbatch; ++b) {
-      __syncwarp();
-      if (put && (s420 || b < 2)) {
-        uint4* ob = reinterpret_cast<uint4*>(obuf + lane * 144);
-        if (s420) {  // texel rows 2b, 2b + 1 = chroma row b; chroma sample x covers texels 2x, 2x+1
+        for (int cy = 0; cy < 8; ++cy) {
 #pragma unroll
           for (int c2 = 0; c2 < 4; ++c2) {  // texels x = 4 c2 .. 4 c2 + 3
-            const uint32_t cb2 = pixel2<M>(col, 4, b, c2), cr2 = pixel2<M>(col, 5, b, c2);
+            const uint32_t cb2 = pixel2<M>(col, 4, cy, c2), cr2 = pixel2<M>(col, 5, cy, c2);
             int ro[2], go[2], bo[2];
             chroma_offsets(cb2 & 255, cr2 & 255, ro[0], go[0], bo[0]);
             chroma_offsets(cb2 >> 8, cr2 >> 8, ro[1], go[1], bo[1]);
 #pragma unroll
             for (int dy = 0; dy < 2; ++dy) {
-              const int ty = 2 * b + dy;
+              const int ty = 2 * cy + dy;
               const int du = (ty >> 3) * 2 + (c2 >> 1), ry = ty & 7, ci = (c2 & 1) * 2;
               const uint32_t ya = pixel2<M>(col, du, ry, ci), yb = pixel2<M>(col, du, ry, ci + 1);
-              ob[dy * 4 + c2] = make_uint4(ycc_pixel(ya & 255, ro[0], go[0], bo[0]),
-                                           ycc_pixel(ya >> 8, ro[0], go[0], bo[0]),
-                                           ycc_pixel(yb & 255, ro[1], go[1], bo[1]),
-                                           ycc_pixel(yb >> 8, ro[1], go[1], bo[1]));
-            }
-          }
-        } else {  // 4:4:4: texel rows 4b .. 4b + 3 of 8 texels; Y Cb Cr data units 0 1 2
-#pragma unroll
-          for (int r = 0; r < 4; ++r) {
-            const int ty = 4 * b + r;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {  // texels x = 4h .. 4h + 3
-              uint32_t o[4];
-#pragma unroll
-              for (int j = 0; j < 2; ++j) {
-                const uint32_t y2 = pixel2<M>(col, 0, ty, 2 * h + j), b2 = pixel2<M>(col, 1, ty, 2 * h + j),
-                               r2 = pixel2<M>(col, 2, ty, 2 * h + j);
-#pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                  int ro, go, bo;
-                  chroma_offsets((b2 >> (8 * e)) & 255, (r2 >> (8 * e)) & 255, ro, go, bo);
-                  o[2 * j + e] = ycc_pixel((y2 >> (8 * e)) & 255, ro, go, bo);
-                }
-              }
-              ob[r * 2 + h] = make_uint4(o[0], o[1], o[2], o[3]);
+              uint4 o;
+              o.x = ycc_pixel(ya & 255, ro[0], go[0], bo[0]);
+              o.y = ycc_pixel(ya >> 8, ro[0], go[0], bo[0]);
+              o.z = ycc_pixel(yb & 255, ro[1], go[1], bo[1]);
+              o.w = ycc_pixel(yb >> 8, ro[1], go[1], bo[1]);
+              *reinterpret_cast<uint4*>(tile + (ty * 16 + 4 * c2) * 4) = o;
             }
           }
         }
-      }
-      __syncwarp();
-      // chunk j of MCU m: lanes 8q .. 8q + 7 store the 8 chunks of MCU 4 i + q
+      } else {  // 4:4:4, 8x8 texels, Y Cb Cr data units 0 1 2
+#pragma unroll 1
+        for (int ty = 0; ty < 8; ++ty) {
 #pragma unroll
-      for (int i = 0; i < M / 4; ++i) {
-        const int m = 4 * i + (lane >> 3), j = lane & 7;
-        const uint32_t om = __shfl_sync(0xFFFFFFFFu, off, m);
-        const bool pm = __shfl_sync(0xFFFFFFFFu, put && (s420 || b < 2), m);
-        if (pm)
-          *reinterpret_cast<uint4*>(a.cache + (size_t)om * kUnitBytes + b * 128 + j * 16) =
-              *reinterpret_cast<const uint4*>(obuf + m * 144 + j * 16);
+          for (int h = 0; h < 2; ++h) {  // texels x = 4h .. 4h + 3
+            uint32_t o[4];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+              const uint32_t y2 = pixel2<M>(col, 0, ty, 2 * h + j), b2 = pixel2<M>(col, 1, ty, 2 * h + j),
+                             r2 = pixel2<M>(col, 2, ty, 2 * h + j);
+#pragma unroll
+              for (int e = 0; e < 2; ++e) {
+                int ro, go, bo;
+                chroma_offsets((b2 >> (8 * e)) & 255, (r2 >> (8 * e)) & 255, ro, go, bo);
+                o[2 * j + e] = ycc_pixel((y2 >> (8 * e)) & 255, ro, go, bo);
+              }
+            }
+            *reinterpret_cast<uint4*>(tile + (ty * 8 + 4 * h) * 4) = make_uint4(o[0], o[1], o[2], o[3]);
+          }
+        }
       }
     }
     __syncwarp();  // the buffers are cleared for the next items
