@@ -38,6 +38,12 @@ UNIT = "blocks/s"
 WORKLOAD = "4K frame 3840x2160, 64 JPEG textures 1024-4096^2 Q50-95 4:2:0 full mip chains, bilinear"
 
 
+# DRAM bytes (read + write) per launch of each pass's kernel in the ncu capture summarised in
+# profiles/frame_4k_kernels.md (this workload, the current kernel code). A kernel changed since
+# its capture must be set back to None.
+NCU_TRAFFIC = {"mark": 93.81e6, "compact": 2.75e6, "decode": 2.10e6, "colorize": 132.64e6}
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -424,7 +430,7 @@ def run_gpu(args, rank, world, local_rank):
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
             "passes_ms": mean,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                         "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(dom), "peak_kind": peak_kind,
                          "algorithmic_bytes": alg[dom]},
             "frame_roofline": {"achieved": sum(alg.values()) / (frame_ms * 1e-3) / 1e9, "unit": "GB/s",
                                "frac": sum(alg.values()) / (frame_ms * 1e-3) / 1e9 / peak},
