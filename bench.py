@@ -268,6 +268,56 @@ def run_views(ctx, ts, jt, dev, flush, stream, steps):
             "blocks_per_s": union / (ms_graph * 1e-3)}
 
 
+def mcu_grid(ts, width: int = 2048):
+    """G-buffer with one pixel on every MCU of every uploaded level (nearest marks each MCU once)."""
+    import synth
+    uvs, texs = [], []
+    for t, l, e in ts.uploads():
+        mw = 16 if e.sampling == 420 else 8
+        mx, my = -(-e.width // mw), -(-e.height // mw)
+        gx, gy = np.meshgrid(np.arange(mx), np.arange(my))
+        tx = np.minimum(gx * mw + mw // 2, e.width - 1)
+        ty = np.minimum(gy * mw + mw // 2, e.height - 1)
+        uvs.append(np.stack([(tx + 0.5) / e.width, (ty + 0.5) / e.height], -1).reshape(-1, 2))
+        texs.append(np.full(mx * my, t, np.uint16))
+    uv = np.concatenate(uvs).astype(np.float32)
+    n, h = uv.shape[0], -(-uv.shape[0] // width)
+    U = np.zeros((h * width, 2), np.float32)
+    T = np.full(h * width, 0xFFFF, np.uint16)
+    U[:n], T[:n] = uv, np.concatenate(texs)
+    return synth.GBuffer(width, h, U.reshape(h, width, 2), T.reshape(h, width), np.zeros((h, width), np.uint8))
+
+
+def run_full_decode(jt, dev, flush, stream, steps, peak, tuning, ntex=16):
+    """Full-decode stress in the shape of the 256-texture case, at 16 textures: 4096^2 at
+    quality 90, half 4:4:4 and half 4:2:0, level 0; every MCU is decoded (compaction +
+    decode timed, after one mark of an MCU-grid G-buffer)."""
+    import torch
+    import synth
+    ts = synth.config4_textures(ntex=ntex)
+    units = sum(e.nmcu * (4 if e.sampling == 420 else 1) for _, _, e in ts.uploads())
+    ctx = jt.Context(dev.index, max_cache_blocks=units // 4 + 1024)
+    ctx.upload_set(ts)
+    ctx.set_tuning(**tuning)  # the frame's autotuned launch shapes
+    dgb = jt.DeviceGBuffer.from_host(mcu_grid(ts), dev)
+
+    def one():
+        ctx.mark(dgb, jt.FILTER_NEAREST)
+        ctx.decode()
+
+    ms = timed(one, steps, 2, stream, flush)
+    st = ctx.stats()
+    ctx.close()
+    n = int(st["needed_blocks"])
+    cbytes = sum(float(e.scan_bits) / 8 for _, _, e in ts.uploads())
+    tile_bytes = 256.0 * int(st["cache_units"])
+    moved = cbytes + 10.0 * n + 8.0 * n + tile_bytes  # stream + index + slot/work + tiles
+    return {"workload": f"{ntex} textures 4096^2 Q90 (half 4:4:4, half 4:2:0), every MCU", "mcus": n,
+            "ms_mark_compact_decode": ms, "blocks_per_s": n / (ms * 1e-3),
+            "hbm_gbs": moved / (ms * 1e-3) / 1e9, "hbm_frac": moved / (ms * 1e-3) / 1e9 / peak,
+            "compressed_mb": cbytes / 1e6, "tiles_mb": tile_bytes / 1e6}
+
+
 def run_adjoint(jt, dev, flush, stream, steps, peak):
     """Differentiable colourise: 16 coefficient textures 2048^2 (float32 dequantised DCT,
     403 MB), 1920x1080 perspective plane, bilinear; forward F, then the adjoint of
@@ -448,6 +498,7 @@ def run_gpu(args, rank, world, local_rank):
         if not args.no_extra:
             line["batched_views"] = run_views(ctx, ts, jt, dev, flush, stream, 20)
             line["adjoint"] = run_adjoint(jt, dev, flush, stream, 20, peak)
+            line["full_decode"] = run_full_decode(jt, dev, flush, stream, 5, peak, ctx.tuning())
         print(json.dumps(line), flush=True)
     ctx.close()
     return 0

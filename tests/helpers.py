@@ -64,3 +64,26 @@ def frame(ctx, dgb, filt, torch):
     ctx.decode()
     ctx.colorize(dgb, filt, out)
     return out
+
+
+def mcu_grid_gbuffer(ts, width: int = 2048) -> synth.GBuffer:
+    """One pixel at a texel of every MCU of every uploaded level (nearest filtering marks each
+    MCU exactly once), packed row-major into a G-buffer `width` pixels wide (tail empty)."""
+    uvs, texs, mips = [], [], []
+    for t, l, e in ts.uploads():
+        mw = 16 if e.sampling == 420 else 8
+        mx, my = -(-e.width // mw), -(-e.height // mw)
+        gx, gy = np.meshgrid(np.arange(mx), np.arange(my))
+        tx = np.minimum(gx * mw + mw // 2, e.width - 1)
+        ty = np.minimum(gy * mw + mw // 2, e.height - 1)
+        uvs.append(np.stack([(tx + 0.5) / e.width, (ty + 0.5) / e.height], -1).reshape(-1, 2))
+        texs.append(np.full(mx * my, t, np.uint16))
+        mips.append(np.full(mx * my, l, np.uint8))
+    uv = np.concatenate(uvs).astype(np.float32)
+    n = uv.shape[0]
+    h = -(-n // width)
+    U = np.zeros((h * width, 2), np.float32)
+    T = np.full(h * width, 0xFFFF, np.uint16)
+    M = np.zeros(h * width, np.uint8)
+    U[:n], T[:n], M[:n] = uv, np.concatenate(texs), np.concatenate(mips)
+    return synth.GBuffer(width, h, U.reshape(h, width, 2), T.reshape(h, width), M.reshape(h, width))

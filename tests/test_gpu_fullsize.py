@@ -89,3 +89,35 @@ def test_config5_adjoint_full_size(jt):
     scale = np.abs(fd).max()
     np.testing.assert_allclose(g.ravel()[pick], fd, rtol=0, atol=2e-5 * scale)
     ctx.close()
+
+
+def test_full_decode_4096_both_samplings(jt):
+    """Full-decode stress shape: 4096^2 textures at quality 90, one 4:4:4 and one 4:2:0;
+    every MCU decoded. All tiles, assembled into images, equal the oracle's sequential
+    decode of the whole texture."""
+    ts = synth.make_texture_set(synth.SEED_BASE + 4, [(4096, 4096)] * 2, [90, 90], [444, 420], full_chain=False)
+    from helpers import mcu_grid_gbuffer
+    gb = mcu_grid_gbuffer(ts)
+    nmcu = ts.total_mcus()
+    ctx = jt.Context(0, max_cache_blocks=(262144 + 4 * 65536) // 4 + 1024)
+    ctx.upload_set(ts)
+    dgb = jt.DeviceGBuffer.from_host(gb)
+    ctx.mark(dgb, jt.FILTER_NEAREST)
+    ctx.decode()
+    st = ctx.stats()
+    assert st["needed_blocks"] == nmcu
+    work = ctx.work_list()
+    np.testing.assert_array_equal(work, np.arange(nmcu, dtype=np.uint32))
+    slots = ctx.slots(0, nmcu)
+    cache = ctx.cache_units(0, int(st["cache_units"]))
+    g0 = 0
+    for t, l, e in ts.uploads():
+        mw = 16 if e.sampling == 420 else 8
+        units = mw * mw * 4 // 256
+        mx, my = e.width // mw, e.height // mw
+        s = slots[g0:g0 + mx * my].astype(np.int64)
+        tiles = np.stack([cache[s + u] for u in range(units)], 1).reshape(my, mx, mw, mw, 4)
+        img = tiles.transpose(0, 2, 1, 3, 4).reshape(my * mw, mx * mw, 4)
+        np.testing.assert_array_equal(img, oracle.Decoded(e.jfif).rgba)
+        g0 += mx * my
+    ctx.close()
