@@ -98,12 +98,15 @@ typedef struct {
 } jt_view;
 
 typedef struct {
-  uint64_t needed_blocks;   /* MCUs in the last compaction's work list */
+  uint64_t needed_blocks;   /* MCUs in the last compaction's work list (decoded by the frame) */
   uint64_t cache_units;     /* 256-byte block-cache units those MCUs occupy */
   uint64_t capacity_units;  /* block-cache capacity in 256-byte units */
   uint64_t total_blocks;    /* MCUs over all uploaded levels (the key space) */
   uint32_t levels;          /* uploaded (texture, level) pairs */
   uint32_t error_bits;      /* JT_DEVERR_* bits seen since the last jt_get_stats */
+  uint64_t visible_blocks;  /* MCUs the last frame needed (= needed_blocks without the block cache) */
+  uint64_t resident_blocks; /* MCUs resident in the cross-frame block cache (0 without it) */
+  uint64_t evicted_blocks;  /* blocks evicted since the last jt_get_stats (0 without the cache) */
 } jt_stats;
 
 /* Launch configuration picked by the autotuner (or set by hand). */
@@ -199,6 +202,19 @@ jt_status jt_set_tuning(jt_ctx* ctx, const jt_tuning* t);
  * fastest in the context and returns it with its median frame time in milliseconds. */
 jt_status jt_autotune(jt_ctx* ctx, const jt_view* views, int nviews, int filter, jt_stream stream, int reps,
                       jt_tuning* best, float* best_ms);
+
+/* ---- cross-frame block cache (Sec. 4.1 "Texture Block Cache", Sec. 4.5 "Update Cache") ----- */
+
+/* persistent = 1: decoded MCUs stay in the block cache between frames, each in a 1 KiB block
+ * (a quarter used at 4:4:4). A frame's compaction step becomes a cache update: the blocks
+ * of resident MCUs that no pixel of the frame needs are evicted, the needed MCUs that are
+ * not resident get free blocks and are the only ones decoded, and every needed MCU's slot
+ * points at its block. Frames, graphs and jt_mark/jt_decode use it; jt_frame_plain refuses
+ * it. Block numbers and the work-list order depend on atomic order; tiles and pixels do
+ * not. More needed MCUs than blocks set JT_DEVERR_CAPACITY. An upload empties the cache.
+ * persistent = 0 (the default): every frame decodes its whole needed set.
+ * Switching mode empties the cache; the call synchronises the device. */
+jt_status jt_set_block_cache(jt_ctx* ctx, int persistent);
 
 /* ---- inspection (tests, tools) ---------------------------------------------------------- */
 

@@ -56,7 +56,9 @@ class jt_view(ctypes.Structure):
 class jt_stats(ctypes.Structure):
     _fields_ = [("needed_blocks", ctypes.c_uint64), ("cache_units", ctypes.c_uint64),
                 ("capacity_units", ctypes.c_uint64), ("total_blocks", ctypes.c_uint64),
-                ("levels", ctypes.c_uint32), ("error_bits", ctypes.c_uint32)]
+                ("levels", ctypes.c_uint32), ("error_bits", ctypes.c_uint32),
+                ("visible_blocks", ctypes.c_uint64), ("resident_blocks", ctypes.c_uint64),
+                ("evicted_blocks", ctypes.c_uint64)]
 
 
 class jt_tuning(ctypes.Structure):
@@ -98,6 +100,7 @@ _SIGS = {
     "jt_colorize_float": [_P, ctypes.POINTER(jt_gbuffer), _P, _P, _P],
     "jt_colorize_backward": [_P, ctypes.POINTER(jt_gbuffer), _P, _P, _P],
     "jt_compact_static": [_P, ctypes.c_uint32, _P, _P, ctypes.c_uint32, _P, _P],
+    "jt_set_block_cache": [_P, _I],
 }
 
 STATIC_COMPACT_MAX_FLAGS = 1 << 24  # JT_STATIC_COMPACT_MAX_FLAGS
@@ -346,6 +349,10 @@ class Context:
         if sampling == 420:
             return self.cache_units(off, 4).reshape(16, 16, 4)
         return self.cache_units(off, 1).reshape(8, 8, 4)
+
+    def set_block_cache(self, persistent: bool) -> None:
+        """Cross-frame block cache on (decode only MCUs not already resident) or off."""
+        self._check(lib().jt_set_block_cache(self._h, 1 if persistent else 0))
 
     # ---- float chain ----
     def register_coeff_textures(self, first_tex_id: int, count: int, width: int, height: int):

@@ -66,6 +66,15 @@ struct jt_ctx {
   uint8_t* cache = nullptr;
   FrameState* state = nullptr;
 
+  // cross-frame block cache (jt_set_block_cache)
+  bool persistent = false;
+  uint32_t* resident = nullptr;   // [ngid]
+  uint32_t* block_gid = nullptr;  // [nblocks]
+  uint32_t* free_list = nullptr;  // [nblocks]
+  uint32_t nblocks = 0;
+  uint64_t resident_ngid = 0;     // gids covered by `resident`
+  CacheState* cstate = nullptr;
+
   // coefficient textures (float chain)
   int coef_first = -1, coef_count = 0, coef_w = 0, coef_h = 0;
   uint32_t coef_gid_base = 0;
@@ -360,6 +369,65 @@ jt_status enqueue_scan(jt_ctx* c, uint64_t gid_lo, uint64_t gid_hi, cudaStream_t
   return check_launch(c, "scan");
 }
 
+// Frees the cross-frame block cache's arrays.
+void cache_free(jt_ctx* c) {
+  dev_free(c->resident);
+  dev_free(c->block_gid);
+  dev_free(c->free_list);
+  dev_free(c->cstate);
+  c->nblocks = 0;
+  c->resident_ngid = 0;
+}
+
+// (Re)builds an empty cross-frame block cache over the current gids and the whole block cache.
+jt_status cache_reset(jt_ctx* c) {
+  cache_free(c);
+  c->nblocks = (uint32_t)(c->cap_units / 4);
+  c->resident_ngid = c->ngid;
+  jt_status s;
+  if ((s = dev_alloc(c, &c->resident, std::max<uint64_t>(1, c->ngid) * 4)) != JT_OK) return s;
+  if ((s = dev_alloc(c, &c->block_gid, std::max<uint32_t>(1, c->nblocks) * 4)) != JT_OK) return s;
+  if ((s = dev_alloc(c, &c->free_list, std::max<uint32_t>(1, c->nblocks) * 4)) != JT_OK) return s;
+  if ((s = dev_alloc(c, &c->cstate, sizeof(CacheState))) != JT_OK) return s;
+  std::vector<uint32_t> fl(c->nblocks);
+  for (uint32_t i = 0; i < c->nblocks; ++i) fl[i] = c->nblocks - 1 - i;  // pops give 0, 1, 2, ...
+  const CacheState cs{c->nblocks, 0, 0, 0};
+  JT_CUDA(c, cudaMemset(c->resident, 0xFF, std::max<uint64_t>(1, c->ngid) * 4));
+  JT_CUDA(c, cudaMemset(c->block_gid, 0xFF, std::max<uint32_t>(1, c->nblocks) * 4));
+  JT_CUDA(c, cudaMemcpy(c->free_list, fl.data(), (size_t)c->nblocks * 4, cudaMemcpyHostToDevice));
+  JT_CUDA(c, cudaMemcpy(c->cstate, &cs, sizeof cs, cudaMemcpyHostToDevice));
+  return JT_OK;
+}
+
+// The cache update of a persistent-cache frame, in place of the compaction: evict the blocks
+// of MCUs the frame does not need, give the needed non-resident ones blocks and a place in the
+// work list, set every needed MCU's slot.
+jt_status enqueue_cache_update(jt_ctx* c, cudaStream_t s) {
+  if (c->resident_ngid != c->ngid) {  // levels were uploaded since: start over
+    jt_status st = cache_reset(c);
+    if (st != JT_OK) return st;
+  }
+  CacheArgs a{};
+  a.flags = c->flags;
+  a.n = (uint32_t)c->ngid;
+  a.resident = c->resident;
+  a.block_gid = c->block_gid;
+  a.free_list = c->free_list;
+  a.nblocks = c->nblocks;
+  a.slot = c->slot;
+  a.work = c->work;
+  a.work_cap = (uint32_t)c->gid_cap;
+  a.state = c->state;
+  a.cs = c->cstate;
+  launch_cache_update(a, c->sm_count * 8, s);
+  return check_launch(c, "cache update");
+}
+
+// The frame's compaction step: the prefix-sum scan, or the cache update in persistent mode.
+jt_status enqueue_compact(jt_ctx* c, cudaStream_t s) {
+  return c->persistent ? enqueue_cache_update(c, s) : enqueue_scan(c, 0, c->ngid, s);
+}
+
 jt_status enqueue_decode(jt_ctx* c, cudaStream_t s) {
   DecodeArgs a{};
   a.descs = c->d_descs;
@@ -406,7 +474,7 @@ jt_status enqueue_frame(jt_ctx* c, const ViewSet& vs, int filter, cudaStream_t s
   mark_time(0);
   if ((st = enqueue_mark(c, vs, filter, -1, 0, s)) != JT_OK) return st;
   mark_time(1);
-  if ((st = enqueue_scan(c, 0, c->ngid, s)) != JT_OK) return st;
+  if ((st = enqueue_compact(c, s)) != JT_OK) return st;
   mark_time(2);
   if ((st = enqueue_decode(c, s)) != JT_OK) return st;
   mark_time(3);
@@ -554,6 +622,7 @@ jt_status jt_destroy(jt_ctx* c) {
   dev_free(c->tile_status);
   dev_free(c->cache);
   dev_free(c->d_desc_of_gid);
+  cache_free(c);
   dev_free(c->state);
   dev_free(c->float_tiles);
   if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
@@ -732,7 +801,7 @@ jt_status jt_decode(jt_ctx* c, jt_stream stream) {
   DeviceGuard dg(c->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   jt_status s;
-  if ((s = enqueue_scan(c, 0, c->ngid, st)) != JT_OK) return s;
+  if ((s = enqueue_compact(c, st)) != JT_OK) return s;
   if ((s = enqueue_decode(c, st)) != JT_OK) return s;
   c->phase = Phase::Decoded;
   c->last_stream = st;
@@ -770,6 +839,17 @@ jt_status jt_get_stats(jt_ctx* c, jt_stats* out) {
   out->total_blocks = c->ngid;
   out->levels = (uint32_t)c->descs.size();
   out->error_bits = fs.err;
+  out->visible_blocks = fs.count;
+  out->resident_blocks = 0;
+  out->evicted_blocks = 0;
+  if (c->persistent && c->cstate) {
+    CacheState cs;
+    JT_CUDA(c, cudaMemcpy(&cs, c->cstate, sizeof cs, cudaMemcpyDeviceToHost));
+    JT_CUDA(c, cudaMemset(&c->cstate->evicted, 0, sizeof(uint32_t)));
+    out->visible_blocks = cs.visible;
+    out->resident_blocks = c->nblocks - cs.free_count;
+    out->evicted_blocks = cs.evicted;
+  }
   if (fs.err & JT_DEVERR_CORRUPT) return fail(c, JT_ERR_CORRUPT_STREAM, "corrupt entropy-coded data in a needed MCU");
   if (fs.err & JT_DEVERR_CAPACITY) return fail(c, JT_ERR_CAPACITY, "needed %u cache units, capacity %llu", fs.units,
                                               (unsigned long long)c->cap_units);
@@ -855,6 +935,7 @@ jt_status jt_frame_plain(jt_ctx* c, const jt_view* views, int nviews, int filter
   if (!valid_filter(filter)) return fail(c, JT_ERR_INVALID_ARG, "bad filter %d", filter);
   if (c->phase == Phase::Marked) return fail(c, JT_ERR_STATE, "a marked frame is pending");
   if (c->descs.empty()) return fail(c, JT_ERR_STATE, "no textures uploaded");
+  if (c->persistent) return fail(c, JT_ERR_STATE, "the per-texture pipeline needs the per-frame cache mode");
   ViewSet all;
   jt_status s = make_views(c, views, nviews, true, all);
   if (s != JT_OK) return s;
@@ -1011,6 +1092,18 @@ jt_status jt_read_cache(jt_ctx* c, uint64_t unit_begin, uint64_t n, uint8_t* dst
   JT_CUDA(c, cudaStreamSynchronize(c->last_stream));
   if (n) JT_CUDA(c, cudaMemcpy(dst, c->cache + unit_begin * kUnitBytes, n * kUnitBytes, cudaMemcpyDefault));
   return JT_OK;
+}
+
+jt_status jt_set_block_cache(jt_ctx* c, int persistent) {
+  if (!c) return JT_ERR_INVALID_ARG;
+  if (persistent != 0 && persistent != 1) return fail(c, JT_ERR_INVALID_ARG, "mode must be 0 or 1");
+  if (c->phase == Phase::Marked) return fail(c, JT_ERR_STATE, "a marked frame is pending");
+  DeviceGuard dg(c->device);
+  JT_CUDA(c, cudaDeviceSynchronize());
+  cache_free(c);
+  c->persistent = persistent == 1;
+  c->phase = Phase::Idle;
+  return c->persistent ? cache_reset(c) : JT_OK;
 }
 
 // ---- float chain ------------------------------------------------------------------------

@@ -169,6 +169,29 @@ constexpr int kScanTile = kScanThreads * kScanPerThread;
 void launch_scan(const ScanArgs& a, int grid, cudaStream_t s);
 int scan_max_ctas_per_sm();  // resident CTAs per SM (the grid must not exceed SMs x this)
 
+// Cross-frame block cache (Sec. 4.1, Sec. 4.5): resident[gid] = block or ~0, block_gid[block]
+// = gid or ~0, free_list[0 .. free_count) = free blocks (a stack). A block is 4 cache units.
+struct CacheState {
+  uint32_t free_count;  // blocks on the free stack
+  uint32_t taken;       // blocks the current allocation pass has taken from its top
+  uint32_t visible;     // MCUs the last frame needed
+  uint32_t evicted;     // blocks evicted since the counter was last cleared
+};
+struct CacheArgs {
+  uint8_t* flags;  // flags[gid], cleared by the allocation pass
+  uint32_t n;      // gids
+  uint32_t* resident;
+  uint32_t* block_gid;
+  uint32_t* free_list;
+  uint32_t nblocks;
+  uint32_t* slot;
+  uint32_t* work;
+  uint32_t work_cap;
+  FrameState* state;
+  CacheState* cs;
+};
+void launch_cache_update(const CacheArgs& a, int grid, cudaStream_t s);
+
 struct DecodeArgs {
   const DevDesc* descs;
   uint32_t ndesc;
