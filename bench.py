@@ -318,6 +318,50 @@ def run_full_decode(jt, dev, flush, stream, steps, peak, tuning, ntex=16):
             "compressed_mb": cbytes / 1e6, "tiles_mb": tile_bytes / 1e6}
 
 
+def run_motion(jt, ts, dev, flush, stream, nframes=24, W=1920, H=1080):
+    """A camera turning 6 degrees per frame over the 64 textures at 1920x1080 (the paper's
+    motion test, shortened): per-frame time with the cross-frame block cache against the
+    per-frame mode, both as graph replays fed each frame's G-buffer."""
+    import torch
+    import synth
+    pose0 = synth.config2_pose()
+    frames = [synth.gbuffer_scene(synth.SEED_BASE + 2, W, H, ts.sizes, ts.nlevels,
+                                  synth.Pose(pose0.cam, pose0.yaw + 6.0 * k, pose0.pitch, pose0.vfov, pose0.quad_seed,
+                                             0.0), nquads=200) for k in range(nframes)]
+    dframes = [jt.DeviceGBuffer.from_host(f, dev) for f in frames]
+    res = {}
+    for mode in ("per_frame", "block_cache"):
+        ctx = jt.Context(dev.index, max_cache_blocks=1 << 18)
+        ctx.upload_set(ts)
+        ctx.set_block_cache(mode == "block_cache")
+        dv = jt.DeviceGBuffer.from_host(frames[0], dev)
+        out = torch.empty((H, W, 4), dtype=torch.uint8, device=dev)
+        g = ctx.frame_graph([(dv, out)], jt.FILTER_BILINEAR)
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        ms, decoded = [], []
+        for rep in range(2):  # the second pass over the sequence is timed (warm caches)
+            for k, f in enumerate(dframes):
+                dv.uv.copy_(f.uv)
+                dv.tex_id.copy_(f.tex_id)
+                dv.mip.copy_(f.mip)
+                flush.fill_(k & 255)
+                a0.record(stream)
+                ctx.graph_launch(g)
+                a1.record(stream)
+                a1.synchronize()
+                if rep == 1:
+                    ms.append(a0.elapsed_time(a1))
+                    decoded.append(int(ctx.stats()["needed_blocks"]))
+        ctx.graph_destroy(g)
+        ctx.close()
+        res[mode] = {"median_ms": float(np.median(ms)), "max_ms": float(max(ms)),
+                     "mean_decoded_blocks": float(np.mean(decoded))}
+    res["workload"] = f"{nframes} frames {W}x{H}, camera turning 6 deg/frame, 64 textures, bilinear"
+    res["speedup_median"] = res["per_frame"]["median_ms"] / res["block_cache"]["median_ms"]
+    return res
+
+
 def run_adjoint(jt, dev, flush, stream, steps, peak):
     """Differentiable colourise: 16 coefficient textures 2048^2 (float32 dequantised DCT,
     403 MB), 1920x1080 perspective plane, bilinear; forward F, then the adjoint of
@@ -499,6 +543,7 @@ def run_gpu(args, rank, world, local_rank):
             line["batched_views"] = run_views(ctx, ts, jt, dev, flush, stream, 20)
             line["adjoint"] = run_adjoint(jt, dev, flush, stream, 20, peak)
             line["full_decode"] = run_full_decode(jt, dev, flush, stream, 5, peak, ctx.tuning())
+            line["motion"] = run_motion(jt, ts, dev, flush, stream)
         print(json.dumps(line), flush=True)
     ctx.close()
     return 0
