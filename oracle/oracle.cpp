@@ -490,14 +490,20 @@ struct Taps {
   float fx, fy;  // bilinear fractions
 };
 
-Taps pixel_taps(float u, float v, int w, int h, int filter) {
+// filter 0: the nearest texel; 1: the four bilinear taps; 2: the bilinear taps clamped to
+// the MCU of the nearest texel (Sec. 4.4, the mode of the linear-interpolation timing in
+// Sec. 6.2): along each axis a tap in another MCU (mw texels wide) is replaced by the
+// nearest texel's coordinate, so all four fetches fall in one MCU.
+Taps pixel_taps(float u, float v, int w, int h, int filter, int mw = 16) {
   Taps t{};
   volatile float uw = u * (float)w;  // one fp32 rounding, no fused multiply-add
   volatile float vh = v * (float)h;
+  const int nx = (int)floor_mod((int64_t)std::floor((float)uw), w);
+  const int ny = (int)floor_mod((int64_t)std::floor((float)vh), h);
   if (filter == 0) {
     t.n = 1;
-    t.x[0] = (int)floor_mod((int64_t)std::floor((float)uw), w);
-    t.y[0] = (int)floor_mod((int64_t)std::floor((float)vh), h);
+    t.x[0] = nx;
+    t.y[0] = ny;
   } else {
     volatile float xs = (float)uw - 0.5f;
     volatile float ys = (float)vh - 0.5f;
@@ -507,6 +513,12 @@ Taps pixel_taps(float u, float v, int w, int h, int filter) {
     int64_t x0 = (int64_t)x0f, y0 = (int64_t)y0f;
     int xa = (int)floor_mod(x0, w), xb = (int)floor_mod(x0 + 1, w);
     int ya = (int)floor_mod(y0, h), yb = (int)floor_mod(y0 + 1, h);
+    if (filter == 2) {
+      if (xa / mw != nx / mw) xa = nx;
+      if (xb / mw != nx / mw) xb = nx;
+      if (ya / mw != ny / mw) ya = ny;
+      if (yb / mw != ny / mw) yb = ny;
+    }
     t.n = 4;
     t.x[0] = xa; t.y[0] = ya;
     t.x[1] = xb; t.y[1] = ya;
@@ -662,7 +674,8 @@ int64_t jto_mark(void* s, const float* uv, const uint16_t* tex, const uint8_t* m
       ++bad;
       continue;
     }
-    Taps t = pixel_taps(uv[2 * p], uv[2 * p + 1], L->w, L->h, filter);
+    // the clamped mode needs only the nearest texel's MCU
+    Taps t = pixel_taps(uv[2 * p], uv[2 * p + 1], L->w, L->h, filter == 2 ? 0 : filter);
     for (int i = 0; i < t.n; ++i) flags[L->gid_base + mcu_of(*L, t.x[i], t.y[i])] = 1;
   }
   return bad;
@@ -693,8 +706,8 @@ int64_t jto_colorize(void* s, const float* uv, const uint16_t* tex, const uint8_
       ++bad;
       continue;
     }
-    Taps t = pixel_taps(uv[2 * p], uv[2 * p + 1], L->w, L->h, filter);
     const int mw = L->mw();
+    Taps t = pixel_taps(uv[2 * p], uv[2 * p + 1], L->w, L->h, filter, mw);
     double c[4][3];
     bool ok = true;
     for (int i = 0; i < t.n; ++i) {

@@ -47,8 +47,10 @@ def test_paper_mcu_geometry():
     assert e.nmcu == 4 and e.width == 32
 
 
-def _taps_np(u, v, w, h, filt):
-    """Texel taps with fp32 index arithmetic, written with numpy."""
+def _taps_np(u, v, w, h, filt, mw=16):
+    """Texel taps with fp32 index arithmetic, written with numpy. Filter 2 (bilinear clamped
+    to one MCU, Sec. 4.4) moves, per axis, a tap outside the nearest texel's MCU onto the
+    nearest texel's row or column."""
     w32 = np.float32(w)
     h32 = np.float32(h)
     uw = (u.astype(np.float32) * w32).astype(np.float32)
@@ -67,6 +69,10 @@ def _taps_np(u, v, w, h, filt):
     y0 = y0.astype(np.int64)
     xa, xb = np.mod(x0, w), np.mod(x0 + 1, w)
     ya, yb = np.mod(y0, h), np.mod(y0 + 1, h)
+    if filt == 2:
+        (nx, ny), = _taps_np(u, v, w, h, 0)[0]
+        xa, xb = [np.where(t // mw == nx // mw, t, nx) for t in (xa, xb)]
+        ya, yb = [np.where(t // mw == ny // mw, t, ny) for t in (ya, yb)]
     return [(xa, ya), (xb, ya), (xa, yb), (xb, yb)], fx, fy
 
 
@@ -82,7 +88,7 @@ def _brute_marks(ts, gb, filt):
         sel = (tex == t) & (mip == l)
         if sel.any():
             mw = 16 if e.sampling == 420 else 8
-            for x, y in _taps_np(u[sel], v[sel], e.width, e.height, filt)[0]:
+            for x, y in _taps_np(u[sel], v[sel], e.width, e.height, filt, mw)[0]:
                 keys |= set((gid + x // mw + (y // mw) * e.mcus_x).tolist())
         gid += e.nmcu
     return keys
@@ -95,7 +101,7 @@ def _small_scene(seed=3, W=320, H=180, nq=30):
     return ts, gb
 
 
-@pytest.mark.parametrize("filt", [0, 1])
+@pytest.mark.parametrize("filt", [0, 1, 2])
 def test_mark_equals_brute_force_config1(filt):
     ts, gb = synth.config1()
     o = oracle.texset_from(ts)
@@ -103,7 +109,7 @@ def test_mark_equals_brute_force_config1(filt):
     assert set(np.nonzero(flags)[0].tolist()) == _brute_marks(ts, gb, filt)
 
 
-@pytest.mark.parametrize("filt", [0, 1])
+@pytest.mark.parametrize("filt", [0, 1, 2])
 def test_mark_equals_brute_force_scene(filt):
     ts, gb = _small_scene()
     o = oracle.texset_from(ts)
@@ -120,12 +126,13 @@ def _full_textures(ts):
     return {(t, l): oracle.Decoded(e.jfif).rgba for t, l, e in ts.uploads()}
 
 
-@pytest.mark.parametrize("filt", [0, 1])
+@pytest.mark.parametrize("filt", [0, 1, 2])
 def test_colorize_equals_full_decode(filt):
     ts, gb = _small_scene(seed=5)
     o = oracle.texset_from(ts)
     out = o.colorize(gb.uv, gb.tex_id, gb.mip, filt)
     full = _full_textures(ts)
+    mws = {(t, l): 16 if e.sampling == 420 else 8 for t, l, e in ts.uploads()}
     ref = np.zeros(gb.tex_id.shape + (3,), np.float64)
     valid = gb.tex_id != 0xFFFF
     for (t, l), img in full.items():
@@ -133,7 +140,8 @@ def test_colorize_equals_full_decode(filt):
         if not sel.any():
             continue
         h, w = img.shape[:2]
-        taps, fx, fy = _taps_np(gb.uv[..., 0][sel], gb.uv[..., 1][sel], w, h, filt)
+        mw = mws[(t, l)]
+        taps, fx, fy = _taps_np(gb.uv[..., 0][sel], gb.uv[..., 1][sel], w, h, filt, mw)
         c = [img[y, x, :3].astype(np.float64) for x, y in taps]
         if filt == 0:
             ref[sel] = c[0]
@@ -152,3 +160,35 @@ def test_colorize_equals_full_decode(filt):
     # exactly the marked MCUs were decoded
     flags = o.mark(gb, filt)
     assert o.cached() == int(flags.sum())
+
+
+def test_clamp_mode_reduces_to_bilinear_and_nearest():
+    """The clamped mode (Sec. 4.4) against the two plain filters: where the four bilinear taps
+    lie in the nearest texel's MCU it is the bilinear result; where the taps straddle an MCU
+    edge on both axes every tap collapses onto the nearest texel, so it is the nearest
+    result; and it marks exactly the nearest filter's MCUs."""
+    ts, gb = _small_scene(seed=7)
+    o = oracle.texset_from(ts)
+    near = o.colorize(gb.uv, gb.tex_id, gb.mip, 0)
+    bil = o.colorize(gb.uv, gb.tex_id, gb.mip, 1)
+    clamp = o.colorize(gb.uv, gb.tex_id, gb.mip, 2)
+    np.testing.assert_array_equal(o.mark(gb, 2), o.mark(gb, 0))
+    valid = gb.tex_id != 0xFFFF
+    inside = np.zeros(gb.tex_id.shape, bool)
+    both = np.zeros(gb.tex_id.shape, bool)
+    for t, l, e in ts.uploads():
+        sel = valid & (gb.tex_id == t) & (gb.mip == l)
+        if not sel.any():
+            continue
+        mw = 16 if e.sampling == 420 else 8
+        u, v = gb.uv[..., 0][sel], gb.uv[..., 1][sel]
+        (nx, ny), = _taps_np(u, v, e.width, e.height, 0)[0]
+        (xa, ya), (xb, _), (_, yb), _ = _taps_np(u, v, e.width, e.height, 1)[0]
+        same_x = (xa // mw == nx // mw) & (xb // mw == nx // mw)
+        same_y = (ya // mw == ny // mw) & (yb // mw == ny // mw)
+        inside[sel] = same_x & same_y
+        both[sel] = ~same_x & ~same_y
+    assert inside.sum() > 1000 and (valid & ~inside).sum() > 100 and both.sum() > 10
+    np.testing.assert_array_equal(clamp[inside], bil[inside])
+    np.testing.assert_array_equal(clamp[both], near[both])
+    assert (clamp[valid & ~inside] != bil[valid & ~inside]).any()
