@@ -268,6 +268,18 @@ def run_views(ctx, ts, jt, dev, flush, stream, steps):
             "blocks_per_s": union / (ms_graph * 1e-3)}
 
 
+def run_clamped(ctx, jt, dgb, out, flush, stream, steps):
+    """The 4K frame with bilinear taps clamped to the nearest texel's MCU (Sec. 4.4, the
+    linear-interpolation mode of Sec. 6.2): the mark flags one MCU per pixel, so the frame
+    decodes the nearest filter's set."""
+    g = ctx.frame_graph([(dgb, out)], jt.FILTER_BILINEAR_CLAMP)
+    ms = timed(lambda: ctx.graph_launch(g), steps, 3, stream, flush)
+    needed = int(ctx.stats()["needed_blocks"])
+    ctx.graph_destroy(g)
+    return {"workload": "as the headline frame, filter bilinear clamped to one MCU", "ms_per_frame": ms,
+            "needed_blocks_per_frame": needed, "blocks_per_s": needed / (ms * 1e-3)}
+
+
 def mcu_grid(ts, width: int = 2048):
     """G-buffer with one pixel on every MCU of every uploaded level (nearest marks each MCU once)."""
     import synth
@@ -540,6 +552,7 @@ def run_gpu(args, rank, world, local_rank):
         if tuned:
             line["tuning"] = tuned
         if not args.no_extra:
+            line["clamped_filter"] = run_clamped(ctx, jt, dgb, out, flush, stream, 20)
             line["batched_views"] = run_views(ctx, ts, jt, dev, flush, stream, 20)
             line["adjoint"] = run_adjoint(jt, dev, flush, stream, 20, peak)
             line["full_decode"] = run_full_decode(jt, dev, flush, stream, 5, peak, ctx.tuning())

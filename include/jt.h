@@ -50,8 +50,13 @@ typedef enum {
 #define JT_DEVERR_MISSING 0x4u     /* a pixel names a (texture, level) that does not exist */
 #define JT_DEVERR_TIMEOUT 0x8u     /* a bounded wait in the compaction scan gave up */
 
+/* Texture filters. BILINEAR_CLAMP (Sec. 4.4, the linear-interpolation mode timed in
+ * Sec. 6.2): the bilinear taps, except that along each axis a tap lying in another MCU than
+ * the nearest texel is moved onto the nearest texel's column or row, so one MCU serves all
+ * four fetches and the mark pass flags only the nearest texel's MCU. */
 #define JT_FILTER_NEAREST 0
 #define JT_FILTER_BILINEAR 1
+#define JT_FILTER_BILINEAR_CLAMP 2
 #define JT_MAX_VIEWS 16
 #define JT_MAX_LEVELS 16
 #define JT_EMPTY_TEXTURE 0xFFFFu
@@ -152,7 +157,7 @@ jt_status jt_upload_texture(jt_ctx* ctx, int tex_id, int level, int width, int h
 
 /* Mark (Sec. 4.2): for every pixel with a texture, computes the texel(s) its uv falls on at
  * its mip level — nearest: x = floor(u*w) mod w; bilinear: the four texels around
- * u*w - 1/2 — and flags the MCUs that hold them. Flags accumulate over calls until the
+ * u*w - 1/2; bilinear clamped: the nearest texel — and flags the MCUs that hold them. Flags accumulate over calls until the
  * next jt_decode, so several views marked in turn are decoded once (union). */
 jt_status jt_mark(jt_ctx* ctx, const jt_gbuffer* g, int filter, jt_stream stream);
 
@@ -164,7 +169,7 @@ jt_status jt_mark(jt_ctx* ctx, const jt_gbuffer* g, int filter, jt_stream stream
 jt_status jt_decode(jt_ctx* ctx, jt_stream stream);
 
 /* Resolve (Sec. 4.4): writes RGBA8 per pixel from the block cache (nearest, or bilinear
- * with fp32 weights and round-half-up). Pixels without texture get (0,0,0,255). `filter`
+ * with fp32 weights and round-half-up, with or without the clamp to the nearest MCU). Pixels without texture get (0,0,0,255). `filter`
  * must match the jt_mark call(s) of this frame. out_rgba: device, [height][width][4],
  * 16-byte aligned. */
 jt_status jt_colorize(jt_ctx* ctx, const jt_gbuffer* g, int filter, uint8_t* out_rgba, jt_stream stream);

@@ -17,10 +17,12 @@ import numpy as np
 
 from . import build as _build
 
-__all__ = ["JTError", "Context", "DeviceGBuffer", "lib", "FILTER_NEAREST", "FILTER_BILINEAR"]
+__all__ = ["JTError", "Context", "DeviceGBuffer", "lib", "FILTER_NEAREST", "FILTER_BILINEAR",
+           "FILTER_BILINEAR_CLAMP"]
 
 FILTER_NEAREST = 0
 FILTER_BILINEAR = 1
+FILTER_BILINEAR_CLAMP = 2  # bilinear taps clamped to the nearest texel's MCU (Sec. 4.4)
 MAX_VIEWS = 16
 EMPTY_TEXTURE = 0xFFFF
 

@@ -483,7 +483,9 @@ jt_status enqueue_frame(jt_ctx* c, const ViewSet& vs, int filter, cudaStream_t s
   return check_launch(c, "event record");
 }
 
-bool valid_filter(int f) { return f == JT_FILTER_NEAREST || f == JT_FILTER_BILINEAR; }
+bool valid_filter(int f) {
+  return f == JT_FILTER_NEAREST || f == JT_FILTER_BILINEAR || f == JT_FILTER_BILINEAR_CLAMP;
+}
 
 const int kMcusPerWarp[] = {4, 8, 16, 32};
 const int kDecodeWarps[] = {2, 4, 8, 16};

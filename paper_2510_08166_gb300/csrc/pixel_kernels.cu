@@ -319,6 +319,23 @@ __global__ void k_colorize(const __grid_constant__ ColorizeArgs a) {
         nearest_texel<P2>(u[i], v[i], L, tx, ty);
         const uint32_t off = slot(L.gid_base + (tx >> L.shift) + (ty >> L.shift) * L.mcus_x, L.units);
         px[i] = __ldg(cache + (size_t)off * (kUnitBytes / 4) + (((ty & mwm) << L.shift) | (tx & mwm)));
+      } else if (FILTER == JT_FILTER_BILINEAR_CLAMP) {
+        // bilinear taps clamped to the nearest texel's MCU: along each axis a tap in
+        // another MCU moves onto the nearest texel's column or row (one MCU, one slot)
+        int nx, ny, xa, xb, ya, yb;
+        float fx, fy;
+        nearest_texel<P2>(u[i], v[i], L, nx, ny);
+        bilinear_taps<P2>(u[i], v[i], L, xa, xb, ya, yb, fx, fy);
+        const int mx = nx >> L.shift, my = ny >> L.shift;
+        xa = (xa >> L.shift) == mx ? xa : nx;
+        xb = (xb >> L.shift) == mx ? xb : nx;
+        ya = (ya >> L.shift) == my ? ya : ny;
+        yb = (yb >> L.shift) == my ? yb : ny;
+        const uint32_t* tile = cache + (size_t)slot(L.gid_base + mx + my * L.mcus_x, L.units) * (kUnitBytes / 4);
+        const int ia = (ya & mwm) << L.shift, ib = (yb & mwm) << L.shift;
+        const int ja = xa & mwm, jb = xb & mwm;
+        px[i] = blend(__ldg(tile + (ia | ja)), __ldg(tile + (ia | jb)), __ldg(tile + (ib | ja)),
+                      __ldg(tile + (ib | jb)), fx, fy);
       } else {
         int xa, xb, ya, yb;
         float fx, fy;
@@ -482,7 +499,8 @@ void launch_float_scatter(const FloatArgs& a, int threads, int grid, cudaStream_
 }
 
 void launch_mark(const MarkArgs& a, int threads, int grid, cudaStream_t s) {
-  if (a.filter == JT_FILTER_NEAREST)
+  // the clamped filter reads only the nearest texel's MCU
+  if (a.filter == JT_FILTER_NEAREST || a.filter == JT_FILTER_BILINEAR_CLAMP)
     k_mark<JT_FILTER_NEAREST><<<grid, threads, 0, s>>>(a);
   else
     k_mark<JT_FILTER_BILINEAR><<<grid, threads, 0, s>>>(a);
@@ -491,6 +509,8 @@ void launch_mark(const MarkArgs& a, int threads, int grid, cudaStream_t s) {
 void launch_colorize(const ColorizeArgs& a, int threads, int grid, cudaStream_t s) {
   if (a.filter == JT_FILTER_NEAREST)
     k_colorize<JT_FILTER_NEAREST><<<grid, threads, 0, s>>>(a);
+  else if (a.filter == JT_FILTER_BILINEAR_CLAMP)
+    k_colorize<JT_FILTER_BILINEAR_CLAMP><<<grid, threads, 0, s>>>(a);
   else
     k_colorize<JT_FILTER_BILINEAR><<<grid, threads, 0, s>>>(a);
 }

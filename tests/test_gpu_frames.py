@@ -35,7 +35,7 @@ def _outs(views):
     return [torch.zeros((v.height, v.width, 4), dtype=torch.uint8, device="cuda") for v in views]
 
 
-@pytest.mark.parametrize("filt", [0, 1])
+@pytest.mark.parametrize("filt", [0, 1, 2])
 def test_batched_equals_oracle_and_union(jt, scene, filt):
     ts, views = scene
     ctx = jt.Context(0, 1 << 15)

@@ -1,7 +1,8 @@
 """GPU parity: the CUDA path (through the C ABI) against the oracle.
 
 Bars: decoded tiles bit-exact; work list equal to the oracle's compacted marks (sorted,
-unique); nearest pixels exact; bilinear pixels within 1 LSB.
+unique); nearest pixels exact; bilinear pixels (plain or clamped to the nearest MCU)
+within 1 LSB.
 """
 
 import numpy as np
@@ -26,7 +27,7 @@ def _ctx(jt, blocks=1 << 15):
     return jt.Context(0, max_cache_blocks=blocks)
 
 
-@pytest.mark.parametrize("filt", [0, 1])
+@pytest.mark.parametrize("filt", [0, 1, 2])
 def test_config1(jt, filt):
     ts, gb = synth.config1()
     ctx = _ctx(jt)
@@ -96,7 +97,7 @@ def test_mip_chain_and_many_textures(jt):
     ctx.close()
 
 
-@pytest.mark.parametrize("filt", [0, 1])
+@pytest.mark.parametrize("filt", [0, 1, 2])
 def test_small_scene(jt, filt):
     sizes = [(64, 64), (128, 128), (256, 256), (96, 48), (512, 512)]
     ts = synth.make_texture_set(3, sizes, [60, 75, 90, 50, 80], [420, 420, 444, 420, 420])
@@ -132,7 +133,7 @@ def test_flags_cleared_between_frames(jt):
     ctx.close()
 
 
-@pytest.mark.parametrize("filt", [0, 1])
+@pytest.mark.parametrize("filt", [0, 1, 2])
 def test_levels_smaller_than_an_mcu_and_odd_sizes(jt, filt):
     """Random uv (repeat wrap) over tiny and non-power-of-two levels: taps wrap inside
     a single MCU and across the last partial MCU."""
