@@ -59,6 +59,10 @@ def lib():
         L.jto_texset_add.restype = I64
         L.jto_texset_add.argtypes = [P, I, I, I, I, I, P, ctypes.c_uint64, ctypes.c_uint64, P, ctypes.c_uint64,
                                      P, P, P]
+        L.jto_texset_add_compact.restype = I64
+        L.jto_texset_add_compact.argtypes = [P, I, I, I, I, I, P, ctypes.c_uint64, P, ctypes.c_uint64, P,
+                                             ctypes.c_uint64, P, ctypes.c_uint64, ctypes.c_uint64, P, P, P]
+        L.jto_mcu_bits.argtypes = [P, I, I, P, P]
         L.jto_texset_decode_mcu.argtypes = [P, I, I, I, P]
         L.jto_mark.restype = I64
         L.jto_mark.argtypes = [P, P, P, P, I64, I, P]
@@ -197,6 +201,38 @@ class TexSet:
         self.total = int(g) + int(idx.size)
         return int(g)
 
+    def add_compact(self, tex: int, level: int, enc) -> int:
+        """Registers the level's compact form (enc.compact: the paper's byte-aligned stream,
+        two-level offset table and 12-bit DC records, Sec. 5.1 / 5.3)."""
+        c = enc.compact
+        scan = np.ascontiguousarray(c.scan, np.uint8)
+        a = np.ascontiguousarray(c.abs, np.uint32)
+        r = np.ascontiguousarray(c.rel, np.uint16)
+        dc = np.ascontiguousarray(c.dc, np.uint32)
+        qt = np.ascontiguousarray(enc.qt, np.uint16)
+        hb = np.ascontiguousarray(enc.huff_bits, np.uint8)
+        hv = np.ascontiguousarray(enc.huff_vals, np.uint8)
+        n = enc.mcus_x * enc.mcus_y
+        g = lib().jto_texset_add_compact(self._h, tex, level, enc.width, enc.height, enc.sampling, _p(scan),
+                                         scan.size, _p(a), a.size, _p(r), r.size, _p(dc), dc.size, n, _p(qt),
+                                         _p(hb), _p(hv))
+        if g < 0:
+            raise ValueError("oracle rejected compact texture level")
+        self.gid_base[(tex, level)] = int(g)
+        self.nmcu[(tex, level)] = n
+        self.total = int(g) + n
+        return int(g)
+
+    def mcu_bits(self, tex: int, level: int):
+        """Per MCU of a standard-form level: (coded bits, bits of its first luma DC and its
+        chroma DCs), from a sequential decode."""
+        n = self.nmcu[(tex, level)]
+        bits = np.empty(n, np.int64)
+        dcb = np.empty(n, np.int64)
+        if lib().jto_mcu_bits(self._h, tex, level, _p(bits), _p(dcb)) != 0:
+            raise ValueError("corrupt stream or compact level")
+        return bits, dcb
+
     def decode_mcu(self, tex: int, level: int, mcu: int, mw: int) -> np.ndarray:
         tile = np.empty((mw, mw, 4), np.uint8)
         rc = lib().jto_texset_decode_mcu(self._h, tex, level, mcu, _p(tile))
@@ -238,11 +274,12 @@ class TexSet:
         lib().jto_texset_clear_cache(self._h)
 
 
-def texset_from(ts) -> TexSet:
-    """Oracle texture set registered in the same (texture-major, level-minor) order."""
+def texset_from(ts, compact: bool = False) -> TexSet:
+    """Oracle texture set registered in the same (texture-major, level-minor) order, in the
+    standard or the compact form."""
     o = TexSet()
     for t, l, e in ts.uploads():
-        o.add(t, l, e)
+        (o.add_compact if compact else o.add)(t, l, e)
     return o
 
 

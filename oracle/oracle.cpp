@@ -170,14 +170,21 @@ int decode_symbol(BitReader& br, const HuffTable& t, bool& err) {
 
 // Decodes one data unit into quantised coefficients (natural order). Returns false when
 // the stream is not a valid coding of a data unit.
-bool decode_du(BitReader& br, const HuffTable& dc, const HuffTable& ac, int16_t& pred, int32_t coef[64]) {
+// dc_coded = false: the data unit carries no DC difference (the compact form of Sec. 5.3
+// stores that DC apart) and its DC is `pred` as given. *dc_bits: the bits the DC took.
+bool decode_du(BitReader& br, const HuffTable& dc, const HuffTable& ac, int16_t& pred, int32_t coef[64],
+               bool dc_coded = true, int* dc_bits = nullptr) {
   const int* zz = zigzag();
   bool err = false;
   for (int k = 0; k < 64; ++k) coef[k] = 0;
-  int t = decode_symbol(br, dc, err);
-  if (err || t > 11) return false;
-  int diff = extend(br.receive(t), t);
-  pred = (int16_t)(uint16_t)((int)pred + diff);  // DC wraps modulo 2^16
+  const uint64_t dc_start = br.pos;
+  if (dc_coded) {
+    int t = decode_symbol(br, dc, err);
+    if (err || t > 11) return false;
+    int diff = extend(br.receive(t), t);
+    pred = (int16_t)(uint16_t)((int)pred + diff);  // DC wraps modulo 2^16
+  }
+  if (dc_bits) *dc_bits = (int)(br.pos - dc_start);
   coef[0] = pred;
   int k = 1;
   while (k < 64) {
@@ -440,6 +447,11 @@ struct Level {
   std::vector<uint8_t> scan;
   uint64_t nbits = 0;
   std::vector<BlockIndex> index;
+  // the compact form (Sec. 5.1 indexing table, Sec. 5.3 DC records), when `compact`
+  bool compact = false;
+  std::vector<uint32_t> c_abs;  // byte offset of MCU 9j
+  std::vector<uint16_t> c_rel;  // byte offset of MCU 9j+i (i = 1..8) relative to c_abs[j]
+  std::vector<uint32_t> c_dc;   // 12-bit absolute DCs (Y0, Cb, Cr), 36 bits per MCU
   uint16_t qt[2][64];
   HuffTable tab[4];
   std::unordered_map<int, std::vector<uint8_t>> tiles;  // decoded MCUs, by MCU id
@@ -457,9 +469,48 @@ struct TexSet {
   }
 };
 
+// First bit of MCU m in the compact stream: its byte offset from the two-level table
+// (absolute every ninth MCU, the next eight relative to it), times 8.
+uint64_t compact_start(const Level& L, int m) {
+  if (m >= L.mcus_x * L.mcus_y) return 8ull * L.scan.size();
+  const int j = m / 9, i = m % 9;
+  return 8ull * ((uint64_t)L.c_abs[j] + (i ? L.c_rel[8 * j + i - 1] : 0u));
+}
+
+// Absolute DC c (0 = first Y, 1 = Cb, 2 = Cr) of MCU m: 12-bit two's complement at bit
+// 36 m + 12 c of the record array (bit b = bit b % 32 of word b / 32).
+int compact_dc(const Level& L, int m, int c) {
+  const uint64_t at = 36ull * m + 12ull * c;
+  int v = 0;
+  for (int i = 0; i < 12; ++i) v |= (int)((L.c_dc[(at + i) / 32] >> ((at + i) % 32)) & 1u) << i;
+  return v >= 2048 ? v - 4096 : v;
+}
+
+// Random-access decode of one MCU of the compact form: start at the MCU's byte; the first
+// luma data unit and the chroma data units take their DCs from the records, the other luma
+// units decode their DC differences against the previous luma unit of the MCU. The MCU's
+// bits must end inside its own bytes.
+int decode_mcu_compact(const Level& L, int mcu, uint8_t* tile) {
+  const int ndu = L.sampling == 420 ? 6 : 3;
+  BitReader br{L.scan.data(), L.scan.size(), compact_start(L, mcu)};
+  int16_t pred[3];
+  for (int c = 0; c < 3; ++c) pred[c] = (int16_t)compact_dc(L, mcu, c);
+  int32_t q[6][64];
+  for (int d = 0; d < ndu; ++d) {
+    int comp = d < ndu - 2 ? 0 : (d == ndu - 2 ? 1 : 2);
+    int tb = comp == 0 ? 0 : 1;
+    const bool stored = d == 0 || comp != 0;
+    if (!decode_du(br, L.tab[tb * 2], L.tab[tb * 2 + 1], pred[comp], q[d], !stored)) return -1;
+  }
+  if (br.pos > compact_start(L, mcu + 1)) return -1;
+  mcu_to_tile(q, L.sampling, L.qt, tile);
+  return 0;
+}
+
 // Random-access decode of one MCU (Sec. 4.3 with the index of Sec. 5.1): start at the
 // MCU's bit offset with its DC predictors and decode its data units.
 int decode_mcu(const Level& L, int mcu, uint8_t* tile) {
+  if (L.compact) return decode_mcu_compact(L, mcu, tile);
   const int ndu = L.sampling == 420 ? 6 : 3;
   const BlockIndex& bi = L.index[mcu];
   BitReader br{L.scan.data(), L.scan.size(), bi.bit_offset};
@@ -614,13 +665,8 @@ void jto_decoded_free(void* h) { delete static_cast<Decoded*>(h); }
 void* jto_texset_new() { return new TexSet(); }
 void jto_texset_free(void* s) { delete static_cast<TexSet*>(s); }
 
-// Registers one (texture, level) with the data the CUDA path receives. Levels receive
-// consecutive global MCU ids in registration order. Returns the level's gid base, or -1.
-int64_t jto_texset_add(void* s, int tex, int level, int w, int h, int sampling, const uint8_t* scan,
-                       uint64_t nbytes, uint64_t nbits, const void* index, uint64_t nindex, const uint16_t* qt,
-                       const uint8_t* hbits, const uint8_t* hvals) {
-  TexSet* S = static_cast<TexSet*>(s);
-  if (S->levels.count({tex, level})) return -1;
+static Level* new_level(int tex, int level, int w, int h, int sampling, uint64_t nindex, const uint16_t* qt,
+                        const uint8_t* hbits, const uint8_t* hvals) {
   Level* L = new Level();
   L->tex = tex;
   L->level = level;
@@ -629,27 +675,87 @@ int64_t jto_texset_add(void* s, int tex, int level, int w, int h, int sampling, 
   L->sampling = sampling;
   L->mcus_x = (w + L->mw() - 1) / L->mw();
   L->mcus_y = (h + L->mw() - 1) / L->mw();
-  if ((uint64_t)L->mcus_x * L->mcus_y != nindex) {
-    delete L;
-    return -1;
+  std::memcpy(L->qt, qt, sizeof L->qt);
+  bool ok = (uint64_t)L->mcus_x * L->mcus_y == nindex;
+  for (int t = 0; t < 4 && ok; ++t) {
+    L->tab[t] = make_table(hbits + 16 * t, hvals + 256 * t);
+    ok = L->tab[t].ok;
   }
+  if (!ok) {
+    delete L;
+    return nullptr;
+  }
+  return L;
+}
+
+static int64_t register_level(TexSet* S, Level* L) {
+  L->gid_base = S->next_gid;
+  S->next_gid += (uint32_t)(L->mcus_x * L->mcus_y);
+  S->levels[{L->tex, L->level}] = L;
+  S->order.push_back(L);
+  return L->gid_base;
+}
+
+// Registers one (texture, level) with the data the CUDA path receives. Levels receive
+// consecutive global MCU ids in registration order. Returns the level's gid base, or -1.
+int64_t jto_texset_add(void* s, int tex, int level, int w, int h, int sampling, const uint8_t* scan,
+                       uint64_t nbytes, uint64_t nbits, const void* index, uint64_t nindex, const uint16_t* qt,
+                       const uint8_t* hbits, const uint8_t* hvals) {
+  TexSet* S = static_cast<TexSet*>(s);
+  if (S->levels.count({tex, level})) return -1;
+  Level* L = new_level(tex, level, w, h, sampling, nindex, qt, hbits, hvals);
+  if (!L) return -1;
   L->scan.assign(scan, scan + nbytes);
   L->nbits = nbits;
   const BlockIndex* bi = static_cast<const BlockIndex*>(index);
   L->index.assign(bi, bi + nindex);
-  std::memcpy(L->qt, qt, sizeof L->qt);
-  for (int t = 0; t < 4; ++t) {
-    L->tab[t] = make_table(hbits + 16 * t, hvals + 256 * t);
-    if (!L->tab[t].ok) {
-      delete L;
-      return -1;
+  return register_level(S, L);
+}
+
+// The same for a level in the compact form: nabs = ceil(n / 9) absolute byte offsets,
+// 8 nabs relative ones, ceil(36 n / 32) words of DC records. Returns the gid base, or -1.
+int64_t jto_texset_add_compact(void* s, int tex, int level, int w, int h, int sampling, const uint8_t* scan,
+                               uint64_t nbytes, const uint32_t* abs_off, uint64_t nabs, const uint16_t* rel_off,
+                               uint64_t nrel, const uint32_t* dc, uint64_t ndc, uint64_t nindex,
+                               const uint16_t* qt, const uint8_t* hbits, const uint8_t* hvals) {
+  TexSet* S = static_cast<TexSet*>(s);
+  if (S->levels.count({tex, level})) return -1;
+  if (nabs != (nindex + 8) / 9 || nrel != 8 * nabs || ndc != (36 * nindex + 31) / 32) return -1;
+  Level* L = new_level(tex, level, w, h, sampling, nindex, qt, hbits, hvals);
+  if (!L) return -1;
+  L->compact = true;
+  L->scan.assign(scan, scan + nbytes);
+  L->nbits = 8 * nbytes;
+  L->c_abs.assign(abs_off, abs_off + nabs);
+  L->c_rel.assign(rel_off, rel_off + nrel);
+  L->c_dc.assign(dc, dc + ndc);
+  return register_level(S, L);
+}
+
+// For a level in the standard form, per MCU: its coded bits and the bits its first luma DC
+// and its chroma DCs take (what the compact form moves out of the stream, Sec. 5.3), from a
+// sequential decode. Returns 0, or -1 on a corrupt stream or a compact level.
+int jto_mcu_bits(void* s, int tex, int level, int64_t* bits, int64_t* dc_bits) {
+  TexSet* S = static_cast<TexSet*>(s);
+  Level* L = find_level(*S, tex, level);
+  if (!L || L->compact) return -1;
+  const int ndu = L->sampling == 420 ? 6 : 3;
+  BitReader br{L->scan.data(), L->scan.size(), 0};
+  int16_t pred[3] = {0, 0, 0};
+  int32_t q[64];
+  for (int m = 0; m < L->mcus_x * L->mcus_y; ++m) {
+    const uint64_t start = br.pos;
+    dc_bits[m] = 0;
+    for (int d = 0; d < ndu; ++d) {
+      int comp = d < ndu - 2 ? 0 : (d == ndu - 2 ? 1 : 2);
+      int tb = comp == 0 ? 0 : 1;
+      int db = 0;
+      if (!decode_du(br, L->tab[tb * 2], L->tab[tb * 2 + 1], pred[comp], q, true, &db)) return -1;
+      if (d == 0 || comp != 0) dc_bits[m] += db;
     }
+    bits[m] = (int64_t)(br.pos - start);
   }
-  L->gid_base = S->next_gid;
-  S->next_gid += (uint32_t)nindex;
-  S->levels[{tex, level}] = L;
-  S->order.push_back(L);
-  return L->gid_base;
+  return br.pos == L->nbits ? 0 : -1;
 }
 
 // Random-access decode of one MCU into an RGBA8 tile; returns 0 or -1 (corrupt).

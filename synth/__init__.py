@@ -62,6 +62,8 @@ def lib():
         L.syn_jpeg_info.argtypes = [P, P]
         L.syn_jpeg_copy.argtypes = [P, P, P, P, P, P, P, P]
         L.syn_jpeg_free.argtypes = [P]
+        L.syn_jpeg_compact_info.argtypes = [P, P]
+        L.syn_jpeg_compact_copy.argtypes = [P, P, P, P, P]
         L.syn_gbuffer_affine.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                          ctypes.c_int, P, P, P]
         L.syn_gbuffer_scene.argtypes = [
@@ -138,6 +140,22 @@ def zigzag() -> np.ndarray:
 
 
 @dataclass
+class Compact:
+    """The paper's compact random-access form of one level (Sec. 5.1 indexing table, the DC
+    records of Sec. 5.3): every MCU starts on a byte of `scan`; the first luma DC and both
+    chroma DCs are not in the stream but in `dc` as 12-bit two's-complement values (bits
+    36 m + 12 c of the little-endian bit array, c = Y, Cb, Cr); MCU 9 j starts at byte
+    abs[j] and MCU 9 j + i (i = 1..8) at abs[j] + rel[8 j + i - 1]."""
+
+    scan: np.ndarray  # uint8, byte-aligned MCUs padded with 1-bits
+    abs: np.ndarray  # uint32 [ceil(n / 9)]
+    rel: np.ndarray  # uint16 [8 ceil(n / 9)]
+    dc: np.ndarray  # uint32 [ceil(36 n / 32)]
+    dc_bits_removed: int  # bits the absolute DCs took in the standard stream
+    pad_bits: int  # alignment bits
+
+
+@dataclass
 class Encoded:
     """One encoded texture level (what `jt_upload_texture` takes, plus the JFIF file)."""
 
@@ -155,6 +173,7 @@ class Encoded:
     huff_bits: np.ndarray  # uint8 [4, 16]
     huff_vals: np.ndarray  # uint8 [4, 256]
     qcoef: np.ndarray | None = None  # int16 [nmcu, ndu, 64] natural order
+    compact: Compact | None = None  # the paper's compact form (when asked for)
 
     @property
     def nmcu(self) -> int:
@@ -165,7 +184,20 @@ class Encoded:
         return 6 if self.sampling == 420 else 3
 
 
-def _collect(h, quality, keep) -> Encoded:
+def _collect_compact(h) -> Compact:
+    info = np.zeros(7, np.int64)
+    lib().syn_jpeg_compact_info(h, _p(info))
+    if info[0] != 0:
+        raise ValueError("coefficients do not fit the compact form (a DC outside 12 bits)")
+    scan = np.empty(int(info[1]), np.uint8)
+    a = np.empty(int(info[2]), np.uint32)
+    r = np.empty(int(info[3]), np.uint16)
+    dc = np.empty(int(info[4]), np.uint32)
+    lib().syn_jpeg_compact_copy(h, _p(scan), _p(a), _p(r), _p(dc))
+    return Compact(scan, a, r, dc, int(info[5]), int(info[6]))
+
+
+def _collect(h, quality, keep, compact=False) -> Encoded:
     L = lib()
     info = np.zeros(10, np.int64)
     L.syn_jpeg_info(h, _p(info))
@@ -183,24 +215,30 @@ def _collect(h, quality, keep) -> Encoded:
     qc = np.empty((mx * my, ndu, 64), np.int16) if keep else None
     L.syn_jpeg_copy(h, _p(jfif), _p(scan), _p(index), _p(qt), _p(bits), _p(vals),
                     _p(qc) if keep else None)
-    L.syn_jpeg_free(h)
-    return Encoded(w, hh, samp, mx, my, quality, jfif, scan, nbits, index, qt, bits, vals, qc)
+    try:
+        cp = _collect_compact(h) if compact else None
+    finally:
+        L.syn_jpeg_free(h)
+    return Encoded(w, hh, samp, mx, my, quality, jfif, scan, nbits, index, qt, bits, vals, qc, cp)
 
 
-def encode(rgb: np.ndarray, quality: int, sampling: int = 420, keep_coefs: bool = False) -> Encoded:
+def encode(rgb: np.ndarray, quality: int, sampling: int = 420, keep_coefs: bool = False,
+           compact: bool = False) -> Encoded:
+    """Baseline JPEG of an RGB8 image; `compact` also returns the paper's compact form."""
     rgb = np.ascontiguousarray(rgb, np.uint8)
     h, w, _ = rgb.shape
     hnd = lib().syn_jpeg_encode_rgb(_p(rgb), w, h, quality, sampling, int(keep_coefs))
     if not hnd:
         raise ValueError("bad encoder arguments")
-    return _collect(hnd, quality, keep_coefs)
+    return _collect(hnd, quality, keep_coefs, compact)
 
 
-def encode_coefs(qcoef: np.ndarray, mcus_x: int, mcus_y: int, sampling: int, quality: int = 75) -> Encoded:
+def encode_coefs(qcoef: np.ndarray, mcus_x: int, mcus_y: int, sampling: int, quality: int = 75,
+                 compact: bool = False) -> Encoded:
     """Entropy-codes given quantised blocks [nmcu, ndu, 64] (natural order)."""
     qcoef = np.ascontiguousarray(qcoef, np.int16)
     hnd = lib().syn_jpeg_encode_coefs(_p(qcoef), mcus_x, mcus_y, sampling, quality)
-    e = _collect(hnd, quality, False)
+    e = _collect(hnd, quality, False, compact)
     e.qcoef = qcoef.copy()
     return e
 
@@ -290,7 +328,7 @@ def _threads() -> int:
 
 
 def make_texture_set(seed: int, sizes, qualities, samplings, full_chain: bool = True,
-                     keep_coefs: bool = False, threads: int | None = None) -> TextureSet:
+                     keep_coefs: bool = False, threads: int | None = None, compact: bool = False) -> TextureSet:
     """Generates and encodes textures t (seeded by mix_seed(seed, 100, t)) with mip chains.
 
     Each mip level is produced from the previous RGB level by the 2x2 box filter and
@@ -302,7 +340,7 @@ def make_texture_set(seed: int, sizes, qualities, samplings, full_chain: bool = 
         w, h = sizes[t]
         rgb = texture(mix_seed(seed, 100, t), w, h)
         chain = mip_chain(rgb) if full_chain else [rgb]
-        return [encode(c, int(qualities[t]), int(samplings[t]), keep_coefs) for c in chain]
+        return [encode(c, int(qualities[t]), int(samplings[t]), keep_coefs, compact) for c in chain]
 
     with ThreadPoolExecutor(threads or _threads()) as ex:
         levels = list(ex.map(one, range(n)))
@@ -317,7 +355,7 @@ def config1():
     return ts, gb
 
 
-def config2_textures(ntex: int = 64, threads: int | None = None) -> TextureSet:
+def config2_textures(ntex: int = 64, threads: int | None = None, compact: bool = False) -> TextureSet:
     """64 textures, sizes uniform in {1024,2048,4096}^2, Q uniform in [50,95], 4:2:0,
     full mip chains each level encoded separately."""
     seed = SEED_BASE + 2
@@ -326,7 +364,7 @@ def config2_textures(ntex: int = 64, threads: int | None = None) -> TextureSet:
         s = mix_seed(seed, 200, t)
         sizes.append((1024 << (s % 3),) * 2)
         quals.append(50 + int((s >> 8) % 46))
-    return make_texture_set(seed, sizes, quals, [420] * ntex, full_chain=True, threads=threads)
+    return make_texture_set(seed, sizes, quals, [420] * ntex, full_chain=True, threads=threads, compact=compact)
 
 
 def config2_pose() -> Pose:

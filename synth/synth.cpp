@@ -5,6 +5,11 @@
 //   * a baseline sequential JPEG encoder (the offline step the paper performs with
 //     libjpeg-turbo / jpegli, Sec. 6.1) that also emits the unstuffed entropy stream and
 //     the per-MCU random-access index (bit offset + DC predictors, Sec. 5.1 / Sec. 5.3),
+//   * the same coefficients in the paper's compact form (Sec. 5.1 indexing table and the
+//     DC accounting of Sec. 5.3): every MCU starts on a byte; the first luma DC and both
+//     chroma DCs leave the entropy stream and are stored as 12-bit absolute values; the
+//     byte offset of every ninth MCU is an absolute uint32, the next eight are uint16
+//     offsets relative to it,
 //   * deferred G-buffers (uv, texture id, mip level; Sec. 4 "Geometry Pass").
 //
 // It holds none of the decode-side arithmetic: Huffman decoding, dequantisation, the
@@ -312,6 +317,20 @@ int category(int v) {
 
 uint32_t magnitude_bits(int v, int s) { return (uint32_t)(v < 0 ? v - 1 : v) & ((1u << s) - 1u); }
 
+// The compact form (see the header): a byte-aligned stream without the absolute DCs, the
+// two-level offset table and the 36-bit DC records, bit i of the record array being bit
+// (i mod 32) of word i / 32, MCU m's values (first Y, Cb, Cr; 12-bit two's complement) at
+// bits 36 m, 36 m + 12, 36 m + 24.
+struct Compact {
+  std::vector<uint8_t> scan;
+  std::vector<uint32_t> abs;  // [ceil(n / 9)]
+  std::vector<uint16_t> rel;  // [8 ceil(n / 9)]; entries past the last MCU are 0
+  std::vector<uint32_t> dc;   // [ceil(36 n / 32)]
+  uint64_t dc_bits_removed = 0;  // bits the absolute DCs took in the standard stream
+  uint64_t pad_bits = 0;         // 1-bits that align each MCU to a byte
+  int status = 0;                // nonzero: a DC outside 12 bits, or a relative offset > 65535
+};
+
 struct Encoded {
   int w = 0, h = 0, sampling = 420, mcus_x = 0, mcus_y = 0, quality = 0;
   std::vector<uint8_t> jfif, scan;
@@ -320,17 +339,30 @@ struct Encoded {
   uint16_t qt[2][64];
   HuffSpec huff[4];
   std::vector<int16_t> qcoef;  // [mcu][du][64] natural order, quantised (optional)
+  Compact compact;
   int status = 0;
 };
 
-// Writes one data unit of quantised coefficients (natural order).
-int encode_du(BitWriter& bw, const int16_t* q, int& pred, const HuffEnc& dc, const HuffEnc& ac) {
+// Writes one data unit of quantised coefficients (natural order) to the standard stream bw
+// and to the compact stream cw, which leaves out the DC difference when dc_absolute.
+int encode_du(BitWriter& bw, BitWriter& cw, bool dc_absolute, uint64_t& dc_removed, const int16_t* q, int& pred,
+              const HuffEnc& dc, const HuffEnc& ac) {
+  auto put = [&](uint32_t v, int n) {
+    bw.put(v, n);
+    cw.put(v, n);
+  };
   int diff = q[0] - pred;
   pred = q[0];
   int s = category(diff);
   if (s > 11 || dc.len[s] == 0) return -1;
   bw.put(dc.code[s], dc.len[s]);
   bw.put(magnitude_bits(diff, s), s);
+  if (dc_absolute) {
+    dc_removed += (uint64_t)(dc.len[s] + s);
+  } else {
+    cw.put(dc.code[s], dc.len[s]);
+    cw.put(magnitude_bits(diff, s), s);
+  }
   int run = 0;
   for (int k = 1; k < 64; ++k) {
     int v = q[kZZ.zz[k]];
@@ -339,19 +371,24 @@ int encode_du(BitWriter& bw, const int16_t* q, int& pred, const HuffEnc& dc, con
       continue;
     }
     while (run > 15) {
-      bw.put(ac.code[0xF0], ac.len[0xF0]);
+      put(ac.code[0xF0], ac.len[0xF0]);
       run -= 16;
     }
     int sz = category(v);
     if (sz > 10) return -1;
     int sym = (run << 4) | sz;
     if (ac.len[sym] == 0) return -1;
-    bw.put(ac.code[sym], ac.len[sym]);
-    bw.put(magnitude_bits(v, sz), sz);
+    put(ac.code[sym], ac.len[sym]);
+    put(magnitude_bits(v, sz), sz);
     run = 0;
   }
-  if (run > 0) bw.put(ac.code[0x00], ac.len[0x00]);
+  if (run > 0) put(ac.code[0x00], ac.len[0x00]);
   return 0;
+}
+
+void put_bits(std::vector<uint32_t>& a, uint64_t at, uint32_t v, int n) {
+  for (int i = 0; i < n; ++i)
+    if ((v >> i) & 1u) a[(at + i) >> 5] |= 1u << ((at + i) & 31);
 }
 
 void put16(std::vector<uint8_t>& o, int v) {
@@ -365,8 +402,14 @@ void entropy_and_container(Encoded& e, const int16_t* qcoef) {
   const int nmcu = e.mcus_x * e.mcus_y;
   HuffEnc enc[4];
   for (int t = 0; t < 4; ++t) enc[t] = encoder_codes(e.huff[t]);
-  std::vector<uint8_t> stuffed;
+  std::vector<uint8_t> stuffed, cstuffed;
   BitWriter bw{&stuffed, &e.scan};
+  Compact& C = e.compact;
+  BitWriter cw{&cstuffed, &C.scan};
+  const int ngroups = (nmcu + 8) / 9;
+  C.abs.assign(ngroups, 0);
+  C.rel.assign((size_t)ngroups * 8, 0);
+  C.dc.assign(((uint64_t)nmcu * 36 + 31) / 32, 0);
   int pred[3] = {0, 0, 0};
   e.index.resize(nmcu);
   for (int m = 0; m < nmcu; ++m) {
@@ -374,14 +417,29 @@ void entropy_and_container(Encoded& e, const int16_t* qcoef) {
     bi.bit_offset = (uint32_t)bw.nbits;
     for (int c = 0; c < 3; ++c) bi.dc_pred[c] = (int16_t)pred[c];
     e.index[m] = bi;
+    const uint64_t byte = C.scan.size();  // cw is byte aligned here
+    if (m % 9 == 0)
+      C.abs[m / 9] = (uint32_t)byte;
+    else if (byte - C.abs[m / 9] > 65535)
+      C.status = -1;
+    else
+      C.rel[(m / 9) * 8 + m % 9 - 1] = (uint16_t)(byte - C.abs[m / 9]);
     for (int d = 0; d < ndu; ++d) {
       int comp = d < ndu - 2 ? 0 : (d == ndu - 2 ? 1 : 2);
       int tab = comp == 0 ? 0 : 1;
-      if (encode_du(bw, qcoef + ((size_t)m * ndu + d) * 64, pred[comp], enc[tab * 2], enc[tab * 2 + 1]) != 0) {
+      const int16_t* q = qcoef + ((size_t)m * ndu + d) * 64;
+      const bool absolute = d == 0 || comp != 0;  // the first luma DC and the chroma DCs
+      if (absolute) {
+        if (q[0] < -2048 || q[0] > 2047) C.status = -1;
+        put_bits(C.dc, (uint64_t)m * 36 + 12 * comp, (uint32_t)q[0] & 0xFFFu, 12);
+      }
+      if (encode_du(bw, cw, absolute, C.dc_bits_removed, q, pred[comp], enc[tab * 2], enc[tab * 2 + 1]) != 0) {
         e.status = -2;
         return;
       }
     }
+    C.pad_bits += cw.nacc ? (uint64_t)(8 - cw.nacc) : 0u;
+    cw.flush_ones();
   }
   e.scan_bits = bw.nbits;
   bw.flush_ones();
@@ -743,6 +801,26 @@ void syn_jpeg_copy(void* hnd, uint8_t* jfif, uint8_t* scan, void* index, uint16_
       std::memcpy(vals + 256 * t, e->huff[t].vals, e->huff[t].nvals);
     }
   if (qcoef && !e->qcoef.empty()) std::memcpy(qcoef, e->qcoef.data(), e->qcoef.size() * sizeof(int16_t));
+}
+
+// Compact form sizes: [status, scan_bytes, n_abs, n_rel, n_dc_words, dc_bits_removed, pad_bits]
+void syn_jpeg_compact_info(void* hnd, int64_t* info) {
+  const Compact& C = static_cast<Encoded*>(hnd)->compact;
+  info[0] = C.status;
+  info[1] = (int64_t)C.scan.size();
+  info[2] = (int64_t)C.abs.size();
+  info[3] = (int64_t)C.rel.size();
+  info[4] = (int64_t)C.dc.size();
+  info[5] = (int64_t)C.dc_bits_removed;
+  info[6] = (int64_t)C.pad_bits;
+}
+
+void syn_jpeg_compact_copy(void* hnd, uint8_t* scan, uint32_t* abs, uint16_t* rel, uint32_t* dc) {
+  const Compact& C = static_cast<Encoded*>(hnd)->compact;
+  std::memcpy(scan, C.scan.data(), C.scan.size());
+  std::memcpy(abs, C.abs.data(), C.abs.size() * 4);
+  std::memcpy(rel, C.rel.data(), C.rel.size() * 2);
+  std::memcpy(dc, C.dc.data(), C.dc.size() * 4);
 }
 
 void syn_jpeg_free(void* hnd) { delete static_cast<Encoded*>(hnd); }
