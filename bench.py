@@ -57,9 +57,9 @@ def peaks():
 # Workload
 # ---------------------------------------------------------------------------------------
 
-def workload():
+def workload(compact: bool = False):
     import synth
-    ts = synth.config2_textures()
+    ts = synth.config2_textures(compact=compact)
     gb = synth.config2_gbuffer(ts)
     return ts, gb
 
@@ -280,6 +280,37 @@ def run_clamped(ctx, jt, dgb, out, flush, stream, steps):
             "needed_blocks_per_frame": needed, "blocks_per_s": needed / (ms * 1e-3)}
 
 
+def run_compact(jt, ts, dgb, ref_out, dev, flush, stream, steps, tuning):
+    """The headline frame over the same textures uploaded in the paper's compact form
+    (byte-aligned MCUs, two-level offset table, 12-bit DC records; Sec. 5.1, 5.3): frame
+    time, identical pixels, and the side-table overhead of both forms per texel."""
+    import torch
+    ctx = jt.Context(dev.index, max_cache_blocks=1 << 18)
+    ctx.upload_set(ts, compact=True)
+    ctx.set_tuning(**tuning)
+    out = torch.empty_like(ref_out)
+    g = ctx.frame_graph([(dgb, out)], jt.FILTER_BILINEAR)
+    ms = timed(lambda: ctx.graph_launch(g), steps, 3, stream, flush)
+    needed = int(ctx.stats()["needed_blocks"])
+    same = bool(torch.equal(out, ref_out))
+    ctx.graph_destroy(g)
+    ctx.close()
+    levels = [e for _, _, e in ts.uploads()]
+    n = sum(e.nmcu for e in levels)
+    texels = sum(e.nmcu * (256 if e.sampling == 420 else 64) for e in levels)
+    table_bits = sum(32 * e.compact.abs.size + 16 * e.compact.rel.size + 36 * e.nmcu for e in levels)
+    removed = sum(e.compact.dc_bits_removed for e in levels)
+    pad = sum(e.compact.pad_bits for e in levels)
+    return {"workload": "as the headline frame, textures in the compact form", "ms_per_frame": ms,
+            "needed_blocks_per_frame": needed, "same_output": same,
+            "index_bpp_standard": 80.0 * n / texels,
+            "side_table_bpp_compact": table_bits / texels,
+            "overhead_bpp_compact": (table_bits - removed) / texels,
+            "overhead_bpp_compact_with_alignment": (table_bits - removed + pad) / texels,
+            "stream_bytes": {"standard": int(sum(e.scan.size for e in levels)),
+                             "compact": int(sum(e.compact.scan.size for e in levels))}}
+
+
 def mcu_grid(ts, width: int = 2048):
     """G-buffer with one pixel on every MCU of every uploaded level (nearest marks each MCU once)."""
     import synth
@@ -330,47 +361,66 @@ def run_full_decode(jt, dev, flush, stream, steps, peak, tuning, ntex=16):
             "compressed_mb": cbytes / 1e6, "tiles_mb": tile_bytes / 1e6}
 
 
-def run_motion(jt, ts, dev, flush, stream, nframes=24, W=1920, H=1080):
-    """A camera turning 6 degrees per frame over the 64 textures at 1920x1080 (the paper's
-    motion test, shortened): per-frame time with the cross-frame block cache against the
-    per-frame mode, both as graph replays fed each frame's G-buffer."""
+def run_motion(jt, ts, dev, flush, stream, reps=100, stereo=False):
+    """The paper's caching measurement under motion: 60 view directions 6 degrees apart (a
+    full turn), the turn repeated `reps` times after one warm-up turn; per direction the
+    median frame time over the repetitions, and the maximum of those medians (the worst
+    viewpoint). Per-frame mode against the cross-frame block cache, bilinear, each
+    direction a graph replay over its own G-buffer(s). With `stereo`, each frame is a VR
+    pair (two eyes of 2064x2208 in one batched frame), and the MCUs both eyes share are
+    counted per direction."""
     import torch
     import synth
-    pose0 = synth.config2_pose()
-    frames = [synth.gbuffer_scene(synth.SEED_BASE + 2, W, H, ts.sizes, ts.nlevels,
-                                  synth.Pose(pose0.cam, pose0.yaw + 6.0 * k, pose0.pitch, pose0.vfov, pose0.quad_seed,
-                                             0.0), nquads=200) for k in range(nframes)]
-    dframes = [jt.DeviceGBuffer.from_host(f, dev) for f in frames]
+    W, H = (2064, 2208) if stereo else (1920, 1080)
+    dirs = synth.motion_views(ts, W, H, stereo=stereo)
+    dviews = [[jt.DeviceGBuffer.from_host(g, dev) for g in d] for d in dirs]
+    outs = [torch.empty((H, W, 4), dtype=torch.uint8, device=dev) for _ in dirs[0]]
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
     res = {}
     for mode in ("per_frame", "block_cache"):
         ctx = jt.Context(dev.index, max_cache_blocks=1 << 18)
         ctx.upload_set(ts)
         ctx.set_block_cache(mode == "block_cache")
-        dv = jt.DeviceGBuffer.from_host(frames[0], dev)
-        out = torch.empty((H, W, 4), dtype=torch.uint8, device=dev)
-        g = ctx.frame_graph([(dv, out)], jt.FILTER_BILINEAR)
-        a0 = torch.cuda.Event(enable_timing=True)
-        a1 = torch.cuda.Event(enable_timing=True)
-        ms, decoded = [], []
-        for rep in range(2):  # the second pass over the sequence is timed (warm caches)
-            for k, f in enumerate(dframes):
-                dv.uv.copy_(f.uv)
-                dv.tex_id.copy_(f.tex_id)
-                dv.mip.copy_(f.mip)
+        ctx.profile(True)
+        graphs = [ctx.frame_graph(list(zip(dv, outs)), jt.FILTER_BILINEAR) for dv in dviews]
+        ms = np.zeros((reps, len(dirs)))
+        dec = np.zeros((reps, len(dirs)))
+        passes = {"mark": [], "compact": [], "decode": [], "colorize": []}
+        for r in range(reps + 1):
+            for k, g in enumerate(graphs):
                 flush.fill_(k & 255)
                 a0.record(stream)
                 ctx.graph_launch(g)
                 a1.record(stream)
                 a1.synchronize()
-                if rep == 1:
-                    ms.append(a0.elapsed_time(a1))
-                    decoded.append(int(ctx.stats()["needed_blocks"]))
-        ctx.graph_destroy(g)
+                if r:
+                    ms[r - 1, k] = a0.elapsed_time(a1)
+                    dec[r - 1, k] = ctx.stats()["needed_blocks"]
+                    for name, v in ctx.profile_read().items():
+                        passes[name].append(v)
+        for g in graphs:
+            ctx.graph_destroy(g)
+        med = np.median(ms, axis=0)
+        res[mode] = {"max_of_medians_ms": float(med.max()), "worst_direction_deg": 6 * int(med.argmax()),
+                     "median_ms": float(np.median(ms)), "mean_decoded_blocks": float(dec.mean()),
+                     "max_decoded_blocks": int(dec.max()),
+                     "passes_median_ms": {k: float(np.median(v)) for k, v in passes.items()}}
+        ctx.profile(False)
+        if stereo and mode == "per_frame":  # MCUs shared by the two eyes: |L & R| / |L | R|
+            share = []
+            for k, dv in enumerate(dviews):
+                n = []
+                for eye in range(2):
+                    ctx.frame([(dv[eye], outs[eye])], jt.FILTER_BILINEAR)
+                    n.append(int(ctx.stats()["needed_blocks"]))
+                union = dec[0, k]
+                share.append((n[0] + n[1] - union) / union)
+            res["shared_mcus"] = {"min": float(min(share)), "mean": float(np.mean(share))}
         ctx.close()
-        res[mode] = {"median_ms": float(np.median(ms)), "max_ms": float(max(ms)),
-                     "mean_decoded_blocks": float(np.mean(decoded))}
-    res["workload"] = f"{nframes} frames {W}x{H}, camera turning 6 deg/frame, 64 textures, bilinear"
-    res["speedup_median"] = res["per_frame"]["median_ms"] / res["block_cache"]["median_ms"]
+    res["workload"] = (f"60 directions x {reps} turns, camera turning 6 deg/frame, "
+                       + ("VR pair 2x(2064x2208), 90 deg fov" if stereo else "1920x1080") + ", 64 textures, bilinear")
+    res["speedup_max_of_medians"] = res["per_frame"]["max_of_medians_ms"] / res["block_cache"]["max_of_medians_ms"]
     return res
 
 
@@ -415,7 +465,7 @@ def run_gpu(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    ts, gb = workload()
+    ts, gb = workload(compact=not args.no_extra)
     ctx = jt.Context(local_rank, max_cache_blocks=1 << 18)
     ctx.upload_set(ts)
     dgb = jt.DeviceGBuffer.from_host(gb, dev)
@@ -553,10 +603,12 @@ def run_gpu(args, rank, world, local_rank):
             line["tuning"] = tuned
         if not args.no_extra:
             line["clamped_filter"] = run_clamped(ctx, jt, dgb, out, flush, stream, 20)
+            line["compact_form"] = run_compact(jt, ts, dgb, ref_out, dev, flush, stream, 20, ctx.tuning())
             line["batched_views"] = run_views(ctx, ts, jt, dev, flush, stream, 20)
             line["adjoint"] = run_adjoint(jt, dev, flush, stream, 20, peak)
             line["full_decode"] = run_full_decode(jt, dev, flush, stream, 5, peak, ctx.tuning())
             line["motion"] = run_motion(jt, ts, dev, flush, stream)
+            line["motion_vr"] = run_motion(jt, ts, dev, flush, stream, stereo=True)
         print(json.dumps(line), flush=True)
     ctx.close()
     return 0

@@ -146,12 +146,35 @@ const char* jt_status_string(jt_status s);
  * 8x8 texels). All pointers are host memory and are copied; they may be freed on return.
  * MCUs of the level get consecutive global ids (gids) in upload order: the first level
  * uploaded starts at gid 0 and each level starts where the previous one ended.
- * 0 <= tex_id < 0xFFFF, 0 <= level < JT_MAX_LEVELS, 1 <= width, height <= 65535; a
- * (tex_id, level) pair may be uploaded once. Not allowed between jt_mark and jt_decode. */
+ * 0 <= tex_id < 0xFFFF, 0 <= level < JT_MAX_LEVELS, 1 <= width, height <= 65535,
+ * nbytes < 2^29 (bit offsets are 32-bit); a (tex_id, level) pair may be uploaded once.
+ * Not allowed between jt_mark and jt_decode. */
 jt_status jt_upload_texture(jt_ctx* ctx, int tex_id, int level, int width, int height, int sampling,
                             const uint8_t* bitstream, uint64_t nbytes, uint64_t nbits,
                             const jt_block_index* index, uint64_t nblocks, const uint16_t* qt,
                             const jt_huff_spec huff[4]);
+
+/* Uploads one mip level in the paper's compact random-access form (Sec. 5.1 "Indexing
+ * Table", Sec. 5.3 "Memory Overhead"), as an alternative to jt_upload_texture; both forms
+ * may be mixed in one context and decode to identical tiles.
+ *  - `stream` (nbytes bytes, unstuffed): MCU m starts on byte
+ *    start(m) = abs_offsets[m / 9] + (m % 9 ? rel_offsets[8 (m / 9) + m % 9 - 1] : 0),
+ *    and its bits end at or before start(m + 1) (the last MCU: at or before nbytes).
+ *    Its data units are coded as in a baseline scan, except that the first luma data unit
+ *    and the chroma data units have no DC difference: their DCs are stored in dc_records.
+ *    The other luma data units code their DC as the difference to the previous luma data
+ *    unit of the same MCU.
+ *  - abs_offsets: ceil(nblocks / 9) uint32; rel_offsets: 8 ceil(nblocks / 9) uint16
+ *    (entries past the last MCU are ignored). Starts must not decrease and must be at most
+ *    nbytes; otherwise JT_ERR_INVALID_ARG.
+ *  - dc_records: ceil(36 nblocks / 32) uint32 words holding a bit array (bit b is bit
+ *    b % 32 of word b / 32); MCU m's first-luma, Cb and Cr DCs are the 12-bit two's
+ *    complement values at bits 36 m, 36 m + 12 and 36 m + 24.
+ * Everything else (sizes, tables, limits, gids, ownership) is as for jt_upload_texture. */
+jt_status jt_upload_texture_compact(jt_ctx* ctx, int tex_id, int level, int width, int height, int sampling,
+                                    const uint8_t* stream, uint64_t nbytes, const uint32_t* abs_offsets,
+                                    const uint16_t* rel_offsets, const uint32_t* dc_records, uint64_t nblocks,
+                                    const uint16_t* qt, const jt_huff_spec huff[4]);
 
 /* ---- per-frame path -------------------------------------------------------------------- */
 

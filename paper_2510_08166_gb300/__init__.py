@@ -80,6 +80,7 @@ _SIGS = {
     "jt_last_error": [_P],
     "jt_status_string": [_I],
     "jt_upload_texture": [_P, _I, _I, _I, _I, _I, _P, _U64, _U64, _P, _U64, _P, _P],
+    "jt_upload_texture_compact": [_P, _I, _I, _I, _I, _I, _P, _U64, _P, _P, _P, _U64, _P, _P],
     "jt_mark": [_P, ctypes.POINTER(jt_gbuffer), _I, _P],
     "jt_decode": [_P, _P],
     "jt_colorize": [_P, ctypes.POINTER(jt_gbuffer), _I, _P, _P],
@@ -245,9 +246,26 @@ class Context:
                                             scan.ctypes.data, scan.size, int(enc.scan_bits), idx.ctypes.data,
                                             idx.size, qt.ctypes.data, _huff_specs(enc.huff_bits, enc.huff_vals)))
 
-    def upload_set(self, ts) -> None:
+    def upload_compact(self, tex_id: int, level: int, enc) -> None:
+        """Uploads enc.compact: the paper's compact form (byte-aligned MCUs, two-level
+        offset table, 12-bit DC records; Sec. 5.1, 5.3)."""
+        c = enc.compact
+        scan = np.ascontiguousarray(c.scan, np.uint8)
+        a = np.ascontiguousarray(c.abs, np.uint32)
+        r = np.ascontiguousarray(c.rel, np.uint16)
+        dc = np.ascontiguousarray(c.dc, np.uint32)
+        qt = np.ascontiguousarray(enc.qt, np.uint16)
+        n = enc.mcus_x * enc.mcus_y
+        if a.size != (n + 8) // 9 or r.size != 8 * a.size or dc.size != (36 * n + 31) // 32:
+            raise JTError(1, "compact side-table sizes do not match the level")
+        self._check(lib().jt_upload_texture_compact(self._h, tex_id, level, enc.width, enc.height, enc.sampling,
+                                                    scan.ctypes.data, scan.size, a.ctypes.data, r.ctypes.data,
+                                                    dc.ctypes.data, n, qt.ctypes.data,
+                                                    _huff_specs(enc.huff_bits, enc.huff_vals)))
+
+    def upload_set(self, ts, compact: bool = False) -> None:
         for t, l, e in ts.uploads():
-            self.upload(t, l, e)
+            (self.upload_compact if compact else self.upload)(t, l, e)
 
     # ---- frame ----
     def mark(self, gb: DeviceGBuffer, filter: int, stream=None):

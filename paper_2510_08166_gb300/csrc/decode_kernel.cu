@@ -164,19 +164,24 @@ __device__ __noinline__ uint32_t walk_symbol(const HuffTable* t, uint32_t w, boo
 // read gives (l, s, r), the s value bits are cut from the same window (T.81 EXTEND without
 // a branch), and the window advances by a select; the next stream word is read ahead. The
 // move to the next data unit (predictor save/restore, table choice) is also branch-free.
-// hs: the lane's tables (shared or global memory). Returns the bit position after the MCU
-// relative to the first staged word, or 0xFFFFFFFF on an invalid coding.
-template <int M, bool SH>
+// hs: the lane's tables (shared or global memory). CPT: the compact form, where the first
+// luma data unit and the chroma data units carry no DC difference and their DCs are
+// p0, p1, p2 as given. Returns the bit position after the MCU relative to the first staged
+// word, or 0xFFFFFFFF on an invalid coding.
+template <int M, bool SH, bool CPT>
 __device__ __forceinline__ uint32_t decode_mcu(const Words& W, uint32_t bit0, const Tables<SH>& T, int ndu,
                                                int16_t& p0, int16_t& p1, int16_t& p2, int16_t* coef) {
+  constexpr bool cpt = CPT;
   uint32_t widx = bit0 >> 5, pos = bit0 & 31;
   uint32_t hi = W(widx), lo = W(widx + 1), nx = W(widx + 2);
   // second-level ranges of the four tables, held in registers so that no table read other
   // than the two LUT entries sits on the chain
   const uint32_t F0 = T.first16(0), F1 = T.first16(1), F2 = T.first16(2), F3 = T.first16(3);
   const uint32_t N0 = T.n2(0), N1 = T.n2(1), N2 = T.n2(2), N3 = T.n2(3);
-  int du = 0, k = 0, comp = 0, pc = p0, q0 = p0, q1 = p1, q2 = p2;
-  uint32_t ti = 0, boff = 0;  // ti: table of the next symbol (0 DC luma, 1 AC luma, 2 DC chroma, 3 AC chroma)
+  int du = 0, k = cpt ? 1 : 0, comp = 0, pc = p0, q0 = p0, q1 = p1, q2 = p2;
+  // ti: table of the next symbol (0 DC luma, 1 AC luma, 2 DC chroma, 3 AC chroma)
+  uint32_t ti = cpt ? 1u : 0u, boff = 0;
+  if (cpt) coef[0] = (int16_t)pc;
   bool bad = false;
 #pragma unroll 1
   for (int it = 0; it < 64 * 6; ++it) {  // at most 64 symbols per data unit
@@ -229,6 +234,11 @@ __device__ __forceinline__ uint32_t decode_mcu(const Words& W, uint32_t bit0, co
     boff += done ? 64u : 0u;
     k = done ? 0 : k;
     if (du == ndu || bad) break;
+    if (cpt && done && cn != 0) {  // compact form: a chroma DC is stored, not coded
+      coef[boff * M] = (int16_t)pc;
+      k = 1;
+      ti |= 1u;
+    }
   }
   p0 = (int16_t)q0;
   p1 = (int16_t)q1;
@@ -296,7 +306,8 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
     const uint32_t di = act ? __ldg(a.desc_of_gid + gid) : 0u;
     int ndu = 0;
     bool s420 = true, store = false;
-    uint32_t off = 0, nbits = 0, bitpos = 0, w0 = 0, want = 0, nwords = 0;
+    uint32_t off = 0, nbits = 0, bitpos = 0, endbit = 0, w0 = 0, want = 0, nwords = 0;
+    bool cpt = false;
     const uint32_t* words = nullptr;
     const uint16_t* Q = a.quant;  // the MCU's quantisation tables (zig-zag), read through L1
     int16_t pr0 = 0, pr1 = 0, pr2 = 0;
@@ -311,18 +322,39 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
         ndu = s420 ? 6 : 3;
         off = __ldg(a.slot + gid);
         store = off + d.units <= a.cap_units;
-        const uint16_t* ix = d.index + (size_t)mcu * 5;
-        bitpos = (uint32_t)__ldg(ix) | ((uint32_t)__ldg(ix + 1) << 16);
-        pr0 = (int16_t)__ldg(ix + 2);
-        pr1 = (int16_t)__ldg(ix + 3);
-        pr2 = (int16_t)__ldg(ix + 4);
+        cpt = d.compact != 0;
+        if (cpt) {
+          // compact form (Sec. 5.1, 5.3): byte offsets from the two-level table, the three
+          // stored DCs from the MCU's 36-bit record (at a multiple of 4 bits, so two words)
+          const uint32_t ng = (d.nmcu + 8) / 9;
+          const uint32_t* ab = reinterpret_cast<const uint32_t*>(d.index);
+          const uint16_t* rl = d.index + 2 * (size_t)ng;
+          const uint32_t* rec = ab + 5 * (size_t)ng;
+          auto start = [&](uint32_t m) {
+            const uint32_t j = m / 9, i = m - 9 * j;
+            return 8u * (__ldg(ab + j) + (i ? (uint32_t)__ldg(rl + 8 * j + i - 1) : 0u));
+          };
+          bitpos = start(mcu);
+          endbit = mcu + 1 < d.nmcu ? start(mcu + 1) : d.nbits;
+          const uint64_t at = 36ull * mcu;
+          const uint64_t r = ((uint64_t)__ldg(rec + (at >> 5)) | ((uint64_t)__ldg(rec + (at >> 5) + 1) << 32)) >>
+                             (at & 31);
+          pr0 = (int16_t)((int32_t)((uint32_t)r << 20) >> 20);  // 12-bit two's complement
+          pr1 = (int16_t)((int32_t)((uint32_t)(r >> 12) << 20) >> 20);
+          pr2 = (int16_t)((int32_t)((uint32_t)(r >> 24) << 20) >> 20);
+        } else {
+          const uint16_t* ix = d.index + (size_t)mcu * 5;
+          bitpos = (uint32_t)__ldg(ix) | ((uint32_t)__ldg(ix + 1) << 16);
+          pr0 = (int16_t)__ldg(ix + 2);
+          pr1 = (int16_t)__ldg(ix + 3);
+          pr2 = (int16_t)__ldg(ix + 4);
+          endbit = mcu + 1 < d.nmcu ? ((uint32_t)__ldg(ix + 5) | ((uint32_t)__ldg(ix + 6) << 16)) : d.nbits;
+        }
         words = d.stream;
         nwords = d.nwords;
         nbits = d.nbits;
         // the MCU's words: from its first word (16 B aligned) to the next MCU's start plus
         // the window's look-ahead (3 words)
-        const uint32_t endbit =
-            mcu + 1 < d.nmcu ? ((uint32_t)__ldg(ix + 5) | ((uint32_t)__ldg(ix + 6) << 16)) : d.nbits;
         w0 = (bitpos >> 5) & ~3u;
         want = (max(endbit, bitpos) >> 5) + 3 - w0;
         want = (want + 3) & ~3u;
@@ -362,12 +394,18 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
     if (act) {
       const Words W{(uint32_t)__cvta_generic_to_shared(stage + sbeg), nst, words + w0,
                     nwords > w0 ? nwords - w0 : 0u};
-      const uint32_t end =
-          hs == sh->t
-              ? decode_mcu<M, true>(W, bitpos - w0 * 32, Tables<true>{hs, (uint32_t)__cvta_generic_to_shared(sh->t)},
-                                    ndu, pr0, pr1, pr2, col)
-              : decode_mcu<M, false>(W, bitpos - w0 * 32, Tables<false>{hs, 0u}, ndu, pr0, pr1, pr2, col);
-      if (end == 0xFFFFFFFFu || (uint64_t)w0 * 32 + end > nbits) any_bad = true;
+      const Tables<true> TS{hs, (uint32_t)__cvta_generic_to_shared(sh->t)};
+      const Tables<false> TG{hs, 0u};
+      const uint32_t b0 = bitpos - w0 * 32;
+      uint32_t end;
+      if (hs == sh->t)
+        end = cpt ? decode_mcu<M, true, true>(W, b0, TS, ndu, pr0, pr1, pr2, col)
+                  : decode_mcu<M, true, false>(W, b0, TS, ndu, pr0, pr1, pr2, col);
+      else
+        end = cpt ? decode_mcu<M, false, true>(W, b0, TG, ndu, pr0, pr1, pr2, col)
+                  : decode_mcu<M, false, false>(W, b0, TG, ndu, pr0, pr1, pr2, col);
+      // a compact MCU must also end inside its own bytes
+      if (end == 0xFFFFFFFFu || (uint64_t)w0 * 32 + end > (cpt ? endbit : nbits)) any_bad = true;
     }
 
     // ---- IDCT: each active lane transforms its own MCU (column m of the buffer, so the

@@ -690,18 +690,20 @@ static jt_status add_level(jt_ctx* c, int tex_id, int level, DevDesc d, Level L)
   return sync_descs(c);
 }
 
-jt_status jt_upload_texture(jt_ctx* c, int tex_id, int level, int width, int height, int sampling,
-                            const uint8_t* bitstream, uint64_t nbytes, uint64_t nbits, const jt_block_index* index,
-                            uint64_t nblocks, const uint16_t* qt, const jt_huff_spec huff[4]) {
-  if (!c) return JT_ERR_INVALID_ARG;
+// Shared by both texture forms: checks, tables, device copies of the stream and of the side
+// table (side_bytes of `side`, already in the device layout), descriptor.
+static jt_status upload_level(jt_ctx* c, int tex_id, int level, int width, int height, int sampling,
+                              const uint8_t* bitstream, uint64_t nbytes, uint64_t nbits, const void* side,
+                              uint64_t side_bytes, uint64_t nblocks, bool compact, const uint16_t* qt,
+                              const jt_huff_spec huff[4]) {
   if (c->phase == Phase::Marked) return fail(c, JT_ERR_STATE, "upload between jt_mark and jt_decode");
   if (tex_id < 0 || tex_id >= 0xFFFF || level < 0 || level >= JT_MAX_LEVELS)
     return fail(c, JT_ERR_INVALID_ARG, "texture id %d / level %d out of range", tex_id, level);
   if (width <= 0 || height <= 0 || width > 65535 || height > 65535)
     return fail(c, JT_ERR_INVALID_ARG, "bad size %dx%d", width, height);
   if (sampling != 420 && sampling != 444) return fail(c, JT_ERR_INVALID_ARG, "sampling must be 420 or 444");
-  if (!bitstream || !index || !qt || !huff) return fail(c, JT_ERR_INVALID_ARG, "null upload pointer");
-  if (nbits > nbytes * 8 || nbytes >= (1ull << 31)) return fail(c, JT_ERR_INVALID_ARG, "bad stream size");
+  if (!bitstream || !side || !qt || !huff) return fail(c, JT_ERR_INVALID_ARG, "null upload pointer");
+  if (nbits > nbytes * 8 || nbytes >= (1ull << 29)) return fail(c, JT_ERR_INVALID_ARG, "bad stream size");
   if ((uint32_t)tex_id < c->map_ntex && c->map[(size_t)tex_id * JT_MAX_LEVELS + level] >= 0)
     return fail(c, JT_ERR_INVALID_ARG, "texture %d level %d already uploaded", tex_id, level);
   const int mw = sampling == 420 ? 16 : 8;
@@ -747,18 +749,18 @@ jt_status jt_upload_texture(jt_ctx* c, int tex_id, int level, int width, int hei
     if (s != JT_OK) return s;
   }
 
-  // stream words (zero padded) and index
+  // stream words (zero padded) and side table
   Level L{tex_id, level};
   const uint64_t words = (nbytes + 3) / 4 + kStreamPadBytes / 4;
   jt_status s;
   if ((s = dev_alloc(c, reinterpret_cast<uint8_t**>(&L.stream_mem), words * 4)) != JT_OK) return s;
-  if ((s = dev_alloc(c, reinterpret_cast<uint8_t**>(&L.index_mem), nblocks * sizeof(jt_block_index) + 16)) != JT_OK) {
+  if ((s = dev_alloc(c, reinterpret_cast<uint8_t**>(&L.index_mem), side_bytes + 16)) != JT_OK) {
     cudaFree(L.stream_mem);
     return s;
   }
   if (cudaMemset(L.stream_mem, 0, words * 4) != cudaSuccess ||
       cudaMemcpy(L.stream_mem, bitstream, nbytes, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(L.index_mem, index, nblocks * sizeof(jt_block_index), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaMemcpy(L.index_mem, side, side_bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
     cudaFree(L.stream_mem);
     cudaFree(L.index_mem);
     return fail(c, JT_ERR_CUDA, "upload copy failed");
@@ -778,7 +780,45 @@ jt_status jt_upload_texture(jt_ctx* c, int tex_id, int level, int width, int hei
   d.units = sampling == 420 ? 4 : 1;
   d.hset = (uint8_t)hset;
   d.qset = (uint8_t)qset;
+  d.compact = compact ? 1 : 0;
   return add_level(c, tex_id, level, d, L);
+}
+
+jt_status jt_upload_texture(jt_ctx* c, int tex_id, int level, int width, int height, int sampling,
+                            const uint8_t* bitstream, uint64_t nbytes, uint64_t nbits, const jt_block_index* index,
+                            uint64_t nblocks, const uint16_t* qt, const jt_huff_spec huff[4]) {
+  if (!c) return JT_ERR_INVALID_ARG;
+  return upload_level(c, tex_id, level, width, height, sampling, bitstream, nbytes, nbits, index,
+                      nblocks * sizeof(jt_block_index), nblocks, false, qt, huff);
+}
+
+jt_status jt_upload_texture_compact(jt_ctx* c, int tex_id, int level, int width, int height, int sampling,
+                                    const uint8_t* stream, uint64_t nbytes, const uint32_t* abs_offsets,
+                                    const uint16_t* rel_offsets, const uint32_t* dc_records, uint64_t nblocks,
+                                    const uint16_t* qt, const jt_huff_spec huff[4]) {
+  if (!c) return JT_ERR_INVALID_ARG;
+  if (!abs_offsets || !rel_offsets || !dc_records) return fail(c, JT_ERR_INVALID_ARG, "null upload pointer");
+  if (nblocks == 0 || nblocks > kMaxGids) return fail(c, JT_ERR_INVALID_ARG, "bad MCU count");
+  // MCU starts must be non-decreasing and inside the stream
+  const uint64_t ng = (nblocks + 8) / 9;
+  uint64_t prev = 0;
+  for (uint64_t m = 0; m < nblocks; ++m) {
+    const uint64_t j = m / 9, i = m % 9;
+    const uint64_t st = (uint64_t)abs_offsets[j] + (i ? rel_offsets[8 * j + i - 1] : 0u);
+    if (st < prev || st > nbytes)
+      return fail(c, JT_ERR_INVALID_ARG, "MCU %llu starts at byte %llu (previous %llu, stream %llu)",
+                  (unsigned long long)m, (unsigned long long)st, (unsigned long long)prev,
+                  (unsigned long long)nbytes);
+    prev = st;
+  }
+  // device layout: [abs x ng][rel x 8 ng][DC records + one zero word]
+  const uint64_t ndc = (36 * nblocks + 31) / 32;
+  std::vector<uint32_t> side(ng + 4 * ng + ndc + 1, 0u);
+  std::memcpy(side.data(), abs_offsets, ng * 4);
+  std::memcpy(side.data() + ng, rel_offsets, ng * 16);
+  std::memcpy(side.data() + 5 * ng, dc_records, ndc * 4);
+  return upload_level(c, tex_id, level, width, height, sampling, stream, nbytes, nbytes * 8, side.data(),
+                      side.size() * 4, nblocks, true, qt, huff);
 }
 
 jt_status jt_mark(jt_ctx* c, const jt_gbuffer* g, int filter, jt_stream stream) {

@@ -66,7 +66,10 @@ struct HuffSet {
 
 struct DevDesc {
   const uint32_t* stream;      // big-endian words (word i = bytes 4i..4i+3)
-  const uint16_t* index;       // packed 10-byte entries, read as 5 halfwords
+  // standard form: packed 10-byte entries, read as 5 halfwords. Compact form: the side
+  // table [abs uint32 x G][rel uint16 x 8G][DC records uint32 x (ceil(36 n / 32) + 1)],
+  // G = ceil(n / 9)
+  const uint16_t* index;
   uint32_t gid_base;
   uint32_t nmcu;
   uint32_t nwords;             // readable words including padding
@@ -76,7 +79,8 @@ struct DevDesc {
   uint8_t sampling;            // kSampling420 / kSampling444 / kSamplingCoef
   uint8_t units;               // cache units per MCU: 4 or 1
   uint8_t hset, qset;
-  uint32_t pad0;
+  uint8_t compact;             // 1: the compact form (byte-aligned MCUs, stored DCs)
+  uint8_t pad0[3];
 };
 static_assert(sizeof(DevDesc) == 48, "descriptor layout");
 

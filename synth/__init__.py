@@ -399,6 +399,32 @@ def config3_views(ts: TextureSet):
     return views
 
 
+def motion_views(ts: TextureSet, W: int = 1920, H: int = 1080, ndir: int = 60, step_deg: float = 6.0,
+                 stereo: bool = False, threads: int | None = None):
+    """The motion test of the paper's caching evaluation: the camera of the 4K scene turns by
+    `step_deg` per frame, `ndir` frames for a full turn. Returns one list of G-buffers per
+    direction: one view, or with `stereo` two eyes 0.064 m apart with a 90 degree field of
+    view (the VR variant)."""
+    p0 = config2_pose()
+    seed = SEED_BASE + 2
+    jobs = []
+    for k in range(ndir):
+        yaw = p0.yaw + step_deg * k
+        if not stereo:
+            jobs.append((k, Pose(p0.cam, yaw, p0.pitch, p0.vfov, p0.quad_seed, 0.0)))
+            continue
+        right = np.array([np.cos(np.radians(yaw)), 0.0, -np.sin(np.radians(yaw))])
+        for sgn in (-1.0, 1.0):
+            cam = tuple(np.array(p0.cam) + sgn * 0.032 * right)
+            jobs.append((k, Pose(cam, yaw, p0.pitch, 90.0, p0.quad_seed, -sgn * 0.008)))
+    with ThreadPoolExecutor(threads or _threads()) as ex:
+        gbs = list(ex.map(lambda j: gbuffer_scene(seed, W, H, ts.sizes, ts.nlevels, j[1], nquads=200), jobs))
+    out = [[] for _ in range(ndir)]
+    for (k, _), g in zip(jobs, gbs):
+        out[k].append(g)
+    return out
+
+
 def config4_textures(ntex: int = 256, size: int = 4096, threads: int | None = None) -> TextureSet:
     """Full-decode stress: `ntex` textures size^2 at Q90; the first half 4:4:4, the second
     half 4:2:0; level 0 only."""
