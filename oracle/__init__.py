@@ -63,6 +63,9 @@ def lib():
         L.jto_texset_add_compact.argtypes = [P, I, I, I, I, I, P, ctypes.c_uint64, P, ctypes.c_uint64, P,
                                              ctypes.c_uint64, P, ctypes.c_uint64, ctypes.c_uint64, P, P, P]
         L.jto_mcu_bits.argtypes = [P, I, I, P, P]
+        L.jto_texset_add_reduced.restype = I64
+        L.jto_texset_add_reduced.argtypes = [P, I, I, I, I]
+        L.jto_idct_pixels_n.argtypes = [P, P, I, I]
         L.jto_texset_decode_mcu.argtypes = [P, I, I, I, P]
         L.jto_mark.restype = I64
         L.jto_mark.argtypes = [P, P, P, P, I64, I, P]
@@ -110,6 +113,14 @@ def idct_pixels(d: np.ndarray) -> np.ndarray:
     d = np.ascontiguousarray(d, np.int32).reshape(-1, 64)
     out = np.empty(d.shape, np.uint8)
     lib().jto_idct_pixels(_p(d), _p(out), d.shape[0])
+    return out
+
+
+def idct_pixels_n(d: np.ndarray, n: int) -> np.ndarray:
+    """Reduced-size IDCT: [blocks, n*n] pixels from the n x n lowest frequencies."""
+    d = np.ascontiguousarray(d, np.int32).reshape(-1, 64)
+    out = np.empty((d.shape[0], n * n), np.uint8)
+    lib().jto_idct_pixels_n(_p(d), _p(out), d.shape[0], n)
     return out
 
 
@@ -218,6 +229,18 @@ class TexSet:
                                          _p(hb), _p(hv))
         if g < 0:
             raise ValueError("oracle rejected compact texture level")
+        self.gid_base[(tex, level)] = int(g)
+        self.nmcu[(tex, level)] = n
+        self.total = int(g) + n
+        return int(g)
+
+    def add_reduced(self, tex: int, src_level: int, reduce: int, level: int) -> int:
+        """Registers `level` as the reduced-resolution decode (1/2^reduce, reduce 1..3) of
+        the registered level `src_level` (the mip alternative of Sec. 7)."""
+        g = lib().jto_texset_add_reduced(self._h, tex, src_level, reduce, level)
+        if g < 0:
+            raise ValueError("oracle rejected reduced level")
+        n = self.nmcu[(tex, src_level)]
         self.gid_base[(tex, level)] = int(g)
         self.nmcu[(tex, level)] = n
         self.total = int(g) + n

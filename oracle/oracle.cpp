@@ -210,43 +210,52 @@ bool decode_du(BitReader& br, const HuffTable& dc, const HuffTable& ac, int16_t&
 // ---------------------------------------------------------------------------------------
 // Integer IDCT and colour conversion (the decode spec)
 // ---------------------------------------------------------------------------------------
-const int64_t* idct_matrix() {  // K[x*8+u]
-  static int64_t K[64];
+// N-point IDCT matrix K_N[x*N+u] = round(2^14 c_u cos((2x+1) u pi / (2N))), c_0 = 1/(2 sqrt 2),
+// c_u = 1/2, for N = 8 (the full decode) and N = 4, 2, 1 (the reduced-resolution decode of
+// Sec. 7's mip alternative: the N x N lowest frequencies give the block at 1/(8/N) scale;
+// the c_u keep their 8-point values because the N-point orthonormal coefficients of a
+// block averaged down by 8/N are the 8-point ones times sqrt(N/8) per axis).
+const int64_t* idct_matrix(int N = 8) {
+  static int64_t K[4][64];
   static bool done = false;
   if (!done) {
-    for (int x = 0; x < 8; ++x)
-      for (int u = 0; u < 8; ++u) {
-        double cu = u == 0 ? 1.0 / (2.0 * std::sqrt(2.0)) : 0.5;
-        K[x * 8 + u] = std::lround(16384.0 * cu * std::cos((2 * x + 1) * u * M_PI / 16.0));
-      }
+    for (int r = 0; r < 4; ++r) {
+      const int n = 8 >> r;
+      for (int x = 0; x < n; ++x)
+        for (int u = 0; u < n; ++u) {
+          double cu = u == 0 ? 1.0 / (2.0 * std::sqrt(2.0)) : 0.5;
+          K[r][x * n + u] = std::lround(16384.0 * cu * std::cos((2 * x + 1) * u * M_PI / (2.0 * n)));
+        }
+    }
     done = true;
   }
-  return K;
+  return K[N == 8 ? 0 : N == 4 ? 1 : N == 2 ? 2 : 3];
 }
 
-// out[y*8+x] = signed spatial value before the +128 level shift (for accuracy tests).
-void idct_raw(const int32_t d_in[64], int32_t out[64]) {
-  const int64_t* K = idct_matrix();
+// out[y*N+x] = signed spatial value before the +128 level shift, from the N x N lowest
+// frequencies d_in[v*8+u], u, v < N (N = 8: the whole block).
+void idct_raw(const int32_t d_in[64], int32_t out[64], int N = 8) {
+  const int64_t* K = idct_matrix(N);
   int64_t d[64], t[64];
   for (int i = 0; i < 64; ++i) d[i] = clamp64(d_in[i], -32768, 32767);
-  for (int u = 0; u < 8; ++u)  // column pass: 1-D IDCT down each column (v -> y)
-    for (int y = 0; y < 8; ++y) {
+  for (int u = 0; u < N; ++u)  // column pass: 1-D IDCT down each column (v -> y)
+    for (int y = 0; y < N; ++y) {
       int64_t s = 0;
-      for (int v = 0; v < 8; ++v) s += K[y * 8 + v] * d[v * 8 + u];
+      for (int v = 0; v < N; ++v) s += K[y * N + v] * d[v * 8 + u];
       t[y * 8 + u] = clamp64(floor_div(s + 256, 512), -32768, 32767);
     }
-  for (int y = 0; y < 8; ++y)  // row pass: 1-D IDCT along each row (u -> x)
-    for (int x = 0; x < 8; ++x) {
+  for (int y = 0; y < N; ++y)  // row pass: 1-D IDCT along each row (u -> x)
+    for (int x = 0; x < N; ++x) {
       int64_t s = 0;
-      for (int u = 0; u < 8; ++u) s += K[x * 8 + u] * t[y * 8 + u];
-      out[y * 8 + x] = (int32_t)floor_div(s + 262144, 524288);
+      for (int u = 0; u < N; ++u) s += K[x * N + u] * t[y * 8 + u];
+      out[y * N + x] = (int32_t)floor_div(s + 262144, 524288);
     }
 }
 
-void idct_pixels(const int32_t d[64], uint8_t out[64]) {
+void idct_pixels(const int32_t d[64], uint8_t out[64], int N = 8) {
   int32_t r[64];
-  idct_raw(d, r);
-  for (int i = 0; i < 64; ++i) out[i] = (uint8_t)clamp64(r[i] + 128, 0, 255);
+  idct_raw(d, r, N);
+  for (int i = 0; i < N * N; ++i) out[i] = (uint8_t)clamp64(r[i] + 128, 0, 255);
 }
 
 void ycc_to_rgb(int Y, int Cb, int Cr, uint8_t rgb[3]) {
@@ -256,28 +265,31 @@ void ycc_to_rgb(int Y, int Cb, int Cr, uint8_t rgb[3]) {
   rgb[2] = (uint8_t)clamp64(Y + floor_div(116130 * cb + 32768, 65536), 0, 255);
 }
 
-// One decoded MCU -> RGBA8 tile (16x16 at 4:2:0, 8x8 at 4:4:4), row-major.
-void mcu_to_tile(const int32_t q[6][64], int sampling, const uint16_t qt[2][64], uint8_t* tile) {
+// One decoded MCU -> RGBA8 tile, row-major: 16x16 at 4:2:0, 8x8 at 4:4:4, divided by 2^r
+// along each axis for the reduced-resolution decode (r = 0..3; each data unit gives
+// N x N pixels, N = 8 >> r; 4:2:0 chroma is replicated 2x2 as at full size).
+void mcu_to_tile(const int32_t q[6][64], int sampling, const uint16_t qt[2][64], uint8_t* tile, int r = 0) {
   const int ndu = sampling == 420 ? 6 : 3;
+  const int N = 8 >> r;
   uint8_t px[6][64];
   for (int d = 0; d < ndu; ++d) {
     int comp = d < ndu - 2 ? 0 : 1;
     int32_t deq[64];
     for (int k = 0; k < 64; ++k) deq[k] = q[d][k] * (int32_t)qt[comp][k];  // dequantise
-    idct_pixels(deq, px[d]);
+    idct_pixels(deq, px[d], N);
   }
-  const int mw = sampling == 420 ? 16 : 8;
+  const int mw = (sampling == 420 ? 16 : 8) >> r;
   for (int y = 0; y < mw; ++y)
     for (int x = 0; x < mw; ++x) {
       int Y, Cb, Cr;
       if (sampling == 420) {
-        Y = px[(y / 8) * 2 + (x / 8)][(y % 8) * 8 + (x % 8)];
-        Cb = px[4][(y >> 1) * 8 + (x >> 1)];
-        Cr = px[5][(y >> 1) * 8 + (x >> 1)];
+        Y = px[(y / N) * 2 + (x / N)][(y % N) * N + (x % N)];
+        Cb = px[4][(y >> 1) * N + (x >> 1)];
+        Cr = px[5][(y >> 1) * N + (x >> 1)];
       } else {
-        Y = px[0][y * 8 + x];
-        Cb = px[1][y * 8 + x];
-        Cr = px[2][y * 8 + x];
+        Y = px[0][y * N + x];
+        Cb = px[1][y * N + x];
+        Cr = px[2][y * N + x];
       }
       uint8_t* o = tile + (y * mw + x) * 4;
       ycc_to_rgb(Y, Cb, Cr, o);
@@ -456,7 +468,8 @@ struct Level {
   HuffTable tab[4];
   std::unordered_map<int, std::vector<uint8_t>> tiles;  // decoded MCUs, by MCU id
   std::vector<uint8_t> full;                            // optional full RGBA decode
-  int mw() const { return sampling == 420 ? 16 : 8; }
+  int reduce = 0;  // reduced-resolution decode of a stored level: tiles at 1/2^reduce (Sec. 7)
+  int mw() const { return (sampling == 420 ? 16 : 8) >> reduce; }
 };
 
 struct TexSet {
@@ -503,7 +516,7 @@ int decode_mcu_compact(const Level& L, int mcu, uint8_t* tile) {
     if (!decode_du(br, L.tab[tb * 2], L.tab[tb * 2 + 1], pred[comp], q[d], !stored)) return -1;
   }
   if (br.pos > compact_start(L, mcu + 1)) return -1;
-  mcu_to_tile(q, L.sampling, L.qt, tile);
+  mcu_to_tile(q, L.sampling, L.qt, tile, L.reduce);
   return 0;
 }
 
@@ -522,7 +535,7 @@ int decode_mcu(const Level& L, int mcu, uint8_t* tile) {
     if (!decode_du(br, L.tab[tb * 2], L.tab[tb * 2 + 1], pred[comp], q[d])) return -1;
   }
   if (br.pos > L.nbits) return -1;
-  mcu_to_tile(q, L.sampling, L.qt, tile);
+  mcu_to_tile(q, L.sampling, L.qt, tile, L.reduce);
   return 0;
 }
 
@@ -599,6 +612,12 @@ void jto_idct_matrix(int64_t* out) { std::memcpy(out, idct_matrix(), 64 * sizeof
 
 void jto_idct_raw(const int32_t* d, int32_t* out, int nblocks) {
   for (int b = 0; b < nblocks; ++b) idct_raw(d + 64 * b, out + 64 * b);
+}
+
+// Reduced-size IDCT: N x N pixels (row-major, N*N bytes per block) from the N x N lowest
+// frequencies of each dequantised block.
+void jto_idct_pixels_n(const int32_t* d, uint8_t* out, int nblocks, int N) {
+  for (int b = 0; b < nblocks; ++b) idct_pixels(d + 64 * b, out + N * N * b, N);
 }
 
 void jto_idct_pixels(const int32_t* d, uint8_t* out, int nblocks) {
@@ -729,6 +748,25 @@ int64_t jto_texset_add_compact(void* s, int tex, int level, int w, int h, int sa
   L->c_abs.assign(abs_off, abs_off + nabs);
   L->c_rel.assign(rel_off, rel_off + nrel);
   L->c_dc.assign(dc, dc + ndc);
+  return register_level(S, L);
+}
+
+// Registers level `level` of texture `tex` as the reduced-resolution decode of the already
+// registered level `src_level` (the mip alternative of Sec. 7): each MCU of the source,
+// decoded from its N x N lowest frequencies (N = 8 >> reduce), gives a tile of 1/2^reduce
+// the size. The level is max(1, w >> reduce) x max(1, h >> reduce) texels on the source's
+// MCU grid and gets its own gid range. Returns the gid base, or -1.
+int64_t jto_texset_add_reduced(void* s, int tex, int src_level, int reduce, int level) {
+  TexSet* S = static_cast<TexSet*>(s);
+  Level* src = find_level(*S, tex, src_level);
+  if (!src || src->reduce != 0 || reduce < 1 || reduce > 3 || S->levels.count({tex, level})) return -1;
+  Level* L = new Level(*src);
+  L->tiles.clear();
+  L->full.clear();
+  L->level = level;
+  L->reduce = reduce;
+  L->w = std::max(1, src->w >> reduce);
+  L->h = std::max(1, src->h >> reduce);
   return register_level(S, L);
 }
 
