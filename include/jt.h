@@ -176,6 +176,19 @@ jt_status jt_upload_texture_compact(jt_ctx* ctx, int tex_id, int level, int widt
                                     const uint16_t* rel_offsets, const uint32_t* dc_records, uint64_t nblocks,
                                     const uint16_t* qt, const jt_huff_spec huff[4]);
 
+/* Registers level `level` of texture `tex_id` as the reduced-resolution decode of the
+ * stored level `src_level` (the mip alternative of Sec. 7: a lower resolution from the
+ * lowest frequencies only). Each data unit of the source gives N x N texels (N = 8 >> reduce,
+ * reduce = 1, 2 or 3; 3 = the DC alone) by the N-point IDCT of its N x N lowest-frequency
+ * coefficients with the 8-point normalisation (the block at 1/2^reduce scale) and the same
+ * integer rounding as the full decode; an MCU becomes a (mw >> reduce)^2 tile, 4:2:0 chroma
+ * replicated 2x2 as at full size. The level is max(1, w >> reduce) x max(1, h >> reduce)
+ * texels on the source's MCU grid, gets its own gids (as many as the source has MCUs) and
+ * shares the source's stream, index and tables. The source must be a level uploaded with
+ * jt_upload_texture or jt_upload_texture_compact; `level` must not exist yet. Not allowed
+ * between jt_mark and jt_decode. */
+jt_status jt_add_reduced_level(jt_ctx* ctx, int tex_id, int src_level, int reduce, int level);
+
 /* ---- per-frame path -------------------------------------------------------------------- */
 
 /* Mark (Sec. 4.2): for every pixel with a texture, computes the texel(s) its uv falls on at

@@ -81,6 +81,7 @@ _SIGS = {
     "jt_status_string": [_I],
     "jt_upload_texture": [_P, _I, _I, _I, _I, _I, _P, _U64, _U64, _P, _U64, _P, _P],
     "jt_upload_texture_compact": [_P, _I, _I, _I, _I, _I, _P, _U64, _P, _P, _P, _U64, _P, _P],
+    "jt_add_reduced_level": [_P, _I, _I, _I, _I],
     "jt_mark": [_P, ctypes.POINTER(jt_gbuffer), _I, _P],
     "jt_decode": [_P, _P],
     "jt_colorize": [_P, ctypes.POINTER(jt_gbuffer), _I, _P, _P],
@@ -263,6 +264,11 @@ class Context:
                                                     dc.ctypes.data, n, qt.ctypes.data,
                                                     _huff_specs(enc.huff_bits, enc.huff_vals)))
 
+    def add_reduced_level(self, tex_id: int, src_level: int, reduce: int, level: int) -> None:
+        """Registers `level` as the 1/2^reduce decode of the stored level `src_level` from its
+        lowest frequencies (reduce 1..3; Sec. 7's mip alternative)."""
+        self._check(lib().jt_add_reduced_level(self._h, tex_id, src_level, reduce, level))
+
     def upload_set(self, ts, compact: bool = False) -> None:
         for t, l, e in ts.uploads():
             (self.upload_compact if compact else self.upload)(t, l, e)
@@ -363,12 +369,13 @@ class Context:
         self._check(lib().jt_read_cache(self._h, unit_begin, n, out.ctypes.data))
         return out
 
-    def tile(self, gid: int, sampling: int) -> np.ndarray:
-        """RGBA8 tile of a gid from the last decode ([16,16,4] at 4:2:0, [8,8,4] at 4:4:4)."""
+    def tile(self, gid: int, sampling: int, reduce: int = 0) -> np.ndarray:
+        """RGBA8 tile of a gid from the last decode ([16,16,4] at 4:2:0, [8,8,4] at 4:4:4,
+        each side divided by 2^reduce for a reduced-resolution level)."""
         off = int(self.slots(gid, 1)[0])
-        if sampling == 420:
-            return self.cache_units(off, 4).reshape(16, 16, 4)
-        return self.cache_units(off, 1).reshape(8, 8, 4)
+        mw = (16 if sampling == 420 else 8) >> reduce
+        units = 4 if (sampling == 420 and reduce == 0) else 1
+        return self.cache_units(off, units).reshape(-1)[:mw * mw * 4].reshape(mw, mw, 4)
 
     def set_block_cache(self, persistent: bool) -> None:
         """Cross-frame block cache on (decode only MCUs not already resident) or off."""

@@ -73,6 +73,24 @@ __device__ __forceinline__ void idct8(const int in[8], int out[8]) {
 __device__ __forceinline__ int sat16(int v) { return min(32767, max(-32768, v)); }
 __device__ __forceinline__ uint32_t clamp255(int v) { return (uint32_t)min(255, max(0, v)); }
 
+// N-point IDCT of the N lowest frequencies, N = 4, 2, 1 (reduced-resolution decode):
+// out[x] = sum_u K_N[x][u] in[u] with K_N[x][u] = round(2^14 c_u cos((2x+1) u pi / (2N))) and
+// the 8-point c_u. The N-point cosines are the 8-point ones at even multiples, so N = 4 is
+// the even half of idct8 (inputs at 0, 2, 4, 6), N = 2 its first butterfly, N = 1 the DC term.
+template <int N>
+__device__ __forceinline__ void idct_small(const int in[4], int out[4]) {
+  if (N == 4) {
+    const int a0 = C4 * (in[0] + in[2]), a1 = C4 * (in[0] - in[2]);
+    const int b0 = C2 * in[1] + C6 * in[3], b1 = C6 * in[1] - C2 * in[3];
+    out[0] = a0 + b0; out[1] = a1 + b1; out[2] = a1 - b1; out[3] = a0 - b0;
+  } else if (N == 2) {
+    out[0] = C4 * (in[0] + in[1]);
+    out[1] = C4 * (in[0] - in[1]);
+  } else {
+    out[0] = C4 * in[0];
+  }
+}
+
 // Words of the MCUs' entropy-coded data copied to shared memory before their serial decode
 // (random loads from HBM take thousands of cycles and would otherwise sit on the serial
 // chain once per word). A warp has kStageWords words per MCU as one pool, shared out by a
@@ -266,6 +284,68 @@ __device__ __forceinline__ uint32_t pixel2(const int16_t* col, int d, int y, int
   return (uint16_t)col[(d * 64 + zz_pos(y, i)) * M];
 }
 
+// Reduced-resolution IDCT of one data unit (N = 8 >> R) in place over the buffer: the same
+// dequantisation and rounding as the full transform on the N x N lowest frequencies; the
+// row pass leaves pixel pairs (x = 2i, 2i+1) in slots zz_pos(y, i), i < N/2 (N = 1: the
+// pixel in the low byte of slot 0), which pixel2() reads as for the full size.
+template <int M, int R>
+__device__ __forceinline__ void idct_reduced(int16_t* blk, const uint16_t* Qd) {
+  constexpr int N = 8 >> R;
+#pragma unroll
+  for (int u = 0; u < N; ++u) {
+    int in[4] = {0, 0, 0, 0}, out[4];
+#pragma unroll
+    for (int v = 0; v < N; ++v) {
+      const int k = zz_pos(v, u);
+      in[v] = sat16(blk[k * M] * (int)__ldg(Qd + k));
+    }
+    idct_small<N>(in, out);
+#pragma unroll
+    for (int y = 0; y < N; ++y) blk[zz_pos(y, u) * M] = (int16_t)sat16((out[y] + 256) >> 9);
+  }
+#pragma unroll
+  for (int y = 0; y < N; ++y) {
+    int in[4] = {0, 0, 0, 0}, out[4];
+#pragma unroll
+    for (int x = 0; x < N; ++x) in[x] = blk[zz_pos(y, x) * M];
+    idct_small<N>(in, out);
+    if (N == 1) {
+      blk[zz_pos(y, 0) * M] = (int16_t)clamp255(((out[0] + (1 << 18)) >> 19) + 128);
+    } else {
+#pragma unroll
+      for (int i = 0; i < N / 2; ++i)
+        blk[zz_pos(y, i) * M] = (int16_t)(clamp255(((out[2 * i] + (1 << 18)) >> 19) + 128) |
+                                          (clamp255(((out[2 * i + 1] + (1 << 18)) >> 19) + 128) << 8));
+    }
+  }
+}
+
+// Colour conversion of a reduced tile ((mw >> r)^2 texels, mw = 16 at 4:2:0, 8 at 4:4:4),
+// chroma replicated 2x2 at 4:2:0 as at full size; one 4-byte store per texel.
+template <int M>
+__device__ __noinline__ void colour_reduced(const int16_t* col, bool s420, int red, uint32_t* tile) {
+  const int n = 8 >> red, tw = (s420 ? 16 : 8) >> red;
+  auto pix = [&](int d, int y, int x) { return (pixel2<M>(col, d, y, x >> 1) >> (8 * (x & 1))) & 255u; };
+#pragma unroll 1
+  for (int ty = 0; ty < tw; ++ty)
+#pragma unroll 1
+    for (int tx = 0; tx < tw; ++tx) {
+      uint32_t Y, cb, cr;
+      if (s420) {
+        Y = pix((ty / n) * 2 + tx / n, ty % n, tx % n);
+        cb = pix(4, ty >> 1, tx >> 1);
+        cr = pix(5, ty >> 1, tx >> 1);
+      } else {
+        Y = pix(0, ty, tx);
+        cb = pix(1, ty, tx);
+        cr = pix(2, ty, tx);
+      }
+      int ro, go, bo;
+      chroma_offsets(cb, cr, ro, go, bo);
+      tile[ty * tw + tx] = ycc_pixel(Y, ro, go, bo);
+    }
+}
+
 template <int M>
 __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
@@ -308,6 +388,7 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
     bool s420 = true, store = false;
     uint32_t off = 0, nbits = 0, bitpos = 0, endbit = 0, w0 = 0, want = 0, nwords = 0;
     bool cpt = false;
+    int red = 0;  // reduced-resolution level: 1/2^red
     const uint32_t* words = nullptr;
     const uint16_t* Q = a.quant;  // the MCU's quantisation tables (zig-zag), read through L1
     int16_t pr0 = 0, pr1 = 0, pr2 = 0;
@@ -323,6 +404,7 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
         off = __ldg(a.slot + gid);
         store = off + d.units <= a.cap_units;
         cpt = d.compact != 0;
+        red = d.reduce;
         if (cpt) {
           // compact form (Sec. 5.1, 5.3): byte offsets from the two-level table, the three
           // stored DCs from the MCU's 36-bit record (at a multiple of 4 bits, so two words)
@@ -411,7 +493,20 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
     // ---- IDCT: each active lane transforms its own MCU (column m of the buffer, so the
     // warp's accesses are consecutive). Column pass with dequantisation on load:
     // t = clamp16(floor((sum_v K[y][v] clamp16(q Q) + 2^8) / 2^9)), written back in place.
-    if (act) {
+    if (act && red != 0) {  // reduced-resolution levels (rare): small transforms
+#pragma unroll 1
+      for (int d = 0; d < ndu; ++d) {
+        const uint16_t* Qd = Q + (d < ndu - 2 ? 0 : 64);
+        int16_t* blk = col + d * 64 * M;
+        if (red == 1)
+          idct_reduced<M, 1>(blk, Qd);
+        else if (red == 2)
+          idct_reduced<M, 2>(blk, Qd);
+        else
+          idct_reduced<M, 3>(blk, Qd);
+      }
+    }
+    if (act && red == 0) {
 #pragma unroll 1
       for (int d = 0; d < ndu; ++d) {
         const uint16_t* Qd = Q + (d < ndu - 2 ? 0 : 64);
@@ -449,7 +544,9 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
 
     // ---- colour conversion + tile stores: each active lane writes its own MCU's tile,
     // four texels (16 B) per store ----
-    if (act && store) {
+    if (act && store && red != 0)
+      colour_reduced<M>(col, s420, red, reinterpret_cast<uint32_t*>(a.cache + (size_t)off * kUnitBytes));
+    if (act && store && red == 0) {
       uint8_t* tile = a.cache + (size_t)off * kUnitBytes;
       if (s420) {  // 16x16 texels; chroma sample (cx, cy) covers texels 2cx..2cx+1, 2cy..2cy+1
 #pragma unroll 1

@@ -664,7 +664,7 @@ static jt_status add_level(jt_ctx* c, int tex_id, int level, DevDesc d, Level L)
   LevelRec& r = c->lrec[(size_t)tex_id * JT_MAX_LEVELS + level];
   r.gid_base = d.gid_base;
   r.wh = (uint32_t)d.width | ((uint32_t)d.height << 16);
-  r.info = level_info(d.mcus_x, d.sampling == kSampling444 ? 3 : 4, d.units, d.sampling, pow2(d.width),
+  r.info = level_info(d.mcus_x, (d.sampling == kSampling444 ? 3u : 4u) - d.reduce, d.units, d.sampling, pow2(d.width),
                       pow2(d.height));
   r.pad = 0;
   c->descs.push_back(d);
@@ -819,6 +819,32 @@ jt_status jt_upload_texture_compact(jt_ctx* c, int tex_id, int level, int width,
   std::memcpy(side.data() + 5 * ng, dc_records, ndc * 4);
   return upload_level(c, tex_id, level, width, height, sampling, stream, nbytes, nbytes * 8, side.data(),
                       side.size() * 4, nblocks, true, qt, huff);
+}
+
+jt_status jt_add_reduced_level(jt_ctx* c, int tex_id, int src_level, int reduce, int level) {
+  if (!c) return JT_ERR_INVALID_ARG;
+  if (c->phase == Phase::Marked) return fail(c, JT_ERR_STATE, "upload between jt_mark and jt_decode");
+  if (reduce < 1 || reduce > 3) return fail(c, JT_ERR_INVALID_ARG, "reduce must be 1, 2 or 3");
+  if (tex_id < 0 || tex_id >= 0xFFFF || src_level < 0 || src_level >= JT_MAX_LEVELS || level < 0 ||
+      level >= JT_MAX_LEVELS)
+    return fail(c, JT_ERR_INVALID_ARG, "texture id %d / level %d / %d out of range", tex_id, src_level, level);
+  const int si = (uint32_t)tex_id < c->map_ntex ? c->map[(size_t)tex_id * JT_MAX_LEVELS + src_level] : -1;
+  if (si < 0) return fail(c, JT_ERR_INVALID_ARG, "texture %d level %d is not uploaded", tex_id, src_level);
+  const DevDesc& src = c->descs[si];
+  if (src.sampling == kSamplingCoef || src.reduce != 0)
+    return fail(c, JT_ERR_INVALID_ARG, "texture %d level %d is not a stored JPEG level", tex_id, src_level);
+  if (c->map[(size_t)tex_id * JT_MAX_LEVELS + level] >= 0)
+    return fail(c, JT_ERR_INVALID_ARG, "texture %d level %d already exists", tex_id, level);
+  if (c->ngid + src.nmcu > kMaxGids) return fail(c, JT_ERR_UNSUPPORTED, "more than 2^26 MCUs in one context");
+  DeviceGuard g(c->device);
+  if (!g.ok) return fail(c, JT_ERR_CUDA, "cannot select device %d", c->device);
+  DevDesc d = src;  // same stream, index and tables; the source level owns the memory
+  d.gid_base = (uint32_t)c->ngid;
+  d.width = (uint16_t)std::max(1, (int)src.width >> reduce);
+  d.height = (uint16_t)std::max(1, (int)src.height >> reduce);
+  d.units = 1;  // at most 8 x 8 texels
+  d.reduce = (uint8_t)reduce;
+  return add_level(c, tex_id, level, d, Level{tex_id, level});
 }
 
 jt_status jt_mark(jt_ctx* c, const jt_gbuffer* g, int filter, jt_stream stream) {

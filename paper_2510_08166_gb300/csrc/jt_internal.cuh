@@ -80,7 +80,8 @@ struct DevDesc {
   uint8_t units;               // cache units per MCU: 4 or 1
   uint8_t hset, qset;
   uint8_t compact;             // 1: the compact form (byte-aligned MCUs, stored DCs)
-  uint8_t pad0[3];
+  uint8_t reduce;              // r > 0: tiles at 1/2^r from the lowest N x N frequencies, N = 8 >> r
+  uint8_t pad0[2];
 };
 static_assert(sizeof(DevDesc) == 48, "descriptor layout");
 
