@@ -66,6 +66,7 @@ def lib():
         L.jto_texset_add_reduced.restype = I64
         L.jto_texset_add_reduced.argtypes = [P, I, I, I, I]
         L.jto_idct_pixels_n.argtypes = [P, P, I, I]
+        L.jto_raster_scene.argtypes = [I, I, P, ctypes.c_uint64, I, P, P, P, I, P, I, P, P, P]
         L.jto_texset_decode_mcu.argtypes = [P, I, I, I, P]
         L.jto_mark.restype = I64
         L.jto_mark.argtypes = [P, P, P, P, I64, I, P]
@@ -295,6 +296,30 @@ class TexSet:
 
     def clear_cache(self):
         lib().jto_texset_clear_cache(self._h)
+
+
+def scene_params(d) -> np.ndarray:
+    """The 20 fp32 camera and frame parameters of a scene description, in the order the
+    rasterisers take them."""
+    return np.concatenate([d.cam, d.rot, np.array([d.ax, d.ay, d.tan_x, d.tan_y, d.max_t, d.kx, d.ky, d.shift],
+                                                   np.float32)]).astype(np.float32)
+
+
+def raster_scene(d):
+    """G-buffer (uv, tex_id, mip) of a scene description (fp32, operations in the order the
+    scene's renderer takes them)."""
+    W, H = d.width, d.height
+    uv = np.empty((H, W, 2), np.float32)
+    tex = np.empty((H, W), np.uint16)
+    mip = np.empty((H, W), np.uint8)
+    prm = scene_params(d)
+    tw = np.ascontiguousarray(d.tex_w, np.int32)
+    th = np.ascontiguousarray(d.tex_h, np.int32)
+    tl = np.ascontiguousarray(d.tex_levels, np.int32)
+    q = np.ascontiguousarray(d.quads)
+    lib().jto_raster_scene(W, H, _p(prm), d.cell_seed, tw.size, _p(tw), _p(th), _p(tl), int(d.use_mips),
+                           q.ctypes.data if q.size else None, q.size, _p(uv), _p(tex), _p(mip))
+    return uv, tex, mip
 
 
 def texset_from(ts, compact: bool = False) -> TexSet:

@@ -1151,3 +1151,154 @@ void jto_float_fd(const float* coef, int T, int W, int H, const float* uv, const
 }
 
 }  // extern "C"
+
+// =======================================================================================
+// Scene rasteriser: the G-buffer of the procedural scene (ground plane + projective quads)
+// that the geometry pass of the paper's renderer (Sec. 4, "Geometry Pass") would produce,
+// in fp32 with every operation rounded in the order written (no contraction), so that a
+// GPU renderer doing the same operations takes the same decisions. The scene's definition
+// (double precision) lives in the input generator; this is its fp32 restatement.
+// =======================================================================================
+namespace {
+
+struct RScene {
+  int W, H;
+  const float* p;  // cam[3] rot[9] ax ay tan_x tan_y max_t kx ky shift
+  uint64_t cell_seed;
+  int ntex, use_mips;
+  const int32_t *tw, *th, *tl;
+};
+
+#pragma pack(push, 4)
+struct RQuad {
+  float cx[4], cy[4], ex[4], ey[4], h[9], rep, cs, sn, ou, ov;
+  int32_t tex, x0, y0, x1, y1;
+};
+#pragma pack(pop)
+static_assert(sizeof(RQuad) == 140, "quad record");
+
+// SplitMix64 (Steele, Lea, Flood 2014), as the generator keys its ground cells
+uint64_t splitmix_next(uint64_t& s) {
+  uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+uint64_t cell_hash(uint64_t seed, uint64_t a, uint64_t b) {
+  uint64_t s = seed ^ (a * 0xD1B54A32D192ED03ull) ^ (b * 0x8CB92BA72F3D8DD7ull);
+  splitmix_next(s);
+  return splitmix_next(s);
+}
+
+// Ground hit of the ray through pixel coordinate (px, py): uv = world (x, z) / 2.
+bool r_ground(const RScene& S, float px, float py, float& u, float& v) {
+  const float* c = S.p;
+  const float* R = S.p + 3;
+  const float ax = S.p[12], ay = S.p[13], tx = S.p[14], ty = S.p[15], max_t = S.p[16];
+  const float sx = (px * ax - 1.0f) * tx;
+  const float sy = (1.0f - py * ay) * ty;
+  const float dx = (R[0] * sx + R[1] * sy) - R[2];
+  const float dy = (R[3] * sx + R[4] * sy) - R[5];
+  const float dz = (R[6] * sx + R[7] * sy) - R[8];
+  if (!(dy < -1e-9f)) return false;
+  const float t = -c[1] / dy;
+  if (t > max_t) return false;
+  u = (c[0] + t * dx) * 0.5f;
+  v = (c[2] + t * dz) * 0.5f;
+  return true;
+}
+
+// Level from the squared footprint r2 (texels^2): floor(log2(sqrt(r2)) + 1/2) clamped to
+// [0, L-1], i.e. the number of k >= 1 with r2 >= 2^(2k-1).
+int r_level(float r2, int L) {
+  if (!(r2 > 0.0f)) return 0;
+  int m = 0;
+  while (m + 1 <= L - 1 && r2 >= std::ldexp(1.0f, 2 * (m + 1) - 1)) ++m;
+  return m;
+}
+
+float r_footprint(float u0, float v0, float u1, float v1, int w, int h) {
+  const float du = (u1 - u0) * (float)w, dv = (v1 - v0) * (float)h;
+  return du * du + dv * dv;
+}
+
+void r_quad_uv(const RQuad& q, float x, float y, float& u, float& v) {
+  float s = (q.h[0] * x + q.h[1] * y) + q.h[2];
+  float t = (q.h[3] * x + q.h[4] * y) + q.h[5];
+  const float w = (q.h[6] * x + q.h[7] * y) + q.h[8];
+  s = s / w;
+  t = t / w;
+  u = q.ou + q.rep * (q.cs * s - q.sn * t);
+  v = q.ov + q.rep * (q.sn * s + q.cs * t);
+}
+
+bool r_inside(const RQuad& q, float x, float y) {
+  for (int i = 0; i < 4; ++i)
+    if (q.ex[i] * (y - q.cy[i]) - q.ey[i] * (x - q.cx[i]) < 0.0f) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+// params: cam[3] rot[9] ax ay tan_x tan_y max_t kx ky shift (20 floats); quads: nquads
+// records of 140 bytes; outputs uv [H][W][2], tex [H][W], mip [H][W].
+void jto_raster_scene(int W, int H, const float* params, uint64_t cell_seed, int ntex, const int32_t* tw,
+                      const int32_t* th, const int32_t* tl, int use_mips, const void* quads, int nquads, float* uv,
+                      uint16_t* tex, uint8_t* mip) {
+  RScene S{W, H, params, cell_seed, ntex, use_mips, tw, th, tl};
+  const RQuad* Q = static_cast<const RQuad*>(quads);
+  const float kx = params[17], ky = params[18], shift = params[19];
+  for (int y = 0; y < H; ++y)
+    for (int x = 0; x < W; ++x) {
+      const size_t p = (size_t)y * W + x;
+      const float fx = (float)x + 0.5f, fy = (float)y + 0.5f;
+      int hit = -1;
+      const float qx = fx * kx - shift, qy = fy * ky;
+      for (int n = nquads - 1; n >= 0 && hit < 0; --n)  // the last quad drawn wins
+        if (x >= Q[n].x0 && x <= Q[n].x1 && y >= Q[n].y0 && y <= Q[n].y1 && r_inside(Q[n], qx, qy)) hit = n;
+      float u = 0.f, v = 0.f;
+      int t = 0xFFFF, lvl = 0;
+      if (hit >= 0) {
+        const RQuad& q = Q[hit];
+        t = q.tex;
+        r_quad_uv(q, qx, qy, u, v);
+        if (use_mips) {
+          const float hx = kx * 0.5f, hy = ky * 0.5f;
+          float u0, v0, u1, v1, u2, v2, u3, v3;
+          r_quad_uv(q, qx - hx, qy, u0, v0);
+          r_quad_uv(q, qx + hx, qy, u1, v1);
+          r_quad_uv(q, qx, qy - hy, u2, v2);
+          r_quad_uv(q, qx, qy + hy, u3, v3);
+          const float rx = r_footprint(u0, v0, u1, v1, tw[t], th[t]);
+          const float ry = r_footprint(u2, v2, u3, v3, tw[t], th[t]);
+          lvl = r_level(std::max(rx, ry), tl[t]);
+        }
+      } else if (r_ground(S, fx, fy, u, v)) {
+        const int64_t cx = (int64_t)std::floor(u), cz = (int64_t)std::floor(v);  // 2 m cells
+        const uint64_t hs = cell_hash(cell_seed, (uint64_t)cx, (uint64_t)cz);
+        t = (int)(hs % (uint64_t)ntex);
+        u = u + (float)((hs >> 16) & 0xFFFFu) * (1.0f / 65536.0f);  // per-cell uv offset
+        v = v + (float)((hs >> 32) & 0xFFFFu) * (1.0f / 65536.0f);
+        if (use_mips) {
+          float u0, v0, u1, v1, u2, v2, u3, v3;
+          const bool ok = r_ground(S, (float)x, fy, u0, v0) && r_ground(S, (float)x + 1.0f, fy, u1, v1) &&
+                          r_ground(S, fx, (float)y, u2, v2) && r_ground(S, fx, (float)y + 1.0f, u3, v3);
+          if (!ok) {
+            lvl = tl[t] - 1;
+          } else {
+            const float rx = r_footprint(u0, v0, u1, v1, tw[t], th[t]);
+            const float ry = r_footprint(u2, v2, u3, v3, tw[t], th[t]);
+            lvl = r_level(std::max(rx, ry), tl[t]);
+          }
+        }
+      }
+      uv[2 * p] = u;
+      uv[2 * p + 1] = v;
+      tex[p] = (uint16_t)t;
+      mip[p] = (uint8_t)lvl;
+    }
+}
+
+}  // extern "C"

@@ -71,6 +71,8 @@ def lib():
             ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_uint64,
             ctypes.c_double, ctypes.c_int, P, P, P, ctypes.c_int, P, P, P]
         L.syn_noise_image.argtypes = [ctypes.c_uint64, ctypes.c_int, ctypes.c_int, P]
+        L.syn_scene_quads.restype = ctypes.c_int
+        L.syn_scene_quads.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_int, P, P]
         _lib = L
     return _lib
 
@@ -287,6 +289,79 @@ def gbuffer_scene(seed: int, W: int, H: int, sizes, levels, pose: Pose, nquads: 
                             pose.vfov, nquads, pose.quad_seed, pose.quad_shift, len(sizes), _p(tw), _p(th),
                             _p(tl), int(use_mips), _p(uv), _p(t), _p(m))
     return GBuffer(W, H, uv, t, m)
+
+
+# One quad of the scene as renderers take it (fp32 values rounded from the generator's
+# doubles): corners and edge vectors in the reference frame, the inverse homography, the uv
+# map, the texture and conservative inclusive pixel bounds.
+QUAD_DTYPE = np.dtype([("cx", "<f4", 4), ("cy", "<f4", 4), ("ex", "<f4", 4), ("ey", "<f4", 4), ("h", "<f4", 9),
+                       ("rep", "<f4"), ("cs", "<f4"), ("sn", "<f4"), ("ou", "<f4"), ("ov", "<f4"),
+                       ("tex", "<i4"), ("x0", "<i4"), ("y0", "<i4"), ("x1", "<i4"), ("y1", "<i4")])
+
+
+@dataclass
+class SceneDesc:
+    """The scene of `gbuffer_scene` as fp32 inputs for a renderer: a camera ray through pixel
+    coordinate (px, py) is rot @ ((px * ax - 1) * tan_x, (1 - py * ay) * tan_y, -1); the
+    ground y = 0 is hit at ray parameter t <= max_t; quads live in a reference frame of kx x ky
+    units per pixel, shifted by `shift`; ground cells of 2 m take their texture and uv offset
+    from mix_seed(cell_seed, cell x, cell z)."""
+
+    width: int
+    height: int
+    cam: np.ndarray  # f32 [3]
+    rot: np.ndarray  # f32 [9], row-major
+    ax: float
+    ay: float
+    tan_x: float
+    tan_y: float
+    max_t: float
+    kx: float
+    ky: float
+    shift: float
+    cell_seed: int
+    tex_w: np.ndarray  # i32 [ntex]
+    tex_h: np.ndarray
+    tex_levels: np.ndarray
+    use_mips: bool
+    quads: np.ndarray  # QUAD_DTYPE [nquads]
+
+
+def scene_desc(seed: int, W: int, H: int, sizes, levels, pose: Pose, nquads: int = 200,
+               use_mips: bool = True) -> SceneDesc:
+    """The inputs a renderer needs to draw what `gbuffer_scene` draws with the same arguments."""
+    f32 = np.float32
+    th = np.tan(np.radians(pose.vfov) / 2.0)
+    cp, sp = np.cos(np.radians(pose.pitch)), np.sin(np.radians(pose.pitch))
+    cy, sy = np.cos(np.radians(pose.yaw)), np.sin(np.radians(pose.yaw))
+    rp = np.array([[1, 0, 0], [0, cp, -sp], [0, sp, cp]])
+    ry = np.array([[cy, 0, sy], [0, 1, 0], [-sy, 0, cy]])
+    rot = (ry @ rp).astype(f32).reshape(-1)
+    ntex = len(sizes)
+    raw = np.zeros((max(nquads, 1), 22), np.float64)
+    tex = np.zeros(max(nquads, 1), np.int32)
+    n = lib().syn_scene_quads(W, H, nquads, pose.quad_seed, ntex, _p(raw), _p(tex))
+    Hn, Wn = 1000.0, 1000.0 * W / H
+    kx, ky = Wn / W, Hn / H
+    shift = pose.quad_shift * Wn
+    q = np.zeros(n, QUAD_DTYPE)
+    for k in range(n):
+        cxd, cyd = raw[k, 0:4], raw[k, 4:8]
+        q[k]["cx"], q[k]["cy"] = cxd.astype(f32), cyd.astype(f32)
+        q[k]["ex"] = (np.roll(cxd, -1) - cxd).astype(f32)
+        q[k]["ey"] = (np.roll(cyd, -1) - cyd).astype(f32)
+        q[k]["h"] = raw[k, 8:17].astype(f32)
+        q[k]["rep"], q[k]["cs"], q[k]["sn"], q[k]["ou"], q[k]["ov"] = raw[k, 17:22].astype(f32)
+        q[k]["tex"] = tex[k]
+        xs, ys = (cxd + shift) / kx, cyd / ky
+        q[k]["x0"] = max(0, int(np.floor(xs.min())) - 1)
+        q[k]["x1"] = min(W - 1, int(np.ceil(xs.max())) + 1)
+        q[k]["y0"] = max(0, int(np.floor(ys.min())) - 1)
+        q[k]["y1"] = min(H - 1, int(np.ceil(ys.max())) + 1)
+    return SceneDesc(W, H, np.array(pose.cam, f32), rot, float(f32(2.0 / W)), float(f32(2.0 / H)),
+                     float(f32(th * W / H)), float(f32(th)), 600.0, float(f32(kx)), float(f32(ky)),
+                     float(f32(shift)), mix_seed(seed, 7, 0), np.array([s[0] for s in sizes], np.int32),
+                     np.array([s[1] for s in sizes], np.int32), np.array(levels, np.int32), use_mips, q)
 
 
 def noise_image(seed: int, W: int, H: int) -> np.ndarray:

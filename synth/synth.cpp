@@ -941,6 +941,38 @@ void syn_gbuffer_scene(uint64_t seed, int W, int H, double cam_x, double cam_y, 
   }
 }
 
+// The quads of syn_gbuffer_scene (same seed, same draws, same order) as its reference frame
+// (1000 units high, 1000 * W / H wide) sees them, for renderers of the same scene. Per quad,
+// 22 doubles: corners cx[4], cy[4], the inverse homography Hinv[9] (reference (x, y, 1) ->
+// unit square (s, t, w)), rep, cos phi, sin phi, ou, ov; and its texture in tex[]. Returns the
+// number of quads written (quads that failed 100 draws are skipped, as there).
+int syn_scene_quads(int W, int H, int nquads, uint64_t quad_seed, int ntex, double* out, int* tex) {
+  const double Hn = 1000.0, Wn = 1000.0 * W / H;
+  SplitMix64 rng(quad_seed);
+  int k = 0;
+  for (int n = 0; n < nquads; ++n) {
+    Quad q;
+    int tries = 0;
+    while (!make_quad(rng, (int)std::lround(Wn), (int)Hn, ntex, 0.0, q) && ++tries < 100) {
+    }
+    if (tries >= 100) continue;
+    double* o = out + 22 * k;
+    for (int i = 0; i < 4; ++i) {
+      o[i] = q.cx[i];
+      o[4 + i] = q.cy[i];
+    }
+    for (int i = 0; i < 9; ++i) o[8 + i] = q.Hinv[i];
+    o[17] = q.rep;
+    o[18] = q.cs;
+    o[19] = q.sn;
+    o[20] = q.ou;
+    o[21] = q.ov;
+    tex[k] = q.tex;
+    ++k;
+  }
+  return k;
+}
+
 // Smooth seeded float image [H][W][3] in [0,255] (value noise), used as a target frame.
 void syn_noise_image(uint64_t seed, int W, int H, float* out) {
   std::vector<uint8_t> rgb((size_t)W * H * 3);
