@@ -343,6 +343,29 @@ def run_reduced_mips(jt, ts, dgb, ref_out, dev, flush, stream, steps, tuning):
             "psnr_db_vs_stored_chain": 10.0 * float(np.log10(255.0 ** 2 / max(mse, 1e-12)))}
 
 
+def run_raster(jt, ctx, ts, gb_host, dev, flush, stream, steps):
+    """The geometry-pass stand-in on the GPU: the 4K scene rasterised into a device
+    G-buffer (fp32), alone and followed by the frame over it (graph), and how much of the
+    rastered G-buffer equals the generator's double-precision one that the headline uses."""
+    import torch
+    import synth
+    d = synth.scene_desc(synth.SEED_BASE + 2, gb_host.width, gb_host.height, ts.sizes, ts.nlevels,
+                         synth.config2_pose(), nquads=200)
+    gb = jt.DeviceGBuffer.empty(d.width, d.height, dev)
+    out = torch.empty((d.height, d.width, 4), dtype=torch.uint8, device=dev)
+    ms_raster = timed(lambda: ctx.raster_scene(d, gb), steps, 3, stream, flush)
+    g = ctx.frame_graph([(gb, out)], jt.FILTER_BILINEAR)
+    ms_both = timed(lambda: (ctx.raster_scene(d, gb), ctx.graph_launch(g)), steps, 3, stream, flush)
+    ctx.stats()
+    ctx.graph_destroy(g)
+    tex = gb.tex_id.cpu().numpy().view(np.uint16)
+    mip = gb.mip.cpu().numpy()
+    return {"workload": "3840x2160 ground plane + 200 quads (the headline scene), fp32 raster",
+            "raster_ms": ms_raster, "raster_plus_frame_ms": ms_both,
+            "same_tex_as_generator": float((tex == gb_host.tex_id).mean()),
+            "same_mip_as_generator": float((mip == gb_host.mip).mean())}
+
+
 def mcu_grid(ts, width: int = 2048):
     """G-buffer with one pixel on every MCU of every uploaded level (nearest marks each MCU once)."""
     import synth
@@ -637,6 +660,7 @@ def run_gpu(args, rank, world, local_rank):
             line["clamped_filter"] = run_clamped(ctx, jt, dgb, out, flush, stream, 20)
             line["compact_form"] = run_compact(jt, ts, dgb, ref_out, dev, flush, stream, 20, ctx.tuning())
             line["reduced_mips"] = run_reduced_mips(jt, ts, dgb, ref_out, dev, flush, stream, 20, ctx.tuning())
+            line["raster"] = run_raster(jt, ctx, ts, gb, dev, flush, stream, 20)
             line["batched_views"] = run_views(ctx, ts, jt, dev, flush, stream, 20)
             line["adjoint"] = run_adjoint(jt, dev, flush, stream, 20, peak)
             line["full_decode"] = run_full_decode(jt, dev, flush, stream, 5, peak, ctx.tuning())

@@ -86,7 +86,8 @@ typedef struct {
  * memory, row-major [height][width]:
  *   uv     float32 pairs (u, v); repeat wrap; 16-byte aligned
  *   tex_id uint16, JT_EMPTY_TEXTURE for pixels without texture;  8-byte aligned
- *   mip    uint8 mip level;                                       4-byte aligned */
+ *   mip    uint8 mip level;                                       4-byte aligned
+ * The passes only read it; jt_raster_scene writes it. */
 typedef struct {
   const float* uv;
   const uint16_t* tex_id;
@@ -188,6 +189,58 @@ jt_status jt_upload_texture_compact(jt_ctx* ctx, int tex_id, int level, int widt
  * jt_upload_texture or jt_upload_texture_compact; `level` must not exist yet. Not allowed
  * between jt_mark and jt_decode. */
 jt_status jt_add_reduced_level(jt_ctx* ctx, int tex_id, int src_level, int reduce, int level);
+
+/* ---- geometry-pass stand-in --------------------------------------------------------- */
+
+/* One screen-space quad of a procedural scene (fp32; "reference units" are a frame
+ * 1000 units high, scaled to pixels by kx, ky of the scene). */
+typedef struct {
+  float cx[4], cy[4]; /* corners, counter-clockwise on screen (y down), reference units */
+  float ex[4], ey[4]; /* edge vectors corner i -> corner (i + 1) % 4 */
+  float h[9];         /* row-major map (x, y, 1) -> (s, t, w); (s/w, t/w) in the unit square */
+  float rep, cs, sn, ou, ov; /* uv = (ou, ov) + rep * [[cs, -sn], [sn, cs]] (s, t) */
+  int32_t tex;        /* texture id */
+  int32_t x0, y0, x1, y1; /* inclusive pixel bounds; pixels outside are not tested */
+} jt_scene_quad;
+
+/* A procedural scene: a ground plane y = 0 of 2 m cells seen from a pinhole camera, under
+ * screen-space quads drawn in order (the last one covering a pixel wins). */
+typedef struct {
+  int32_t width, height;   /* G-buffer size */
+  float cam[3];            /* camera position (metres) */
+  float rot[9];            /* row-major: world ray = rot * (sx, sy, -1) */
+  float ax, ay;            /* 2 / width, 2 / height */
+  float tan_x, tan_y;      /* sx = (px * ax - 1) * tan_x, sy = (1 - py * ay) * tan_y at pixel coordinate (px, py) */
+  float max_t;             /* farthest ground hit (ray parameter) */
+  float kx, ky, shift;     /* quad reference units per pixel; quad x = px * kx - shift */
+  uint64_t cell_seed;      /* ground cell (i, j) takes hash = SplitMix64 mix of (cell_seed, i, j) */
+  int32_t ntex;            /* textures: cell texture = hash % ntex */
+  int32_t use_mips;        /* 0: every level 0 */
+  const int32_t* tex_w;    /* host, ntex: level-0 size and level count of each texture */
+  const int32_t* tex_h;
+  const int32_t* tex_levels;
+  const jt_scene_quad* quads; /* host, nquads <= 4096 */
+  int32_t nquads;
+  int32_t reserved;
+} jt_scene;
+
+/* Writes the G-buffer of `scene` into `out` (device, width x height of the scene), standing
+ * in for the geometry pass that precedes the path (Sec. 4). Per pixel at centre
+ * (px, py) = (x + 1/2, y + 1/2), all arithmetic in fp32 with each operation rounded in the
+ * order written:
+ *  - quads: the last quad in drawing order whose bounds hold (x, y) and whose four edge
+ *    tests ex[i] (qy - cy[i]) - ey[i] (qx - cx[i]) are >= 0 at qx = px kx - shift, qy = py ky;
+ *    uv from h and the uv map; the footprint from uv at qx -+ kx/2 and qy -+ ky/2;
+ *  - else the ground: the ray hits y = 0 at t = -cam_y / d_y if d_y < -1e-9 and
+ *    t <= max_t; uv = (x, z) / 2 plus the cell's offset ((hash >> 16) & 0xFFFF,
+ *    (hash >> 32) & 0xFFFF) / 65536, texture hash % ntex; the footprint from the hits at
+ *    (x, py), (x + 1, py), (px, y), (px, y + 1), the last level when one of them misses;
+ *  - else sky: uv (0, 0), texture 0xFFFF, level 0.
+ * The level is floor(log2(rho) + 1/2) clamped to [0, levels - 1], rho^2 = the larger
+ * squared texel-space footprint (uv differences times the level-0 size), decided exactly by
+ * comparing rho^2 with 2^(2k-1). Errors: JT_ERR_INVALID_ARG for a bad size, null pointer,
+ * more than 4096 quads, a quad texture outside [0, ntex) or a level count outside [1, 16]. */
+jt_status jt_raster_scene(jt_ctx* ctx, const jt_scene* scene, const jt_gbuffer* out, jt_stream stream);
 
 /* ---- per-frame path -------------------------------------------------------------------- */
 

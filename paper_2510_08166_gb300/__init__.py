@@ -51,6 +51,19 @@ class jt_gbuffer(ctypes.Structure):
                 ("width", ctypes.c_int32), ("height", ctypes.c_int32)]
 
 
+class jt_scene(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("cam", ctypes.c_float * 3),
+                ("rot", ctypes.c_float * 9), ("ax", ctypes.c_float), ("ay", ctypes.c_float),
+                ("tan_x", ctypes.c_float), ("tan_y", ctypes.c_float), ("max_t", ctypes.c_float),
+                ("kx", ctypes.c_float), ("ky", ctypes.c_float), ("shift", ctypes.c_float),
+                ("cell_seed", ctypes.c_uint64), ("ntex", ctypes.c_int32), ("use_mips", ctypes.c_int32),
+                ("tex_w", ctypes.c_void_p), ("tex_h", ctypes.c_void_p), ("tex_levels", ctypes.c_void_p),
+                ("quads", ctypes.c_void_p), ("nquads", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+assert ctypes.sizeof(jt_scene) == 144
+
+
 class jt_view(ctypes.Structure):
     _fields_ = [("g", jt_gbuffer), ("out_rgba", ctypes.c_void_p)]
 
@@ -82,6 +95,7 @@ _SIGS = {
     "jt_upload_texture": [_P, _I, _I, _I, _I, _I, _P, _U64, _U64, _P, _U64, _P, _P],
     "jt_upload_texture_compact": [_P, _I, _I, _I, _I, _I, _P, _U64, _P, _P, _P, _U64, _P, _P],
     "jt_add_reduced_level": [_P, _I, _I, _I, _I],
+    "jt_raster_scene": [_P, _P, _P, _P],
     "jt_mark": [_P, ctypes.POINTER(jt_gbuffer), _I, _P],
     "jt_decode": [_P, _P],
     "jt_colorize": [_P, ctypes.POINTER(jt_gbuffer), _I, _P, _P],
@@ -191,6 +205,14 @@ class DeviceGBuffer:
         mip = torch.from_numpy(np.ascontiguousarray(gb.mip, np.uint8)).to(device)
         return cls(uv, tex, mip)
 
+    @classmethod
+    def empty(cls, width: int, height: int, device="cuda"):
+        """Uninitialised device G-buffer (e.g. for jt_raster_scene to fill)."""
+        import torch
+        return cls(torch.empty((height, width, 2), dtype=torch.float32, device=device),
+                   torch.empty((height, width), dtype=torch.int16, device=device),
+                   torch.empty((height, width), dtype=torch.uint8, device=device))
+
     def c(self) -> jt_gbuffer:
         return jt_gbuffer(self.uv.data_ptr(), self.tex_id.data_ptr(), self.mip.data_ptr(), self.width, self.height)
 
@@ -268,6 +290,22 @@ class Context:
         """Registers `level` as the 1/2^reduce decode of the stored level `src_level` from its
         lowest frequencies (reduce 1..3; Sec. 7's mip alternative)."""
         self._check(lib().jt_add_reduced_level(self._h, tex_id, src_level, reduce, level))
+
+    def raster_scene(self, d, gb: "DeviceGBuffer", stream=None) -> None:
+        """Fills the device G-buffer `gb` with the scene description `d` (fields of
+        jt_scene; d.quads a structured array laid out as jt_scene_quad)."""
+        tw = np.ascontiguousarray(d.tex_w, np.int32)
+        th = np.ascontiguousarray(d.tex_h, np.int32)
+        tl = np.ascontiguousarray(d.tex_levels, np.int32)
+        q = np.ascontiguousarray(d.quads)
+        if q.size and q.dtype.itemsize != 140:
+            raise JTError(1, "quads must be 140-byte jt_scene_quad records")
+        sc = jt_scene(d.width, d.height, (ctypes.c_float * 3)(*[float(v) for v in d.cam]),
+                      (ctypes.c_float * 9)(*[float(v) for v in d.rot]), d.ax, d.ay, d.tan_x, d.tan_y, d.max_t,
+                      d.kx, d.ky, d.shift, int(d.cell_seed), tw.size, int(d.use_mips), tw.ctypes.data,
+                      th.ctypes.data, tl.ctypes.data, q.ctypes.data if q.size else None, q.size, 0)
+        g = gb.c()
+        self._check(lib().jt_raster_scene(self._h, ctypes.byref(sc), ctypes.byref(g), _stream(stream)))
 
     def upload_set(self, ts, compact: bool = False) -> None:
         for t, l, e in ts.uploads():

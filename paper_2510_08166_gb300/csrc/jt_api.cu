@@ -82,6 +82,10 @@ struct jt_ctx {
   uint32_t float_tile_cap = 0;
   cudaStream_t capture_stream = nullptr;
 
+  // scene rasteriser inputs (jt_raster_scene)
+  uint8_t* raster_buf = nullptr;
+  size_t raster_cap = 0;
+
   // pass timing (jt_profile)
   bool profiling = false;
   cudaEvent_t prof[5] = {};
@@ -627,6 +631,7 @@ jt_status jt_destroy(jt_ctx* c) {
   cache_free(c);
   dev_free(c->state);
   dev_free(c->float_tiles);
+  dev_free(c->raster_buf);
   if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
   for (cudaEvent_t& e : c->prof)
     if (e) cudaEventDestroy(e);
@@ -845,6 +850,78 @@ jt_status jt_add_reduced_level(jt_ctx* c, int tex_id, int src_level, int reduce,
   d.units = 1;  // at most 8 x 8 texels
   d.reduce = (uint8_t)reduce;
   return add_level(c, tex_id, level, d, Level{tex_id, level});
+}
+
+static_assert(sizeof(jt_scene_quad) == sizeof(SceneQuad), "jt_scene_quad layout");
+static_assert(sizeof(jt_scene) == 144, "jt_scene layout");
+
+jt_status jt_raster_scene(jt_ctx* c, const jt_scene* sc, const jt_gbuffer* out, jt_stream stream) {
+  if (!c) return JT_ERR_INVALID_ARG;
+  if (!sc || !out) return fail(c, JT_ERR_INVALID_ARG, "null scene or G-buffer");
+  if (sc->width <= 0 || sc->height <= 0 || out->width != sc->width || out->height != sc->height)
+    return fail(c, JT_ERR_INVALID_ARG, "G-buffer %dx%d does not match the scene's %dx%d", out->width, out->height,
+                sc->width, sc->height);
+  if (!out->uv || !out->tex_id || !out->mip) return fail(c, JT_ERR_INVALID_ARG, "null G-buffer pointer");
+  if (sc->ntex <= 0 || sc->ntex > 0xFFFF || !sc->tex_w || !sc->tex_h || !sc->tex_levels)
+    return fail(c, JT_ERR_INVALID_ARG, "bad texture table");
+  if (sc->nquads < 0 || sc->nquads > kMaxSceneQuads || (sc->nquads > 0 && !sc->quads))
+    return fail(c, JT_ERR_INVALID_ARG, "bad quad list (%d quads, at most %d)", sc->nquads, kMaxSceneQuads);
+  for (int t = 0; t < sc->ntex; ++t)
+    if (sc->tex_levels[t] < 1 || sc->tex_levels[t] > JT_MAX_LEVELS || sc->tex_w[t] <= 0 || sc->tex_h[t] <= 0)
+      return fail(c, JT_ERR_INVALID_ARG, "texture %d: bad size or level count", t);
+  for (int n = 0; n < sc->nquads; ++n)
+    if (sc->quads[n].tex < 0 || sc->quads[n].tex >= sc->ntex)
+      return fail(c, JT_ERR_INVALID_ARG, "quad %d names texture %d", n, sc->quads[n].tex);
+  DeviceGuard dg(c->device);
+  if (!dg.ok) return fail(c, JT_ERR_CUDA, "cannot select device %d", c->device);
+  // device copies of the texture table and the quads: [w][h][levels] x ntex, then quads
+  const size_t tbytes = (size_t)sc->ntex * 4, qoff = (3 * tbytes + 15) & ~(size_t)15;
+  const size_t need = qoff + (size_t)sc->nquads * sizeof(SceneQuad);
+  if (need > c->raster_cap) {
+    dev_free(c->raster_buf);
+    c->raster_buf = nullptr;
+    c->raster_cap = 0;
+    jt_status s = dev_alloc(c, &c->raster_buf, need);
+    if (s != JT_OK) return s;
+    c->raster_cap = need;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  JT_CUDA(c, cudaMemcpyAsync(c->raster_buf, sc->tex_w, tbytes, cudaMemcpyHostToDevice, st));
+  JT_CUDA(c, cudaMemcpyAsync(c->raster_buf + tbytes, sc->tex_h, tbytes, cudaMemcpyHostToDevice, st));
+  JT_CUDA(c, cudaMemcpyAsync(c->raster_buf + 2 * tbytes, sc->tex_levels, tbytes, cudaMemcpyHostToDevice, st));
+  if (sc->nquads)
+    JT_CUDA(c, cudaMemcpyAsync(c->raster_buf + qoff, sc->quads, (size_t)sc->nquads * sizeof(SceneQuad),
+                               cudaMemcpyHostToDevice, st));
+  RasterArgs a{};
+  a.width = sc->width;
+  a.height = sc->height;
+  std::memcpy(a.cam, sc->cam, sizeof a.cam);
+  std::memcpy(a.rot, sc->rot, sizeof a.rot);
+  a.ax = sc->ax;
+  a.ay = sc->ay;
+  a.tan_x = sc->tan_x;
+  a.tan_y = sc->tan_y;
+  a.max_t = sc->max_t;
+  a.kx = sc->kx;
+  a.ky = sc->ky;
+  a.shift = sc->shift;
+  a.cell_seed = sc->cell_seed;
+  a.ntex = sc->ntex;
+  a.use_mips = sc->use_mips;
+  a.nquads = sc->nquads;
+  a.tex_w = reinterpret_cast<const int32_t*>(c->raster_buf);
+  a.tex_h = reinterpret_cast<const int32_t*>(c->raster_buf + tbytes);
+  a.tex_levels = reinterpret_cast<const int32_t*>(c->raster_buf + 2 * tbytes);
+  a.quads = reinterpret_cast<const SceneQuad*>(c->raster_buf + qoff);
+  // the G-buffer record is declared read-only for the passes that consume it; here it is
+  // the output
+  a.uv = reinterpret_cast<float2*>(const_cast<float*>(out->uv));
+  a.tex = const_cast<uint16_t*>(out->tex_id);
+  a.mip = const_cast<uint8_t*>(out->mip);
+  launch_raster(a, st);
+  JT_CUDA(c, cudaGetLastError());
+  c->last_stream = st;
+  return JT_OK;
 }
 
 jt_status jt_mark(jt_ctx* c, const jt_gbuffer* g, int filter, jt_stream stream) {

@@ -197,6 +197,29 @@ struct CacheArgs {
 };
 void launch_cache_update(const CacheArgs& a, int grid, cudaStream_t s);
 
+// Scene rasteriser (geometry-pass stand-in): one quad, laid out as jt_scene_quad.
+struct SceneQuad {
+  float cx[4], cy[4], ex[4], ey[4], h[9], rep, cs, sn, ou, ov;
+  int32_t tex, x0, y0, x1, y1;
+};
+static_assert(sizeof(SceneQuad) == 140, "scene quad layout");
+constexpr int kMaxSceneQuads = 4096;
+struct RasterArgs {
+  int32_t width, height;
+  float cam[3], rot[9];
+  float ax, ay, tan_x, tan_y, max_t, kx, ky, shift;
+  uint64_t cell_seed;
+  int32_t ntex, use_mips, nquads;
+  const int32_t* tex_w;       // device copies
+  const int32_t* tex_h;
+  const int32_t* tex_levels;
+  const SceneQuad* quads;
+  float2* uv;
+  uint16_t* tex;
+  uint8_t* mip;
+};
+void launch_raster(const RasterArgs& a, cudaStream_t s);
+
 struct DecodeArgs {
   const DevDesc* descs;
   uint32_t ndesc;
