@@ -118,7 +118,7 @@ typedef struct {
 /* Launch configuration picked by the autotuner (or set by hand). */
 typedef struct {
   int32_t decode_mcus_per_warp; /* MCUs a decode warp takes at a time: 4, 8, 16 or 32 */
-  int32_t decode_warps;         /* warps per decode CTA: 2, 4, 8 or 16 */
+  int32_t decode_warps;         /* warps per decode CTA: 1..16 (the CTA must fit shared memory) */
   int32_t decode_ctas_per_sm;   /* resident decode CTAs per SM of the persistent grid (>= 1) */
   int32_t pixel_threads;        /* threads per CTA of mark and colourise (64..1024, mult. of 32) */
   int32_t pixel_ctas_per_sm;    /* CTAs per SM of the grid-stride mark and colourise grids */

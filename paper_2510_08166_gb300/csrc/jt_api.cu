@@ -492,12 +492,14 @@ bool valid_filter(int f) {
 }
 
 const int kMcusPerWarp[] = {4, 8, 16, 32};
-const int kDecodeWarps[] = {2, 4, 8, 16};
+// warps per decode CTA the autotuner tries (any 1..16 is valid); the odd counts let the
+// 32-MCU shape fill an SM's shared memory (seven warps of 28 KiB)
+const int kDecodeWarps[] = {2, 3, 4, 5, 6, 7, 8, 12, 16};
 
 bool valid_tuning(const jt_ctx* c, const jt_tuning& t) {
   const int M = t.decode_mcus_per_warp, W = t.decode_warps;
   const bool m_ok = M == 4 || M == 8 || M == 16 || M == 32;
-  const bool w_ok = W == 2 || W == 4 || W == 8 || W == 16;
+  const bool w_ok = W >= 1 && W <= 16;
   return m_ok && w_ok && c->decode_occ[M][W] > 0 && t.decode_ctas_per_sm >= 1 && t.pixel_threads >= 64 &&
          t.pixel_threads <= 1024 && t.pixel_threads % 32 == 0 && t.pixel_ctas_per_sm >= 1 &&
          t.pixel_ctas_per_sm <= 32;
@@ -585,7 +587,7 @@ jt_status jt_create(jt_ctx** out, int device, uint64_t max_cache_blocks) {
       return JT_ERR_UNSUPPORTED;
     }
   for (int M : kMcusPerWarp)
-    for (int W : kDecodeWarps) c->decode_occ[M][W] = decode_max_ctas_per_sm(W, M);
+    for (int W = 1; W <= 16; ++W) c->decode_occ[M][W] = decode_max_ctas_per_sm(W, M);
   c->scan_per_sm = scan_max_ctas_per_sm();
   cudaGetLastError();
   c->tuning.decode_mcus_per_warp = 32;

@@ -130,7 +130,7 @@ def test_autotune_keeps_results(jt, scene):
 
 
 @pytest.mark.parametrize("mcus,warps,per_sm", [(4, 2, 1), (8, 8, 2), (4, 16, 1), (16, 4, 1), (32, 2, 1),
-                                               (16, 2, 2)])
+                                               (16, 2, 2), (32, 7, 1), (16, 13, 1), (8, 3, 2)])
 def test_decode_shapes_bit_exact(jt, scene, mcus, warps, per_sm):
     ts, views = scene
     ctx = jt.Context(0, 1 << 15)
