@@ -4,24 +4,29 @@
 //
 // GB300 design (the paper's one 64-thread block per MCU with a 32-lane code compare,
 // Sec. 5.2, is prior art here):
-//  * persistent grid; each warp fetches M work items (M = 4, 8, 16 or 32 MCUs per warp, one
-//    per lane) at a time from a device counter, so uneven MCU sizes balance dynamically and
-//    the count never goes to the host;
-//  * entropy phase: lane m < M runs MCU m's serial entropy chain over all its data units
-//    from a byte-swapped copy of its words staged in shared memory (a per-warp pool shared
-//    out by a prefix sum). Per symbol: one funnel shift of a two-word window, one 10-bit
-//    LUT read (16-bit entries: code length, value size, run) together with an independent
-//    read of the second-level entry for codes longer than 10 bits, the value cut from the
-//    same window without a branch, and a select to advance the window. The quantised coefficients go in zig-zag order into a
-//    per-warp buffer coef[du][k][m] (int16). Nothing but the LUT and the stream is read on
-//    this serial chain: dequantisation waits for the IDCT phase;
-//  * IDCT phase: each lane transforms its own MCU, column then row, over the warp's
-//    buffer coef[du][k][m] (lane m at column m, so the warp's accesses are consecutive and
-//    conflict-free); all zig-zag positions are compile-time constants. Columns are
-//    dequantised on load with the MCU's quantisation table (read through L1); even/odd
+//  * persistent grid; each warp takes batches of m_eff work items (one per lane), m_eff the
+//    smallest power of two up to M (4, 8, 16 or 32, the buffer width) that covers the list
+//    in one batch per warp: a short list (a frame under motion with a warm block cache)
+//    runs one MCU per warp, spread first over the SMs, and a long one fills the lanes. The
+//    first batch of each warp is fixed by its rank, later ones come from a device counter,
+//    so uneven MCU sizes balance dynamically and the count never goes to the host;
+//  * entropy phase: lane m < m_eff runs MCU m's serial entropy chain over all its data
+//    units from a byte-swapped copy of its words staged in shared memory (a per-warp pool
+//    shared out by a prefix sum). Per symbol: one funnel shift of a two-word window, one
+//    10-bit LUT read (16-bit entries: code length, value size, run) together with an
+//    independent read of the second-level entry for codes longer than 10 bits, the value
+//    cut from the same window without a branch, and a select to advance the window. The
+//    quantised coefficients go in zig-zag order into a per-warp buffer coef[du][k][m]
+//    (int16). Nothing but the LUT and the stream is read on this serial chain:
+//    dequantisation waits for the IDCT phase;
+//  * IDCT phase: the batch's data units are shared out over all 32 lanes, one (data unit,
+//    MCU) pair per lane and round; lanes of one round read consecutive columns of the
+//    buffer (conflict-free), and all zig-zag positions are compile-time constants. Columns
+//    are dequantised on load with the MCU's quantisation table (read through L1); even/odd
 //    butterflies give an exact integer factorisation of the matrix product of the decode
 //    spec; the row pass writes each row's pixels in place over the slots it just read;
-//  * colour phase: each lane converts its MCU and writes its tile with 16-byte stores.
+//  * colour phase: 4:2:0 tiles are shared out as (MCU, group of four texels) pairs, 16-byte
+//    stores; 4:4:4 and reduced-resolution tiles are written by the MCU's own lane.
 //    The buffers per MCU are 768 B of coefficients plus 128 B of staged words, so up to
 //    seven 32-MCU warps fit on an SM.
 //
@@ -346,6 +351,37 @@ __device__ __noinline__ void colour_reduced(const int16_t* col, bool s420, int r
     }
 }
 
+// Full-size IDCT of one data unit in place over the buffer: column pass with dequantisation
+// on load, t = clamp16(floor((sum_v K[y][v] clamp16(q Q) + 2^8) / 2^9)), then the row pass
+// p = clamp(floor((sum_u K[x][u] t[y][u] + 2^18) / 2^19) + 128, 0, 255), whose pixel pairs
+// land in the slots the row just read (see pixel2).
+template <int M>
+__device__ __forceinline__ void idct_full(int16_t* blk, const uint16_t* Qd) {
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    int in[8], out[8];
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+      const int k = zz_pos(v, u);
+      in[v] = sat16(blk[k * M] * (int)__ldg(Qd + k));
+    }
+    idct8(in, out);
+#pragma unroll
+    for (int y = 0; y < 8; ++y) blk[zz_pos(y, u) * M] = (int16_t)sat16((out[y] + 256) >> 9);
+  }
+#pragma unroll
+  for (int y = 0; y < 8; ++y) {
+    int in[8], out[8];
+#pragma unroll
+    for (int x = 0; x < 8; ++x) in[x] = blk[zz_pos(y, x) * M];
+    idct8(in, out);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      blk[zz_pos(y, i) * M] = (int16_t)(clamp255(((out[2 * i] + (1 << 18)) >> 19) + 128) |
+                                        (clamp255(((out[2 * i + 1] + (1 << 18)) >> 19) + 128) << 8));
+  }
+}
+
 template <int M>
 __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
@@ -365,12 +401,24 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
 
   const uint32_t count = min(*(volatile uint32_t*)&a.state->count, a.work_cap);
   bool any_bad = false;
+  // MCUs per batch: the smallest power of two <= M that covers the list in one batch per
+  // warp, so short lists spread one MCU per warp (latency) and long ones fill the lanes
+  const uint32_t total_warps = gridDim.x * (blockDim.x >> 5);
+  const uint32_t per_warp = (count + total_warps - 1) / total_warps;
+  int lmeff = 0;
+  while ((1u << lmeff) < per_warp && (1 << lmeff) < M) ++lmeff;
+  const int meff = 1 << lmeff;
+  // first batch by rank, interleaved over the CTAs (one warp per SM first), then dynamic
+  const uint32_t wrank = (uint32_t)warp * gridDim.x + blockIdx.x;
 
 #pragma unroll 1
-  for (;;) {
-    uint32_t base = 0;
-    if (lane == 0) base = atomicAdd(&a.state->decode_next, (uint32_t)M);
-    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+  for (uint32_t it = 0;; ++it) {
+    uint32_t base = wrank * (uint32_t)meff;
+    if (it != 0) {
+      uint32_t b = 0;
+      if (lane == 0) b = atomicAdd(&a.state->decode_next, (uint32_t)meff);
+      base = __shfl_sync(0xFFFFFFFFu, b, 0) + total_warps * (uint32_t)meff;
+    }
     if (base >= count) break;
 
     {  // clear the coefficient buffer (768 M bytes)
@@ -381,7 +429,7 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
 
     // ---- set-up: lane m < M takes item base + m ----
     const uint32_t item = base + lane;
-    bool act = lane < M && item < count;
+    bool act = lane < meff && item < count;
     const uint32_t gid = act ? __ldg(a.work + item) : 0u;
     const uint32_t di = act ? __ldg(a.desc_of_gid + gid) : 0u;
     int ndu = 0;
@@ -390,7 +438,7 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
     bool cpt = false;
     int red = 0;  // reduced-resolution level: 1/2^red
     const uint32_t* words = nullptr;
-    const uint16_t* Q = a.quant;  // the MCU's quantisation tables (zig-zag), read through L1
+    uint32_t qs = 0;  // the MCU's quantisation table set (zig-zag order, read through L1)
     int16_t pr0 = 0, pr1 = 0, pr2 = 0;
     const HuffTable* hs = sh->t;
     if (act && di < a.ndesc) {
@@ -442,7 +490,7 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
         want = (want + 3) & ~3u;
         if (w0 + want > nwords) want = nwords > w0 ? (nwords - w0) & ~3u : 0u;
         if (d.hset != 0) hs = a.huff[d.hset].t;
-        Q = a.quant + (size_t)d.qset * 128;
+        qs = d.qset;
       }
     } else {
       act = false;
@@ -490,106 +538,88 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
       if (end == 0xFFFFFFFFu || (uint64_t)w0 * 32 + end > (cpt ? endbit : nbits)) any_bad = true;
     }
 
-    // ---- IDCT: each active lane transforms its own MCU (column m of the buffer, so the
-    // warp's accesses are consecutive). Column pass with dequantisation on load:
-    // t = clamp16(floor((sum_v K[y][v] clamp16(q Q) + 2^8) / 2^9)), written back in place.
-    if (act && red != 0) {  // reduced-resolution levels (rare): small transforms
+    // ---- IDCT: the batch's data units are shared out over the warp: pair q = (d, m) (data
+    // unit d of MCU m) goes to lane q % 32 in round q / 32, which runs the column and the
+    // row pass of that data unit. MCU m's set-up values come from lane m.
+    const uint32_t minfo =
+        (act ? 1u : 0u) | (s420 ? 2u : 0u) | ((uint32_t)red << 2) | (store ? 16u : 0u) | (qs << 8);
+    __syncwarp();  // every lane's coefficients are visible to the warp
 #pragma unroll 1
-      for (int d = 0; d < ndu; ++d) {
-        const uint16_t* Qd = Q + (d < ndu - 2 ? 0 : 64);
-        int16_t* blk = col + d * 64 * M;
-        if (red == 1)
+    for (int r0 = 0; r0 < 6 * meff; r0 += 32) {
+      const int q = r0 + lane;
+      const int d = q >> lmeff, m = q & (meff - 1);
+      const uint32_t im = __shfl_sync(0xFFFFFFFFu, minfo, m);
+      if (q < 6 * meff && (im & 1u) && d < ((im & 2u) ? 6 : 3)) {
+        const uint16_t* Qd = a.quant + (size_t)(im >> 8) * 128 + (d < ((im & 2u) ? 4 : 1) ? 0 : 64);
+        int16_t* blk = coef + d * 64 * M + m;
+        const int rm = (int)((im >> 2) & 3u);
+        if (rm == 0)
+          idct_full<M>(blk, Qd);
+        else if (rm == 1)
           idct_reduced<M, 1>(blk, Qd);
-        else if (red == 2)
+        else if (rm == 2)
           idct_reduced<M, 2>(blk, Qd);
         else
           idct_reduced<M, 3>(blk, Qd);
       }
     }
-    if (act && red == 0) {
+    __syncwarp();  // every data unit's pixels are visible to the warp
+
+    // ---- colour conversion + tile stores. Full-size 4:2:0 tiles are shared out as pairs
+    // (MCU m, column group c2 of 4 texels), 16-byte stores; 4:4:4 and reduced tiles are
+    // written by their own lane ----
 #pragma unroll 1
-      for (int d = 0; d < ndu; ++d) {
-        const uint16_t* Qd = Q + (d < ndu - 2 ? 0 : 64);
-        int16_t* blk = col + d * 64 * M;
+    for (int r0 = 0; r0 < 4 * meff; r0 += 32) {
+      const int q = r0 + lane;
+      const int m = (q >> 2) & (meff - 1), c2 = q & 3;
+      const uint32_t im = __shfl_sync(0xFFFFFFFFu, minfo, m);
+      const uint32_t om = __shfl_sync(0xFFFFFFFFu, off, m);
+      if (q < 4 * meff && (im & 0x1Fu) == (1u | 2u | 16u)) {  // active, 4:2:0, full size, stored
+        const int16_t* cm = coef + m;
+        uint8_t* tile = a.cache + (size_t)om * kUnitBytes;
+        // chroma sample (cx, cy) covers texels 2cx..2cx+1, 2cy..2cy+1; texels x = 4 c2 .. 4 c2 + 3
+#pragma unroll 1
+        for (int cy = 0; cy < 8; ++cy) {
+          const uint32_t cb2 = pixel2<M>(cm, 4, cy, c2), cr2 = pixel2<M>(cm, 5, cy, c2);
+          int ro[2], go[2], bo[2];
+          chroma_offsets(cb2 & 255, cr2 & 255, ro[0], go[0], bo[0]);
+          chroma_offsets(cb2 >> 8, cr2 >> 8, ro[1], go[1], bo[1]);
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          int in[8], out[8];
-#pragma unroll
-          for (int v = 0; v < 8; ++v) {
-            const int k = zz_pos(v, u);
-            in[v] = sat16(blk[k * M] * (int)__ldg(Qd + k));
+          for (int dy = 0; dy < 2; ++dy) {
+            const int ty = 2 * cy + dy;
+            const int du = (ty >> 3) * 2 + (c2 >> 1), ry = ty & 7, ci = (c2 & 1) * 2;
+            const uint32_t ya = pixel2<M>(cm, du, ry, ci), yb = pixel2<M>(cm, du, ry, ci + 1);
+            uint4 o;
+            o.x = ycc_pixel(ya & 255, ro[0], go[0], bo[0]);
+            o.y = ycc_pixel(ya >> 8, ro[0], go[0], bo[0]);
+            o.z = ycc_pixel(yb & 255, ro[1], go[1], bo[1]);
+            o.w = ycc_pixel(yb >> 8, ro[1], go[1], bo[1]);
+            *reinterpret_cast<uint4*>(tile + (ty * 16 + 4 * c2) * 4) = o;
           }
-          idct8(in, out);
-#pragma unroll
-          for (int y = 0; y < 8; ++y) blk[zz_pos(y, u) * M] = (int16_t)sat16((out[y] + 256) >> 9);
-        }
-      }
-      // row pass -> pixels p = clamp(floor((sum + 2^18) / 2^19) + 128), stored in place
-#pragma unroll 1
-      for (int d = 0; d < ndu; ++d) {
-        int16_t* blk = col + d * 64 * M;
-#pragma unroll
-        for (int y = 0; y < 8; ++y) {
-          int in[8], out[8];
-#pragma unroll
-          for (int x = 0; x < 8; ++x) in[x] = blk[zz_pos(y, x) * M];
-          idct8(in, out);
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-            blk[zz_pos(y, i) * M] = (int16_t)(clamp255(((out[2 * i] + (1 << 18)) >> 19) + 128) |
-                                              (clamp255(((out[2 * i + 1] + (1 << 18)) >> 19) + 128) << 8));
         }
       }
     }
-
-    // ---- colour conversion + tile stores: each active lane writes its own MCU's tile,
-    // four texels (16 B) per store ----
     if (act && store && red != 0)
       colour_reduced<M>(col, s420, red, reinterpret_cast<uint32_t*>(a.cache + (size_t)off * kUnitBytes));
-    if (act && store && red == 0) {
+    if (act && store && red == 0 && !s420) {  // 4:4:4, 8x8 texels, Y Cb Cr data units 0 1 2
       uint8_t* tile = a.cache + (size_t)off * kUnitBytes;
-      if (s420) {  // 16x16 texels; chroma sample (cx, cy) covers texels 2cx..2cx+1, 2cy..2cy+1
 #pragma unroll 1
-        for (int cy = 0; cy < 8; ++cy) {
+      for (int ty = 0; ty < 8; ++ty) {
 #pragma unroll
-          for (int c2 = 0; c2 < 4; ++c2) {  // texels x = 4 c2 .. 4 c2 + 3
-            const uint32_t cb2 = pixel2<M>(col, 4, cy, c2), cr2 = pixel2<M>(col, 5, cy, c2);
-            int ro[2], go[2], bo[2];
-            chroma_offsets(cb2 & 255, cr2 & 255, ro[0], go[0], bo[0]);
-            chroma_offsets(cb2 >> 8, cr2 >> 8, ro[1], go[1], bo[1]);
+        for (int h = 0; h < 2; ++h) {  // texels x = 4h .. 4h + 3
+          uint32_t o[4];
 #pragma unroll
-            for (int dy = 0; dy < 2; ++dy) {
-              const int ty = 2 * cy + dy;
-              const int du = (ty >> 3) * 2 + (c2 >> 1), ry = ty & 7, ci = (c2 & 1) * 2;
-              const uint32_t ya = pixel2<M>(col, du, ry, ci), yb = pixel2<M>(col, du, ry, ci + 1);
-              uint4 o;
-              o.x = ycc_pixel(ya & 255, ro[0], go[0], bo[0]);
-              o.y = ycc_pixel(ya >> 8, ro[0], go[0], bo[0]);
-              o.z = ycc_pixel(yb & 255, ro[1], go[1], bo[1]);
-              o.w = ycc_pixel(yb >> 8, ro[1], go[1], bo[1]);
-              *reinterpret_cast<uint4*>(tile + (ty * 16 + 4 * c2) * 4) = o;
+          for (int j = 0; j < 2; ++j) {
+            const uint32_t y2 = pixel2<M>(col, 0, ty, 2 * h + j), b2 = pixel2<M>(col, 1, ty, 2 * h + j),
+                           r2 = pixel2<M>(col, 2, ty, 2 * h + j);
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+              int ro, go, bo;
+              chroma_offsets((b2 >> (8 * e)) & 255, (r2 >> (8 * e)) & 255, ro, go, bo);
+              o[2 * j + e] = ycc_pixel((y2 >> (8 * e)) & 255, ro, go, bo);
             }
           }
-        }
-      } else {  // 4:4:4, 8x8 texels, Y Cb Cr data units 0 1 2
-#pragma unroll 1
-        for (int ty = 0; ty < 8; ++ty) {
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {  // texels x = 4h .. 4h + 3
-            uint32_t o[4];
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-              const uint32_t y2 = pixel2<M>(col, 0, ty, 2 * h + j), b2 = pixel2<M>(col, 1, ty, 2 * h + j),
-                             r2 = pixel2<M>(col, 2, ty, 2 * h + j);
-#pragma unroll
-              for (int e = 0; e < 2; ++e) {
-                int ro, go, bo;
-                chroma_offsets((b2 >> (8 * e)) & 255, (r2 >> (8 * e)) & 255, ro, go, bo);
-                o[2 * j + e] = ycc_pixel((y2 >> (8 * e)) & 255, ro, go, bo);
-              }
-            }
-            *reinterpret_cast<uint4*>(tile + (ty * 8 + 4 * h) * 4) = make_uint4(o[0], o[1], o[2], o[3]);
-          }
+          *reinterpret_cast<uint4*>(tile + (ty * 8 + 4 * h) * 4) = make_uint4(o[0], o[1], o[2], o[3]);
         }
       }
     }
