@@ -159,6 +159,17 @@ struct Tables {
   __device__ __forceinline__ uint32_t n2(uint32_t ti) const {
     return SH ? lds_u32(hs_sa + ti * (uint32_t)sizeof(HuffTable) + (uint32_t)offsetof(HuffTable, n2)) : hs[ti].n2;
   }
+  // table ti as a byte address (shared) or byte offset from hs (global), and reads through it
+  __device__ __forceinline__ uint32_t base(uint32_t ti) const {
+    return (SH ? hs_sa : 0u) + ti * (uint32_t)sizeof(HuffTable);
+  }
+  __device__ __forceinline__ uint32_t lut_at(uint32_t b, uint32_t i) const {
+    return SH ? lds_u16(b + i * 2) : (uint32_t)*reinterpret_cast<const uint16_t*>(reinterpret_cast<const char*>(hs) + b + i * 2);
+  }
+  __device__ __forceinline__ uint32_t lut2_at(uint32_t b, uint32_t j) const {
+    const uint32_t o = b + (uint32_t)offsetof(HuffTable, lut2) + j * 2;
+    return SH ? lds_u16(o) : (uint32_t)*reinterpret_cast<const uint16_t*>(reinterpret_cast<const char*>(hs) + o);
+  }
 };
 
 // Symbol entry by the MAXCODE walk (T.81 F.2.2.3), or 0 for an invalid code or a symbol
@@ -202,30 +213,48 @@ __device__ __forceinline__ uint32_t decode_mcu(const Words& W, uint32_t bit0, co
   const uint32_t F0 = T.first16(0), F1 = T.first16(1), F2 = T.first16(2), F3 = T.first16(3);
   const uint32_t N0 = T.n2(0), N1 = T.n2(1), N2 = T.n2(2), N3 = T.n2(3);
   int du = 0, k = cpt ? 1 : 0, comp = 0, pc = p0, q0 = p0, q1 = p1, q2 = p2;
-  // ti: table of the next symbol (0 DC luma, 1 AC luma, 2 DC chroma, 3 AC chroma)
-  uint32_t ti = cpt ? 1u : 0u, boff = 0;
+  // the table of the symbol being decoded (0 DC luma, 1 AC luma, 2 DC chroma, 3 AC chroma),
+  // its address and second-level range. The two possible successors (the next data unit's
+  // first table, or this one's AC table) are prepared before the symbol is read, so the
+  // symbol only has to select between them: a short dependent chain from one LUT read to the
+  // next.
+  uint32_t tcur = cpt ? 1u : 0u;
+  uint32_t bcur = T.base(tcur), fcur = cpt ? F1 : F0, ncur = cpt ? N1 : N0;
+  uint32_t boff = 0;
   if (cpt) coef[0] = (int16_t)pc;
   bool bad = false;
 #pragma unroll 1
   for (int it = 0; it < 64 * 6; ++it) {  // at most 64 symbols per data unit
-    const uint32_t w = __funnelshift_l(lo, hi, pos);
+    // successors, off the chain: the next data unit's component and first table, and the
+    // AC table of this data unit
+    const int cn1 = du + 1 < ndu - 2 ? 0 : (du + 1 == ndu - 2 ? 1 : 2);
+    const uint32_t tA = cn1 ? (cpt ? 3u : 2u) : 0u, tB = tcur | 1u;
+    const uint32_t bA = T.base(tA), bB = T.base(tB);
+    const uint32_t fA = cn1 ? (cpt ? F3 : F2) : F0, fB = (tcur & 2u) ? F3 : F1;
+    const uint32_t nA = cn1 ? (cpt ? N3 : N2) : N0, nB = (tcur & 2u) ? N3 : N1;
+    const int lim = 63 - k;  // the data unit ends when the run reaches it
     const bool dc = k == 0;
+
+    const uint32_t w = __funnelshift_l(lo, hi, pos);
     // both levels read at once (independent loads): the first-level entry when the code is
     // short, else the second-level entry of the 16-bit prefix
-    const uint32_t f16 = (ti & 2) ? ((ti & 1) ? F3 : F2) : ((ti & 1) ? F1 : F0);
-    const uint32_t n2 = (ti & 2) ? ((ti & 1) ? N3 : N2) : ((ti & 1) ? N1 : N0);
-    const uint32_t e1 = T.lut(ti, w >> (32 - kLutBits));
-    const uint32_t j = (w >> 16) - f16;
-    const uint32_t e2 = T.lut2(ti, min(j, (uint32_t)kLut2Size - 1u));
-    uint32_t e = (e1 & 31u) ? e1 : (j < n2 ? e2 : 0u);
+    const uint32_t e1 = T.lut_at(bcur, w >> (32 - kLutBits));
+    const uint32_t j = (w >> 16) - fcur;
+    const uint32_t e2 = T.lut2_at(bcur, min(j, (uint32_t)kLut2Size - 1u));
+    uint32_t e = (e1 & 31u) ? e1 : (j < ncur ? e2 : 0u);
     if (e == 0) {  // no table entry: the MAXCODE walk decodes or rejects it
-      e = walk_symbol(T.hs + ti, w, dc);
+      e = walk_symbol(T.hs + tcur, w, dc);
       if (e == 0) {
         bad = true;
         break;
       }
     }
     const uint32_t l = e & 31u, sz = (e >> 5) & 15u, r = e >> 9;
+    const bool done = (int)r >= lim;  // data unit complete
+    tcur = done ? tA : tB;
+    bcur = done ? bA : bB;
+    fcur = done ? fA : fB;
+    ncur = done ? nA : nB;
     const uint32_t tw = w << l;
     // EXTEND: the s bits after the code; a leading 0 bit makes the value negative
     int v = (int)__funnelshift_l(tw, 0u, sz) + (int)(~((int)tw >> 31) & (int)(1u - (1u << sz)));
@@ -236,32 +265,22 @@ __device__ __forceinline__ uint32_t decode_mcu(const Words& W, uint32_t bit0, co
     pos = step ? pos - 32 : pos;
     widx += step ? 1u : 0u;
     nx = W(widx + 2);
-    if (dc) {
-      pc = (int16_t)(uint16_t)(pc + v);  // DC values wrap modulo 2^16
-      v = pc;
-    }
+    const int dcv = (int16_t)(uint16_t)(pc + v);  // DC values wrap modulo 2^16
+    v = dc ? dcv : v;
+    pc = dc ? dcv : pc;
     const int kst = k + (int)r;
     bad |= sz != 0 && kst > 63;
     coef[(boff + (uint32_t)min(kst, 63)) * M] = (int16_t)v;
-    k += (int)r + 1;
-    const bool done = k >= 64;  // data unit complete
     q0 = done && comp == 0 ? pc : q0;
     q1 = done && comp == 1 ? pc : q1;
     q2 = done && comp == 2 ? pc : q2;
     du += done ? 1 : 0;
-    const int cn = du < ndu - 2 ? 0 : (du == ndu - 2 ? 1 : 2);
-    pc = done ? (cn == 0 ? q0 : (cn == 1 ? q1 : q2)) : pc;
-    comp = cn;
-    // next symbol: the DC table of the next data unit's component, else this one's AC table
-    ti = (cn ? 2u : 0u) + (done ? 0u : 1u);
+    pc = done ? (cn1 == 0 ? q0 : (cn1 == 1 ? q1 : q2)) : pc;
+    comp = done ? cn1 : comp;
     boff += done ? 64u : 0u;
-    k = done ? 0 : k;
+    k = done ? ((cpt && cn1 != 0) ? 1 : 0) : kst + 1;
     if (du == ndu || bad) break;
-    if (cpt && done && cn != 0) {  // compact form: a chroma DC is stored, not coded
-      coef[boff * M] = (int16_t)pc;
-      k = 1;
-      ti |= 1u;
-    }
+    if (cpt && done && cn1 != 0) coef[boff * M] = (int16_t)pc;  // compact form: a stored chroma DC
   }
   p0 = (int16_t)q0;
   p1 = (int16_t)q1;
