@@ -529,7 +529,13 @@ def run_gpu(args, rank, world, local_rank):
     stream = torch.cuda.current_stream()
 
     tuned = None
-    if args.autotune:
+    if args.tuning:
+        M, W, C = (int(v) for v in args.tuning.split(","))
+        t = ctx.tuning()
+        t.update(decode_mcus_per_warp=M, decode_warps=W, decode_ctas_per_sm=C)
+        ctx.set_tuning(**t)
+        tuned = ctx.tuning()
+    elif args.autotune:
         tuned, tuned_ms = ctx.autotune([(dgb, out)], jt.FILTER_BILINEAR, reps=10)
     ctx.profile(True)
     graph = ctx.frame_graph([(dgb, out)], jt.FILTER_BILINEAR)
@@ -680,6 +686,8 @@ def main():
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the default launch shapes instead of autotuning them first")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--tuning", default=None,
+                    help="fixed decode shape M,W,C (MCUs per warp, warps per CTA, CTAs per SM) instead of autotuning")
     ap.add_argument("--quick", action="store_true", help="timed frames only: no e2e, plain or CPU legs")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched-views and adjoint measurements")
     args = ap.parse_args()
