@@ -38,10 +38,10 @@ UNIT = "blocks/s"
 WORKLOAD = "4K frame 3840x2160, 64 JPEG textures 1024-4096^2 Q50-95 4:2:0 full mip chains, bilinear"
 
 
-# DRAM bytes (read + write) per launch of each pass's kernel in the ncu capture summarised in
-# profiles/frame_4k_kernels.md (this workload, the current kernel code). A kernel changed since
-# its capture must be set back to None.
-NCU_TRAFFIC = {"mark": 93.81e6, "compact": 2.75e6, "decode": 2.10e6, "colorize": 132.64e6}
+# DRAM bytes (read + write) per launch of each pass's kernel in an ncu capture of this workload
+# with the current kernel code (the summaries under profiles/). A kernel changed since its
+# capture must be set back to None.
+NCU_TRAFFIC = {"mark": 93.81e6, "compact": 2.75e6, "decode": 2.08e6, "colorize": 132.64e6}
 
 
 def peaks():
