@@ -121,3 +121,76 @@ def test_full_decode_4096_both_samplings(jt):
         np.testing.assert_array_equal(img, oracle.Decoded(e.jfif).rgba)
         g0 += mx * my
     ctx.close()
+
+
+def _sampled_pixels(o, gb, got, n, seed, filt=1):
+    rng = np.random.default_rng(seed)
+    idx = rng.choice(gb.width * gb.height, n, replace=False)
+    ref = o.colorize(gb.uv.reshape(-1, 2)[idx], gb.tex_id.reshape(-1)[idx], gb.mip.reshape(-1)[idx], filt)
+    d = np.abs(got.reshape(-1, 4)[idx].astype(np.int32) - ref.astype(np.int32))
+    return d.max()
+
+
+def test_4k_frame_compact_form(jt):
+    """The 4K frame over the same textures in the paper's compact form: identical pixels to
+    the standard form, work list and sampled tiles equal to the oracle's compact decode."""
+    ts = synth.config2_textures(compact=True)
+    gb = synth.config2_gbuffer(ts)
+    dgb = jt.DeviceGBuffer.from_host(gb)
+    outs = []
+    for compact in (False, True):
+        ctx = jt.Context(0, max_cache_blocks=1 << 18)
+        ctx.upload_set(ts, compact=compact)
+        out = torch.empty((gb.height, gb.width, 4), dtype=torch.uint8, device="cuda")
+        g = ctx.frame_graph([(dgb, out)], jt.FILTER_BILINEAR)
+        ctx.graph_launch(g)
+        ctx.stats()
+        if compact:
+            o = oracle.texset_from(ts, compact=True)
+            work = ctx.work_list()
+            np.testing.assert_array_equal(work, o.compact(o.mark(gb, 1)))
+            gm = GidMap(ts)
+            for gid in np.random.default_rng(4).choice(work, 300, replace=False):
+                t, l, e, mcu = gm(int(gid))
+                np.testing.assert_array_equal(ctx.tile(int(gid), e.sampling), o.decode_mcu(t, l, mcu, 16))
+        ctx.graph_destroy(g)
+        ctx.close()
+        outs.append(out)
+    assert torch.equal(outs[0], outs[1])
+
+
+def test_4k_frame_reduced_mips(jt):
+    """The 4K frame with levels 1, 2, 4, 5, ... decoded from levels 0, 3, 6, ... by reduction:
+    work list equal to the oracle's, sampled tiles bit-exact, sampled pixels within 1 LSB."""
+    ts = synth.config2_textures()
+    gb = synth.config2_gbuffer(ts)
+    ctx = jt.Context(0, max_cache_blocks=1 << 18)
+    o = oracle.TexSet()
+    items = []
+    for t, lv in enumerate(ts.levels):
+        for l, e in enumerate(lv):
+            base = 3 * (l // 3)
+            if l == base:
+                ctx.upload(t, l, e)
+                g0 = o.add(t, l, e)
+            else:
+                ctx.add_reduced_level(t, base, l - base, l)
+                g0 = o.add_reduced(t, base, l - base, l)
+            items.append((g0, t, l, e.sampling, l - base))
+    dgb = jt.DeviceGBuffer.from_host(gb)
+    out = torch.empty((gb.height, gb.width, 4), dtype=torch.uint8, device="cuda")
+    g = ctx.frame_graph([(dgb, out)], jt.FILTER_BILINEAR)
+    ctx.graph_launch(g)
+    ctx.stats()
+    work = ctx.work_list()
+    np.testing.assert_array_equal(work, o.compact(o.mark(gb, 1)))
+    bases = [it[0] for it in items]
+    import bisect
+    for gid in np.random.default_rng(5).choice(work, 300, replace=False):
+        i = bisect.bisect_right(bases, int(gid)) - 1
+        g0, t, l, sampling, r = items[i]
+        mw = (16 if sampling == 420 else 8) >> r
+        np.testing.assert_array_equal(ctx.tile(int(gid), sampling, r), o.decode_mcu(t, l, int(gid) - g0, mw))
+    assert _sampled_pixels(o, gb, out.cpu().numpy(), 50000, 6) <= 1
+    ctx.graph_destroy(g)
+    ctx.close()
