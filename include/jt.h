@@ -117,7 +117,8 @@ typedef struct {
 
 /* Launch configuration picked by the autotuner (or set by hand). */
 typedef struct {
-  int32_t decode_mcus_per_warp; /* MCUs a decode warp takes at a time: 4, 8, 16 or 32 */
+  int32_t decode_mcus_per_warp; /* most MCUs a decode warp takes at a time (its buffer
+                                   width): 4, 8, 16 or 32; a short list runs fewer per warp */
   int32_t decode_warps;         /* warps per decode CTA: 1..16 (the CTA must fit shared memory) */
   int32_t decode_ctas_per_sm;   /* resident decode CTAs per SM of the persistent grid (>= 1) */
   int32_t pixel_threads;        /* threads per CTA of mark and colourise (64..1024, mult. of 32) */

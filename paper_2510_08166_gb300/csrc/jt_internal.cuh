@@ -224,7 +224,7 @@ struct DecodeArgs {
   const DevDesc* descs;
   uint32_t ndesc;
   const uint32_t* desc_of_gid;  // descriptor index of each gid
-  int mcus_per_warp;      // M: 4, 8, 16 or 32
+  int mcus_per_warp;      // M, the buffer width: 4, 8, 16 or 32 (batches may be smaller)
   const HuffSet* huff;    // set 0 is staged in shared memory
   const uint16_t* quant;  // [nq][2][64] zig-zag order
   const uint32_t* work;
