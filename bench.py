@@ -311,6 +311,32 @@ def run_compact(jt, ts, dgb, ref_out, dev, flush, stream, steps, tuning):
                              "compact": int(sum(e.compact.scan.size for e in levels))}}
 
 
+def run_units(jt, ts, dgb, ref_out, dev, flush, stream, steps):
+    """The headline frame with data-unit starts recorded for every level (an index extension,
+    uint16 per data unit after the first: 80 more bits per 4:2:0 MCU), so six lanes decode an
+    MCU's data units at once; autotuned like the headline."""
+    import torch
+    ctx = jt.Context(dev.index, max_cache_blocks=1 << 18)
+    ctx.upload_set(ts, units=True)
+    out = torch.empty_like(ref_out)
+    tuned, _ = ctx.autotune([(dgb, out)], jt.FILTER_BILINEAR, reps=5)
+    ctx.profile(True)
+    g = ctx.frame_graph([(dgb, out)], jt.FILTER_BILINEAR)
+    ms = []
+    passes = {"mark": [], "compact": [], "decode": [], "colorize": []}
+    for _ in range(steps):
+        ms.append(timed(lambda: ctx.graph_launch(g), 1, 0, stream, flush))
+        for k, v in ctx.profile_read().items():
+            passes[k].append(v)
+    needed = int(ctx.stats()["needed_blocks"])
+    same = bool(torch.equal(out, ref_out))
+    ctx.graph_destroy(g)
+    ctx.close()
+    return {"workload": "as the headline frame, data-unit starts for every level", "ms_per_frame": statistics.mean(ms),
+            "passes_ms": {k: float(np.mean(v)) for k, v in passes.items()}, "needed_blocks_per_frame": needed,
+            "same_output": same, "tuning": tuned}
+
+
 def run_reduced_mips(jt, ts, dgb, ref_out, dev, flush, stream, steps, tuning):
     """The headline frame with mip levels 1, 2, 4, 5, ... not stored but decoded from the
     lowest frequencies of the stored levels 0, 3, 6, ... (the mip alternative of Sec. 7):
@@ -433,10 +459,16 @@ def run_motion(jt, ts, dev, flush, stream, reps=100, stereo=False):
     a0 = torch.cuda.Event(enable_timing=True)
     a1 = torch.cuda.Event(enable_timing=True)
     res = {}
-    for mode in ("per_frame", "block_cache"):
+    modes = ("per_frame", "block_cache") if stereo else ("per_frame", "block_cache", "block_cache_units")
+    for mode in modes:
         ctx = jt.Context(dev.index, max_cache_blocks=1 << 18)
-        ctx.upload_set(ts)
-        ctx.set_block_cache(mode == "block_cache")
+        units = mode.endswith("_units")
+        ctx.upload_set(ts, units=units)
+        if units:  # data units in parallel: small buffers, many warps
+            t = ctx.tuning()
+            t.update(decode_mcus_per_warp=4, decode_warps=16, decode_ctas_per_sm=4)
+            ctx.set_tuning(**t)
+        ctx.set_block_cache(mode != "per_frame")
         ctx.profile(True)
         graphs = [ctx.frame_graph(list(zip(dv, outs)), jt.FILTER_BILINEAR) for dv in dviews]
         ms = np.zeros((reps, len(dirs)))
@@ -664,6 +696,7 @@ def run_gpu(args, rank, world, local_rank):
             line["tuning"] = tuned
         if not args.no_extra:
             line["clamped_filter"] = run_clamped(ctx, jt, dgb, out, flush, stream, 20)
+            line["units"] = run_units(jt, ts, dgb, ref_out, dev, flush, stream, 20)
             line["compact_form"] = run_compact(jt, ts, dgb, ref_out, dev, flush, stream, 20, ctx.tuning())
             line["reduced_mips"] = run_reduced_mips(jt, ts, dgb, ref_out, dev, flush, stream, 20, ctx.tuning())
             line["raster"] = run_raster(jt, ctx, ts, gb, dev, flush, stream, 20)

@@ -178,6 +178,16 @@ jt_status jt_upload_texture_compact(jt_ctx* ctx, int tex_id, int level, int widt
                                     const uint16_t* rel_offsets, const uint32_t* dc_records, uint64_t nblocks,
                                     const uint16_t* qt, const jt_huff_spec huff[4]);
 
+/* Index extension (not in the paper): records where each data unit of each MCU of a level
+ * uploaded with jt_upload_texture starts, so that the decoder can run an MCU's data units
+ * on six lanes at once instead of one chain (each unit's DC difference is chained
+ * afterwards). du_offsets: host, count = nblocks * (ndu - 1) uint16, [mcu][unit 1..ndu-1],
+ * bits from the MCU's first bit, non-decreasing within an MCU (ndu = 6 at 4:2:0, 3 at
+ * 4:4:4); copied. Reduced levels made from the level use them too. A unit that runs past
+ * the next unit's start sets JT_DEVERR_CORRUPT. Not for compact or reduced levels; not
+ * allowed between jt_mark and jt_decode. */
+jt_status jt_set_du_offsets(jt_ctx* ctx, int tex_id, int level, const uint16_t* du_offsets, uint64_t count);
+
 /* Registers level `level` of texture `tex_id` as the reduced-resolution decode of the
  * stored level `src_level` (the mip alternative of Sec. 7: a lower resolution from the
  * lowest frequencies only). Each data unit of the source gives N x N texels (N = 8 >> reduce,

@@ -63,6 +63,10 @@ def lib():
         L.jto_texset_add_compact.argtypes = [P, I, I, I, I, I, P, ctypes.c_uint64, P, ctypes.c_uint64, P,
                                              ctypes.c_uint64, P, ctypes.c_uint64, ctypes.c_uint64, P, P, P]
         L.jto_mcu_bits.argtypes = [P, I, I, P, P]
+        L.jto_texset_set_du_offsets.restype = I
+        L.jto_texset_set_du_offsets.argtypes = [P, I, I, P, ctypes.c_uint64]
+        L.jto_du_starts.restype = I
+        L.jto_du_starts.argtypes = [P, I, I, P]
         L.jto_texset_add_reduced.restype = I64
         L.jto_texset_add_reduced.argtypes = [P, I, I, I, I]
         L.jto_idct_pixels_n.argtypes = [P, P, I, I]
@@ -246,6 +250,20 @@ class TexSet:
         self.nmcu[(tex, level)] = n
         self.total = int(g) + n
         return int(g)
+
+    def set_du_offsets(self, tex: int, level: int, offs) -> None:
+        """Data-unit starts [mcu][ndu - 1] (bits from each MCU's first bit) for a standard-form
+        level: its MCUs are then decoded data unit by data unit."""
+        o = np.ascontiguousarray(offs, np.uint16).reshape(-1)
+        if lib().jto_texset_set_du_offsets(self._h, tex, level, _p(o), o.size) != 0:
+            raise ValueError("oracle rejected data-unit offsets")
+
+    def du_starts(self, tex: int, level: int, ndu: int) -> np.ndarray:
+        """The data-unit starts a sequential decode finds, [mcu][ndu - 1]."""
+        out = np.empty((self.nmcu[(tex, level)], ndu - 1), np.int64)
+        if lib().jto_du_starts(self._h, tex, level, _p(out)) != 0:
+            raise ValueError("corrupt stream or compact level")
+        return out
 
     def mcu_bits(self, tex: int, level: int):
         """Per MCU of a standard-form level: (coded bits, bits of its first luma DC and its

@@ -469,6 +469,10 @@ struct Level {
   std::unordered_map<int, std::vector<uint8_t>> tiles;  // decoded MCUs, by MCU id
   std::vector<uint8_t> full;                            // optional full RGBA decode
   int reduce = 0;  // reduced-resolution decode of a stored level: tiles at 1/2^reduce (Sec. 7)
+  int src = -1;    // a reduced level's source level
+  // optional data-unit starts [mcu][ndu - 1] (bits from the MCU's first bit): each data unit
+  // is then decoded from its own start, its DC difference chained afterwards
+  std::vector<uint16_t> du_off;
   int mw() const { return (sampling == 420 ? 16 : 8) >> reduce; }
 };
 
@@ -520,10 +524,38 @@ int decode_mcu_compact(const Level& L, int mcu, uint8_t* tile) {
   return 0;
 }
 
+// Random-access decode of one MCU by data units: data unit d starts at the MCU's bit offset
+// plus its recorded offset and must end at or before the next one's start (the next MCU's
+// for the last). Each DC difference is decoded from a zero predictor, then chained: a
+// component's first data unit adds the index's predictor, each further luma unit the
+// previous luma DC (modulo 2^16, as in the sequential decode).
+int decode_mcu_by_units(const Level& L, int mcu, uint8_t* tile) {
+  const int ndu = L.sampling == 420 ? 6 : 3;
+  const uint64_t start = L.index[mcu].bit_offset;
+  const uint64_t next = mcu + 1 < (int)L.index.size() ? L.index[mcu + 1].bit_offset : L.nbits;
+  int32_t q[6][64];
+  int16_t prev[3] = {L.index[mcu].dc_pred[0], L.index[mcu].dc_pred[1], L.index[mcu].dc_pred[2]};
+  for (int d = 0; d < ndu; ++d) {
+    const uint64_t s0 = start + (d ? L.du_off[(size_t)mcu * (ndu - 1) + d - 1] : 0u);
+    const uint64_t s1 = d + 1 < ndu ? start + L.du_off[(size_t)mcu * (ndu - 1) + d] : next;
+    int comp = d < ndu - 2 ? 0 : (d == ndu - 2 ? 1 : 2);
+    int tb = comp == 0 ? 0 : 1;
+    BitReader br{L.scan.data(), L.scan.size(), s0};
+    int16_t diff = 0;
+    if (!decode_du(br, L.tab[tb * 2], L.tab[tb * 2 + 1], diff, q[d])) return -1;
+    if (br.pos > s1) return -1;
+    prev[comp] = (int16_t)(uint16_t)((int)prev[comp] + (int)diff);
+    q[d][0] = prev[comp];
+  }
+  mcu_to_tile(q, L.sampling, L.qt, tile, L.reduce);
+  return 0;
+}
+
 // Random-access decode of one MCU (Sec. 4.3 with the index of Sec. 5.1): start at the
 // MCU's bit offset with its DC predictors and decode its data units.
 int decode_mcu(const Level& L, int mcu, uint8_t* tile) {
   if (L.compact) return decode_mcu_compact(L, mcu, tile);
+  if (!L.du_off.empty()) return decode_mcu_by_units(L, mcu, tile);
   const int ndu = L.sampling == 420 ? 6 : 3;
   const BlockIndex& bi = L.index[mcu];
   BitReader br{L.scan.data(), L.scan.size(), bi.bit_offset};
@@ -765,9 +797,45 @@ int64_t jto_texset_add_reduced(void* s, int tex, int src_level, int reduce, int 
   L->full.clear();
   L->level = level;
   L->reduce = reduce;
+  L->src = src_level;
   L->w = std::max(1, src->w >> reduce);
   L->h = std::max(1, src->h >> reduce);
   return register_level(S, L);
+}
+
+// Records data-unit starts for a standard-form level (and so for the reduced levels made
+// from it later): [mcu][ndu - 1] offsets in bits from each MCU's first bit. Returns 0 or -1.
+int jto_texset_set_du_offsets(void* s, int tex, int level, const uint16_t* offs, uint64_t n) {
+  TexSet* S = static_cast<TexSet*>(s);
+  Level* L = find_level(*S, tex, level);
+  const int ndu = L && L->sampling == 420 ? 6 : 3;
+  if (!L || L->compact || n != (uint64_t)L->mcus_x * L->mcus_y * (ndu - 1)) return -1;
+  L->du_off.assign(offs, offs + n);
+  for (Level* R : S->order)  // reduced levels share the source's stream
+    if (R->tex == tex && R->reduce != 0 && R->src == level) R->du_off = L->du_off;
+  return 0;
+}
+
+// The data-unit starts a sequential decode of a standard-form level finds:
+// [mcu][ndu - 1] offsets from each MCU's first bit. Returns 0, or -1 on a corrupt stream.
+int jto_du_starts(void* s, int tex, int level, int64_t* out) {
+  TexSet* S = static_cast<TexSet*>(s);
+  Level* L = find_level(*S, tex, level);
+  if (!L || L->compact) return -1;
+  const int ndu = L->sampling == 420 ? 6 : 3;
+  BitReader br{L->scan.data(), L->scan.size(), 0};
+  int16_t pred[3] = {0, 0, 0};
+  int32_t q[64];
+  for (int m = 0; m < L->mcus_x * L->mcus_y; ++m) {
+    const uint64_t start = br.pos;
+    for (int d = 0; d < ndu; ++d) {
+      if (d) out[(size_t)m * (ndu - 1) + d - 1] = (int64_t)(br.pos - start);
+      int comp = d < ndu - 2 ? 0 : (d == ndu - 2 ? 1 : 2);
+      int tb = comp == 0 ? 0 : 1;
+      if (!decode_du(br, L->tab[tb * 2], L->tab[tb * 2 + 1], pred[comp], q)) return -1;
+    }
+  }
+  return 0;
 }
 
 // For a level in the standard form, per MCU: its coded bits and the bits its first luma DC

@@ -96,6 +96,7 @@ _SIGS = {
     "jt_upload_texture_compact": [_P, _I, _I, _I, _I, _I, _P, _U64, _P, _P, _P, _U64, _P, _P],
     "jt_add_reduced_level": [_P, _I, _I, _I, _I],
     "jt_raster_scene": [_P, _P, _P, _P],
+    "jt_set_du_offsets": [_P, _I, _I, _P, _U64],
     "jt_mark": [_P, ctypes.POINTER(jt_gbuffer), _I, _P],
     "jt_decode": [_P, _P],
     "jt_colorize": [_P, ctypes.POINTER(jt_gbuffer), _I, _P, _P],
@@ -307,9 +308,17 @@ class Context:
         g = gb.c()
         self._check(lib().jt_raster_scene(self._h, ctypes.byref(sc), ctypes.byref(g), _stream(stream)))
 
-    def upload_set(self, ts, compact: bool = False) -> None:
+    def set_du_offsets(self, tex_id: int, level: int, offs) -> None:
+        """Data-unit starts [mcu][ndu - 1] of a standard-form level (an index extension that
+        lets six lanes decode one MCU's data units at once)."""
+        o = np.ascontiguousarray(offs, np.uint16).reshape(-1)
+        self._check(lib().jt_set_du_offsets(self._h, tex_id, level, o.ctypes.data, o.size))
+
+    def upload_set(self, ts, compact: bool = False, units: bool = False) -> None:
         for t, l, e in ts.uploads():
             (self.upload_compact if compact else self.upload)(t, l, e)
+            if units and not compact:
+                self.set_du_offsets(t, l, e.du_offsets)
 
     # ---- frame ----
     def mark(self, gb: DeviceGBuffer, filter: int, stream=None):

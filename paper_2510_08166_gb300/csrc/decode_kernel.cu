@@ -288,6 +288,58 @@ __device__ __forceinline__ uint32_t decode_mcu(const Words& W, uint32_t bit0, co
   return (bad || du != ndu) ? 0xFFFFFFFFu : widx * 32 + pos;
 }
 
+// Entropy-decodes one data unit of component comp (0 luma, else chroma) from bit0 into
+// coef[k * M] (zig-zag k; zero on entry); its DC slot receives the DC *difference* (the
+// caller chains it). Same symbol step as decode_mcu, without data-unit transitions: the DC
+// table for the first symbol, then the AC table. Returns the bit position after the unit
+// relative to the first staged word, or 0xFFFFFFFF on an invalid coding.
+template <int M, bool SH>
+__device__ __forceinline__ uint32_t decode_unit(const Words& W, uint32_t bit0, const Tables<SH>& T, int comp,
+                                                int16_t* coef) {
+  uint32_t widx = bit0 >> 5, pos = bit0 & 31;
+  uint32_t hi = W(widx), lo = W(widx + 1), nx = W(widx + 2);
+  const uint32_t tdc = comp ? 2u : 0u, tac = tdc | 1u;
+  const uint32_t bac = T.base(tac), fac = T.first16(tac), nac = T.n2(tac);
+  uint32_t tcur = tdc, bcur = T.base(tdc), fcur = T.first16(tdc), ncur = T.n2(tdc);
+  int k = 0;
+  bool bad = false;
+#pragma unroll 1
+  for (int it = 0; it < 64; ++it) {  // every symbol advances k by at least one
+    const uint32_t w = __funnelshift_l(lo, hi, pos);
+    const uint32_t e1 = T.lut_at(bcur, w >> (32 - kLutBits));
+    const uint32_t j = (w >> 16) - fcur;
+    const uint32_t e2 = T.lut2_at(bcur, min(j, (uint32_t)kLut2Size - 1u));
+    uint32_t e = (e1 & 31u) ? e1 : (j < ncur ? e2 : 0u);
+    if (e == 0) {
+      e = walk_symbol(T.hs + tcur, w, k == 0);
+      if (e == 0) {
+        bad = true;
+        break;
+      }
+    }
+    const uint32_t l = e & 31u, sz = (e >> 5) & 15u, r = e >> 9;
+    const uint32_t tw = w << l;
+    const int v = (int)__funnelshift_l(tw, 0u, sz) + (int)(~((int)tw >> 31) & (int)(1u - (1u << sz)));
+    pos += l + sz;
+    const bool step = pos >= 32;
+    hi = step ? lo : hi;
+    lo = step ? nx : lo;
+    pos = step ? pos - 32 : pos;
+    widx += step ? 1u : 0u;
+    nx = W(widx + 2);
+    const int kst = k + (int)r;
+    bad |= sz != 0 && kst > 63;
+    coef[min(kst, 63) * M] = (int16_t)v;
+    k = kst + 1;
+    tcur = tac;
+    bcur = bac;
+    fcur = fac;
+    ncur = nac;
+    if (k >= 64 || bad) break;
+  }
+  return (bad || k < 64) ? 0xFFFFFFFFu : widx * 32 + pos;
+}
+
 __device__ __forceinline__ uint32_t ycc_pixel(uint32_t Y, int ro, int go, int bo) {
   return clamp255((int)Y + ro) | (clamp255((int)Y + go) << 8) | (clamp255((int)Y + bo) << 16) | 0xFF000000u;
 }
@@ -401,7 +453,10 @@ __device__ __forceinline__ void idct_full(int16_t* blk, const uint16_t* Qd) {
   }
 }
 
-template <int M>
+// UNITS: the variant for contexts with data-unit starts. Each MCU of a batch then takes six
+// lanes, lane 6m + d decoding data unit d of MCU m from its own start (levels without
+// starts are decoded whole by lane 6m); MCUs per batch are at most 4.
+template <int M, bool UNITS>
 __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   HuffSet* sh = reinterpret_cast<HuffSet*>(smem);
@@ -409,7 +464,10 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
   uint8_t* wbase = smem + sizeof(HuffSet) + 64 + (size_t)warp * warp_smem(M);
   int16_t* coef = reinterpret_cast<int16_t*>(wbase);                    // [6][64][M]
   uint32_t* stage = reinterpret_cast<uint32_t*>(wbase + 6 * 64 * M * 2);  // [M * kStageWords]
-  int16_t* col = coef + (lane < M ? lane : 0);                          // this lane's MCU
+  // this lane's MCU slot and data unit (the whole MCU outside the unit variant)
+  const int lm = UNITS ? lane / 6 : lane, ld = UNITS ? lane % 6 : 0;
+  int16_t* col = coef + (lm < M ? lm : 0);  // this lane's MCU column
+  constexpr int kMaxBatch = UNITS ? (M < 4 ? M : 4) : M;
 
   {  // stage Huffman set 0
     const uint4* src = reinterpret_cast<const uint4*>(a.huff);
@@ -425,7 +483,7 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
   const uint32_t total_warps = gridDim.x * (blockDim.x >> 5);
   const uint32_t per_warp = (count + total_warps - 1) / total_warps;
   int lmeff = 0;
-  while ((1u << lmeff) < per_warp && (1 << lmeff) < M) ++lmeff;
+  while ((1u << lmeff) < per_warp && (1 << lmeff) < kMaxBatch) ++lmeff;
   const int meff = 1 << lmeff;
   // first batch by rank, interleaved over the CTAs (one warp per SM first), then dynamic
   const uint32_t wrank = (uint32_t)warp * gridDim.x + blockIdx.x;
@@ -446,9 +504,10 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
       for (int i = lane; i < 48 * M; i += 32) z[i] = make_uint4(0, 0, 0, 0);
     }
 
-    // ---- set-up: lane m < M takes item base + m ----
-    const uint32_t item = base + lane;
-    bool act = lane < meff && item < count;
+    // ---- set-up: lanes of MCU slot m < m_eff take item base + m ----
+    const uint32_t item = base + lm;
+    bool act = lm < meff && item < count;
+    bool unit = false;  // this lane decodes data unit ld only
     const uint32_t gid = act ? __ldg(a.work + item) : 0u;
     const uint32_t di = act ? __ldg(a.desc_of_gid + gid) : 0u;
     int ndu = 0;
@@ -498,7 +557,16 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
           pr1 = (int16_t)__ldg(ix + 3);
           pr2 = (int16_t)__ldg(ix + 4);
           endbit = mcu + 1 < d.nmcu ? ((uint32_t)__ldg(ix + 5) | ((uint32_t)__ldg(ix + 6) << 16)) : d.nbits;
+          if (UNITS && d.du_index != nullptr) {  // this lane's data unit and its bit range
+            unit = true;
+            const uint16_t* du = d.du_index + (size_t)mcu * (ndu - 1);
+            const uint32_t mcu0 = bitpos;
+            if (ld >= ndu) act = false;
+            if (ld > 0 && ld < ndu) bitpos = mcu0 + __ldg(du + ld - 1);
+            if (ld + 1 < ndu) endbit = mcu0 + __ldg(du + ld);
+          }
         }
+        if (UNITS && !unit && ld != 0) act = false;  // decoded whole by the MCU's first lane
         words = d.stream;
         nwords = d.nwords;
         nbits = d.nbits;
@@ -514,6 +582,7 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
     } else {
       act = false;
     }
+    if (!act) want = 0;
     // share the warp's stage pool out by a prefix sum of the lanes' word counts
     uint32_t sbeg = want;
 #pragma unroll
@@ -539,8 +608,22 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
     }
     __syncwarp();
 
-    // ---- entropy phase: each active lane decodes all data units of its MCU ----
-    if (act) {
+    // ---- entropy phase: each active lane decodes all data units of its MCU (or, with
+    // data-unit starts, one data unit) ----
+    if (act && unit) {
+      const Words W{(uint32_t)__cvta_generic_to_shared(stage + sbeg), nst, words + w0,
+                    nwords > w0 ? nwords - w0 : 0u};
+      const int comp = ld < ndu - 2 ? 0 : 1;
+      const uint32_t b0 = bitpos - w0 * 32;
+      int16_t* cu = col + ld * 64 * M;
+      const uint32_t end = hs == sh->t
+                               ? decode_unit<M, true>(W, b0, Tables<true>{hs, (uint32_t)__cvta_generic_to_shared(sh->t)},
+                                                      comp, cu)
+                               : decode_unit<M, false>(W, b0, Tables<false>{hs, 0u}, comp, cu);
+      // a data unit must end at or before the next one's start
+      if (end == 0xFFFFFFFFu || (uint64_t)w0 * 32 + end > endbit) any_bad = true;
+    }
+    if (act && !unit) {
       const Words W{(uint32_t)__cvta_generic_to_shared(stage + sbeg), nst, words + w0,
                     nwords > w0 ? nwords - w0 : 0u};
       const Tables<true> TS{hs, (uint32_t)__cvta_generic_to_shared(sh->t)};
@@ -557,9 +640,26 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
       if (end == 0xFFFFFFFFu || (uint64_t)w0 * 32 + end > (cpt ? endbit : nbits)) any_bad = true;
     }
 
+    if (UNITS) {  // chain the data units' DC differences (first lane of each MCU)
+      __syncwarp();
+      if (act && unit && ld == 0) {
+        int c0 = pr0;
+#pragma unroll 1
+        for (int du = 0; du < ndu - 2; ++du) {  // luma: each unit's difference to the previous
+          int16_t* dcp = col + du * 64 * M;
+          c0 = (int16_t)(uint16_t)(c0 + (int)*dcp);  // modulo 2^16
+          *dcp = (int16_t)c0;
+        }
+        int16_t* cb = col + (ndu - 2) * 64 * M;
+        int16_t* cr = col + (ndu - 1) * 64 * M;
+        *cb = (int16_t)(uint16_t)((int)pr1 + (int)*cb);
+        *cr = (int16_t)(uint16_t)((int)pr2 + (int)*cr);
+      }
+    }
+
     // ---- IDCT: the batch's data units are shared out over the warp: pair q = (d, m) (data
     // unit d of MCU m) goes to lane q % 32 in round q / 32, which runs the column and the
-    // row pass of that data unit. MCU m's set-up values come from lane m.
+    // row pass of that data unit. MCU m's set-up values come from its first lane.
     const uint32_t minfo =
         (act ? 1u : 0u) | (s420 ? 2u : 0u) | ((uint32_t)red << 2) | (store ? 16u : 0u) | (qs << 8);
     __syncwarp();  // every lane's coefficients are visible to the warp
@@ -567,7 +667,7 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
     for (int r0 = 0; r0 < 6 * meff; r0 += 32) {
       const int q = r0 + lane;
       const int d = q >> lmeff, m = q & (meff - 1);
-      const uint32_t im = __shfl_sync(0xFFFFFFFFu, minfo, m);
+      const uint32_t im = __shfl_sync(0xFFFFFFFFu, minfo, UNITS ? 6 * m : m);
       if (q < 6 * meff && (im & 1u) && d < ((im & 2u) ? 6 : 3)) {
         const uint16_t* Qd = a.quant + (size_t)(im >> 8) * 128 + (d < ((im & 2u) ? 4 : 1) ? 0 : 64);
         int16_t* blk = coef + d * 64 * M + m;
@@ -591,8 +691,8 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
     for (int r0 = 0; r0 < 4 * meff; r0 += 32) {
       const int q = r0 + lane;
       const int m = (q >> 2) & (meff - 1), c2 = q & 3;
-      const uint32_t im = __shfl_sync(0xFFFFFFFFu, minfo, m);
-      const uint32_t om = __shfl_sync(0xFFFFFFFFu, off, m);
+      const uint32_t im = __shfl_sync(0xFFFFFFFFu, minfo, UNITS ? 6 * m : m);
+      const uint32_t om = __shfl_sync(0xFFFFFFFFu, off, UNITS ? 6 * m : m);
       if (q < 4 * meff && (im & 0x1Fu) == (1u | 2u | 16u)) {  // active, 4:2:0, full size, stored
         const int16_t* cm = coef + m;
         uint8_t* tile = a.cache + (size_t)om * kUnitBytes;
@@ -618,9 +718,9 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
         }
       }
     }
-    if (act && store && red != 0)
+    if (act && ld == 0 && store && red != 0)
       colour_reduced<M>(col, s420, red, reinterpret_cast<uint32_t*>(a.cache + (size_t)off * kUnitBytes));
-    if (act && store && red == 0 && !s420) {  // 4:4:4, 8x8 texels, Y Cb Cr data units 0 1 2
+    if (act && ld == 0 && store && red == 0 && !s420) {  // 4:4:4, 8x8 texels, Y Cb Cr data units 0 1 2
       uint8_t* tile = a.cache + (size_t)off * kUnitBytes;
 #pragma unroll 1
       for (int ty = 0; ty < 8; ++ty) {
@@ -649,20 +749,27 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
 
 size_t smem_bytes(int warps, int M) { return sizeof(HuffSet) + 64 + (size_t)warps * warp_smem(M); }
 
-template <int M>
-int occupancy(int warps) {
+template <int M, bool UNITS>
+int occupancy_of(int warps) {
   const size_t smem = smem_bytes(warps, M);
   if (smem > 227 * 1024) return 0;
-  if (cudaFuncSetAttribute(k_decode<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+  if (cudaFuncSetAttribute(k_decode<M, UNITS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_decode<M>, warps * 32, smem) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_decode<M, UNITS>, warps * 32, smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   return n;
+}
+
+// resident CTAs per SM that both variants reach (the launch picks one per frame)
+template <int M>
+int occupancy(int warps) {
+  return min(occupancy_of<M, false>(warps), occupancy_of<M, true>(warps));
 }
 
 }  // namespace
@@ -673,11 +780,20 @@ size_t decode_smem_bytes(int warps, int mcus_per_warp) { return smem_bytes(warps
 // which the context calls for every (warps, M) on its device before the first launch.
 void launch_decode(const DecodeArgs& a, int warps, int grid, cudaStream_t s) {
   const size_t smem = smem_bytes(warps, a.mcus_per_warp);
+  if (a.unit_mode) {
+    switch (a.mcus_per_warp) {
+      case 4: k_decode<4, true><<<grid, warps * 32, smem, s>>>(a); break;
+      case 8: k_decode<8, true><<<grid, warps * 32, smem, s>>>(a); break;
+      case 16: k_decode<16, true><<<grid, warps * 32, smem, s>>>(a); break;
+      default: k_decode<32, true><<<grid, warps * 32, smem, s>>>(a); break;
+    }
+    return;
+  }
   switch (a.mcus_per_warp) {
-    case 4: k_decode<4><<<grid, warps * 32, smem, s>>>(a); break;
-    case 8: k_decode<8><<<grid, warps * 32, smem, s>>>(a); break;
-    case 16: k_decode<16><<<grid, warps * 32, smem, s>>>(a); break;
-    default: k_decode<32><<<grid, warps * 32, smem, s>>>(a); break;
+    case 4: k_decode<4, false><<<grid, warps * 32, smem, s>>>(a); break;
+    case 8: k_decode<8, false><<<grid, warps * 32, smem, s>>>(a); break;
+    case 16: k_decode<16, false><<<grid, warps * 32, smem, s>>>(a); break;
+    default: k_decode<32, false><<<grid, warps * 32, smem, s>>>(a); break;
   }
 }
 

@@ -24,6 +24,7 @@ struct Level {
   int tex, level;
   void* stream_mem = nullptr;
   void* index_mem = nullptr;
+  void* du_mem = nullptr;  // data-unit starts (jt_set_du_offsets)
 };
 
 }  // namespace
@@ -68,6 +69,7 @@ struct jt_ctx {
 
   // cross-frame block cache (jt_set_block_cache)
   bool persistent = false;
+  bool unit_mode = false;  // some level has data-unit starts
   uint32_t* resident = nullptr;   // [ngid]
   uint32_t* block_gid = nullptr;  // [nblocks]
   uint32_t* free_list = nullptr;  // [nblocks]
@@ -438,6 +440,7 @@ jt_status enqueue_decode(jt_ctx* c, cudaStream_t s) {
   a.ndesc = (uint32_t)c->descs.size();
   a.desc_of_gid = c->d_desc_of_gid;
   a.mcus_per_warp = c->tuning.decode_mcus_per_warp;
+  a.unit_mode = c->unit_mode ? 1 : 0;
   a.huff = c->d_huff;
   a.quant = c->d_quant;
   a.work = c->work;
@@ -618,6 +621,7 @@ jt_status jt_destroy(jt_ctx* c) {
   for (Level& l : c->levels) {
     if (l.stream_mem) cudaFree(l.stream_mem);
     if (l.index_mem) cudaFree(l.index_mem);
+    if (l.du_mem) cudaFree(l.du_mem);
   }
   dev_free(c->d_descs);
   dev_free(c->d_map);
@@ -826,6 +830,41 @@ jt_status jt_upload_texture_compact(jt_ctx* c, int tex_id, int level, int width,
   std::memcpy(side.data() + 5 * ng, dc_records, ndc * 4);
   return upload_level(c, tex_id, level, width, height, sampling, stream, nbytes, nbytes * 8, side.data(),
                       side.size() * 4, nblocks, true, qt, huff);
+}
+
+jt_status jt_set_du_offsets(jt_ctx* c, int tex_id, int level, const uint16_t* du_offsets, uint64_t count) {
+  if (!c) return JT_ERR_INVALID_ARG;
+  if (c->phase == Phase::Marked) return fail(c, JT_ERR_STATE, "upload between jt_mark and jt_decode");
+  if (tex_id < 0 || tex_id >= 0xFFFF || level < 0 || level >= JT_MAX_LEVELS || !du_offsets)
+    return fail(c, JT_ERR_INVALID_ARG, "bad texture id, level or pointer");
+  const int di = (uint32_t)tex_id < c->map_ntex ? c->map[(size_t)tex_id * JT_MAX_LEVELS + level] : -1;
+  if (di < 0) return fail(c, JT_ERR_INVALID_ARG, "texture %d level %d is not uploaded", tex_id, level);
+  DevDesc& d = c->descs[di];
+  if (d.sampling == kSamplingCoef || d.compact || d.reduce)
+    return fail(c, JT_ERR_INVALID_ARG, "texture %d level %d is not a standard-form stored level", tex_id, level);
+  const int ndu = d.sampling == kSampling420 ? 6 : 3;
+  if (count != (uint64_t)d.nmcu * (ndu - 1))
+    return fail(c, JT_ERR_INVALID_ARG, "%llu offsets, expected %llu", (unsigned long long)count,
+                (unsigned long long)d.nmcu * (ndu - 1));
+  for (uint64_t m = 0; m < d.nmcu; ++m)  // starts must not decrease inside an MCU
+    for (int i = 1; i < ndu - 1; ++i)
+      if (du_offsets[m * (ndu - 1) + i] < du_offsets[m * (ndu - 1) + i - 1])
+        return fail(c, JT_ERR_INVALID_ARG, "MCU %llu: data-unit starts decrease", (unsigned long long)m);
+  DeviceGuard g(c->device);
+  if (!g.ok) return fail(c, JT_ERR_CUDA, "cannot select device %d", c->device);
+  Level& L = c->levels[di];
+  if (L.du_mem) {
+    cudaFree(L.du_mem);
+    L.du_mem = nullptr;
+  }
+  jt_status s;
+  if ((s = dev_alloc(c, reinterpret_cast<uint8_t**>(&L.du_mem), count * 2 + 16)) != JT_OK) return s;
+  JT_CUDA(c, cudaMemcpy(L.du_mem, du_offsets, count * 2, cudaMemcpyHostToDevice));
+  // the level and the reduced levels decoded from it (they share its stream)
+  for (DevDesc& o : c->descs)
+    if (o.stream == d.stream) o.du_index = static_cast<const uint16_t*>(L.du_mem);
+  c->unit_mode = true;
+  return sync_descs(c);
 }
 
 jt_status jt_add_reduced_level(jt_ctx* c, int tex_id, int src_level, int reduce, int level) {

@@ -82,8 +82,10 @@ struct DevDesc {
   uint8_t compact;             // 1: the compact form (byte-aligned MCUs, stored DCs)
   uint8_t reduce;              // r > 0: tiles at 1/2^r from the lowest N x N frequencies, N = 8 >> r
   uint8_t pad0[2];
+  const uint16_t* du_index;    // optional data-unit starts [mcu][ndu - 1] (bits from the MCU start)
+  uint64_t pad1;
 };
-static_assert(sizeof(DevDesc) == 48, "descriptor layout");
+static_assert(sizeof(DevDesc) == 64, "descriptor layout");
 
 struct FrameState {
   uint32_t count;        // needed MCUs after the last compaction
@@ -225,6 +227,7 @@ struct DecodeArgs {
   uint32_t ndesc;
   const uint32_t* desc_of_gid;  // descriptor index of each gid
   int mcus_per_warp;      // M, the buffer width: 4, 8, 16 or 32 (batches may be smaller)
+  int unit_mode;          // some level has data-unit starts: the kernel that decodes them in parallel
   const HuffSet* huff;    // set 0 is staged in shared memory
   const uint16_t* quant;  // [nq][2][64] zig-zag order
   const uint32_t* work;

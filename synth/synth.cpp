@@ -340,6 +340,8 @@ struct Encoded {
   HuffSpec huff[4];
   std::vector<int16_t> qcoef;  // [mcu][du][64] natural order, quantised (optional)
   Compact compact;
+  // start bit of data units 1..ndu-1 of each MCU relative to the MCU's first bit
+  std::vector<uint16_t> du_offsets;  // [mcu][ndu - 1]
   int status = 0;
 };
 
@@ -412,6 +414,7 @@ void entropy_and_container(Encoded& e, const int16_t* qcoef) {
   C.dc.assign(((uint64_t)nmcu * 36 + 31) / 32, 0);
   int pred[3] = {0, 0, 0};
   e.index.resize(nmcu);
+  e.du_offsets.assign((size_t)nmcu * (ndu - 1), 0);
   for (int m = 0; m < nmcu; ++m) {
     BlockIndex bi;
     bi.bit_offset = (uint32_t)bw.nbits;
@@ -428,6 +431,11 @@ void entropy_and_container(Encoded& e, const int16_t* qcoef) {
       int comp = d < ndu - 2 ? 0 : (d == ndu - 2 ? 1 : 2);
       int tab = comp == 0 ? 0 : 1;
       const int16_t* q = qcoef + ((size_t)m * ndu + d) * 64;
+      if (d > 0) {
+        const uint64_t rel = bw.nbits - bi.bit_offset;
+        if (rel > 65535) e.status = -3;
+        e.du_offsets[(size_t)m * (ndu - 1) + d - 1] = (uint16_t)rel;
+      }
       const bool absolute = d == 0 || comp != 0;  // the first luma DC and the chroma DCs
       if (absolute) {
         if (q[0] < -2048 || q[0] > 2047) C.status = -1;
@@ -821,6 +829,13 @@ void syn_jpeg_compact_copy(void* hnd, uint8_t* scan, uint32_t* abs, uint16_t* re
   std::memcpy(abs, C.abs.data(), C.abs.size() * 4);
   std::memcpy(rel, C.rel.data(), C.rel.size() * 2);
   std::memcpy(dc, C.dc.data(), C.dc.size() * 4);
+}
+
+// Data-unit start offsets: [mcu][ndu - 1] uint16 (bits from the MCU's first bit).
+int64_t syn_jpeg_du_count(void* hnd) { return (int64_t) static_cast<Encoded*>(hnd)->du_offsets.size(); }
+void syn_jpeg_du_copy(void* hnd, uint16_t* out) {
+  const Encoded* e = static_cast<Encoded*>(hnd);
+  std::memcpy(out, e->du_offsets.data(), e->du_offsets.size() * 2);
 }
 
 void syn_jpeg_free(void* hnd) { delete static_cast<Encoded*>(hnd); }

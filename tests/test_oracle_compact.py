@@ -107,3 +107,32 @@ def test_bad_table_sizes_are_rejected():
     e.compact.rel = e.compact.rel[:-1]
     with pytest.raises(ValueError):
         o.add_compact(0, 0, e)
+
+
+def test_data_unit_offsets_and_decode_by_units():
+    """Data-unit starts (an index extension: each data unit decodable on its own, its DC
+    difference chained afterwards): the generator's offsets equal the starts a sequential
+    decode finds, and decoding every MCU unit by unit gives the MCU decode's tiles, also for
+    levels reduced from it."""
+    ts = _set(15)
+    std = oracle.texset_from(ts)
+    units = oracle.texset_from(ts)
+    for t, l, e in ts.uploads():
+        ndu = 6 if e.sampling == 420 else 3
+        np.testing.assert_array_equal(std.du_starts(t, l, ndu), e.du_offsets.astype(np.int64))
+        units.set_du_offsets(t, l, e.du_offsets)
+    n = 0
+    for t, l, e in ts.uploads():
+        mw = 16 if e.sampling == 420 else 8
+        for m in range(e.nmcu):
+            np.testing.assert_array_equal(units.decode_mcu(t, l, m, mw), std.decode_mcu(t, l, m, mw))
+            n += 1
+    assert n > 300
+    # a wrong offset is caught: the unit runs past the next unit's start
+    e = ts.levels[0][0]
+    bad = oracle.texset_from(synth.TextureSet([[e]]))
+    offs = e.du_offsets.copy()
+    offs[0, 0] -= 1
+    bad.set_du_offsets(0, 0, offs)
+    with pytest.raises(ValueError):
+        bad.decode_mcu(0, 0, 0, 16)
