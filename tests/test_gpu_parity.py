@@ -155,3 +155,29 @@ def test_levels_smaller_than_an_mcu_and_odd_sizes(jt, filt):
     d = np.abs(out.astype(np.int32) - ref.astype(np.int32))
     assert d.max() <= (0 if filt == 0 else 1)
     ctx.close()
+
+
+def test_degenerate_g_buffers(jt):
+    """A G-buffer with no textured pixel needs no MCU and writes (0, 0, 0, 255) everywhere; a
+    1x1 G-buffer needs exactly its pixel's MCU; a 0-pixel G-buffer is an argument error."""
+    ts, _ = synth.config1()
+    ctx = _ctx(jt)
+    ctx.upload_set(ts)
+    o = oracle.texset_from(ts)
+    H, W = 48, 64
+    empty = synth.GBuffer(W, H, np.zeros((H, W, 2), np.float32), np.full((H, W), 0xFFFF, np.uint16),
+                          np.zeros((H, W), np.uint8))
+    for filt in (0, 1, 2):
+        out = frame(ctx, jt.DeviceGBuffer.from_host(empty), filt, torch).cpu().numpy()
+        st = ctx.stats()
+        assert st["needed_blocks"] == 0 and ctx.work_list().size == 0
+        assert (out == np.array([0, 0, 0, 255], np.uint8)).all()
+    one = synth.GBuffer(1, 1, np.array([[[0.3, 0.7]]], np.float32), np.zeros((1, 1), np.uint16),
+                        np.zeros((1, 1), np.uint8))
+    out = frame(ctx, jt.DeviceGBuffer.from_host(one), 1, torch).cpu().numpy()
+    ctx.stats()
+    np.testing.assert_array_equal(ctx.work_list(), o.compact(o.mark(one, 1)))
+    assert np.abs(out.astype(int) - o.colorize(one.uv, one.tex_id, one.mip, 1).astype(int)).max() <= 1
+    with pytest.raises(jt.JTError):
+        ctx.mark(jt.DeviceGBuffer.empty(0, 0), 0)
+    ctx.close()
