@@ -2,7 +2,6 @@
 declares, the binding declares each with the header's arity, and the multi-replica timing
 logic of the benchmark (max over ranks, whole-job throughput) on two gloo ranks."""
 
-import ctypes
 import os
 import re
 import socket

@@ -6,7 +6,6 @@ any step, and <J dc, g> = <dc, J^T g> holds for the linear part J.
 """
 
 import numpy as np
-import pytest
 
 import oracle
 import synth
