@@ -9,7 +9,10 @@ Pinned parts (see ``tests/test_oracle_*.py``): zig-zag order, canonical Huffman
 tables, entropy decode (round trips and a brute-force prefix decoder), random access
 equals sequential decode, IDCT accuracy and DC constancy, colour conversion, mark /
 compact / colourise against brute force and the full decode, the FP64 float chain's
-gradient against central differences and the adjoint identity.
+gradient against central differences and the adjoint identity, the compact form and the
+data-unit starts against the standard decode and a sequential parse, reduced levels
+against scipy's orthonormal IDCT and box means, the clamped filter against the plain
+filters, and the fp32 rasteriser against the generator's double-precision scene.
 """
 
 from __future__ import annotations

@@ -15,9 +15,15 @@
 //   * random-access decode of one MCU from that index (Sec. 4.3);
 //   * Mark: pixel uv -> texel -> MCU id, MCUs keyed by (texture, mip level) (Sec. 4.2,
 //     Sec. 4.6); Compact: the sorted unique set (Fig. "pipeline" a);
-//   * Resolve / colourise: nearest and bilinear lookups (Sec. 4.4);
+//   * Resolve / colourise: nearest, bilinear, and bilinear clamped to the nearest texel's
+//     MCU (Sec. 4.4);
 //   * a float (FP64) forward of the colourise chain from dequantised DCT coefficients,
-//     its L2 loss, analytic gradient and central finite differences.
+//     its L2 loss, analytic gradient and central finite differences;
+//   * the paper's compact random-access form: byte offsets every ninth MCU with relative
+//     offsets between, 12-bit stored DCs (Sec. 5.1, Sec. 5.3);
+//   * reduced-resolution levels from the lowest N x N frequencies (Sec. 7);
+//   * decode data unit by data unit from recorded unit starts (an index extension);
+//   * the fp32 rasteriser of the procedural G-buffer scene (the geometry-pass stand-in).
 //
 // Readings where the paper is silent (all listed with reasons in the design notes):
 //   * integer IDCT: K[x][u] = round(2^14 * c_u * cos((2x+1) u pi / 16)), c_0 = 1/(2 sqrt 2),
