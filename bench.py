@@ -41,7 +41,11 @@ WORKLOAD = "4K frame 3840x2160, 64 JPEG textures 1024-4096^2 Q50-95 4:2:0 full m
 # DRAM bytes (read + write) per launch of each pass's kernel in an ncu capture of this workload
 # with the current kernel code (the summaries under profiles/). A kernel changed since its
 # capture must be set back to None.
-NCU_TRAFFIC = {"mark": 93.81e6, "compact": 2.75e6, "decode": 2.08e6, "colorize": 132.64e6}
+NCU_TRAFFIC = {"mark": 93.81e6, "compact": None, "decode": 2.08e6, "colorize": None}
+
+
+# kernels one frame launches: mark, the compaction's two passes, decode, colourise
+LAUNCHES_PER_FRAME = 5
 
 
 def peaks():
@@ -216,6 +220,26 @@ def replica_value(units_per_rank: float, world: int, total_ms: float) -> float:
     """Whole-job throughput of `world` replicas that each processed `units_per_rank` units in
     at most `total_ms` (weak scaling)."""
     return world * units_per_rank / (total_ms * 1e-3)
+
+
+class L2Flush:
+    """Evicts every frame's data from L2 (129 MB) between timed steps: a 256 MB write, then a
+    read of another 256 MB buffer, so that the dirty lines the write leaves are written back
+    before the step begins instead of during it (with `read=False`, the write alone)."""
+
+    def __init__(self, dev, nbytes: int = 256 << 20, read: bool = True):
+        import torch
+        self.w = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        self.r = torch.ones(nbytes, dtype=torch.uint8, device=dev) if read else None
+        self.sink = None
+
+    def fill_(self, value: int):
+        self.w.fill_(value)
+        if self.r is not None:
+            self.sink = self.r.amax()
+
+    def zero_(self):
+        self.fill_(0)
 
 
 def timed(fn, steps, warmup, stream, flush=None):
@@ -557,7 +581,7 @@ def run_gpu(args, rank, world, local_rank):
     ctx.upload_set(ts)
     dgb = jt.DeviceGBuffer.from_host(gb, dev)
     out = torch.empty((gb.height, gb.width, 4), dtype=torch.uint8, device=dev)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    flush = L2Flush(dev)
     stream = torch.cuda.current_stream()
 
     tuned = None
@@ -605,10 +629,16 @@ def run_gpu(args, rank, world, local_rank):
     step_ms = [a.elapsed_time(b) for a, b in zip(e0, e1)]
     total_ms = max_over_ranks(float(sum(step_ms)), world, dev)
     ctx.stats()
+    # the same frame after the write alone (L2 full of the flush's dirty lines), for
+    # comparison with earlier measurements taken that way
+    ms_write_flush = timed(lambda: ctx.graph_launch(graph), max(5, min(args.steps, 50)), 3, stream,
+                           L2Flush(dev, read=False))
+    ctx.stats()
 
     if args.quick:  # timed frames only (used under the profiler)
         if rank == 0:
             print(json.dumps({"metric": METRIC, "quick": True, "ms_per_step": total_ms / args.steps,
+                              "ms_per_step_write_only_flush": ms_write_flush,
                               "needed_blocks_per_frame": nblocks, "tuning": ctx.tuning(),
                               "passes_ms": {k: float(np.mean(v)) for k, v in passes.items()}}), flush=True)
         ctx.close()
@@ -675,9 +705,11 @@ def run_gpu(args, rank, world, local_rank):
             "warmup": args.warmup, "ms_per_step": frame_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": {"workload": WORKLOAD, "needed_blocks_per_frame": nblocks, "pixels": npx,
-                       "l2": "flushed between timed steps (256 MB write)", "graph": True,
+                       "l2": "flushed between timed steps (256 MB write, then 256 MB read of another "
+                             "buffer)", "graph": True,
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
             "passes_ms": mean,
+            "ms_per_step_write_only_flush": ms_write_flush,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(dom), "peak_kind": peak_kind,
                          "algorithmic_bytes": alg[dom]},
@@ -687,7 +719,7 @@ def run_gpu(args, rank, world, local_rank):
                     "ms_per_step": statistics.mean(e2e_ms)},
             "plain": {"ms_per_frame": statistics.mean(plain_ms), "same_output": plain_same,
                       "graph_speedup": statistics.mean(plain_ms) / frame_ms},
-            "gpu_launches": 4 * args.steps,
+            "gpu_launches": LAUNCHES_PER_FRAME * args.steps,
             "clocks": clk,
             "wall_s": wall,
             "cpu_baseline": cpu,

@@ -48,7 +48,8 @@ typedef enum {
 #define JT_DEVERR_CORRUPT 0x1u     /* invalid code, category or run, or bits past the stream */
 #define JT_DEVERR_CAPACITY 0x2u    /* needed cache units > capacity; extra tiles not written */
 #define JT_DEVERR_MISSING 0x4u     /* a pixel names a (texture, level) that does not exist */
-#define JT_DEVERR_TIMEOUT 0x8u     /* a bounded wait in the compaction scan gave up */
+#define JT_DEVERR_TIMEOUT 0x8u     /* a bounded wait gave up (reserved: no kernel of this
+                                      library waits on another CTA or launch) */
 
 /* Texture filters. BILINEAR_CLAMP (Sec. 4.4, the linear-interpolation mode timed in
  * Sec. 6.2): the bilinear taps, except that along each axis a tap lying in another MCU than
@@ -343,11 +344,11 @@ jt_status jt_read_cache(jt_ctx* ctx, uint64_t unit_begin, uint64_t n, uint8_t* d
 
 /* ---- compaction without allocation (no counterpart in the paper) ------------------------- */
 
-/* Largest n accepted by jt_compact_static: 256 scan tiles of 65536 flags. */
+/* Largest n accepted by jt_compact_static: 4096 scan tiles of 4096 flags. */
 #define JT_STATIC_COMPACT_MAX_FLAGS 16777216u
 
-/* The compaction step of jt_decode (Sec. 4.2's decode queue; flags -> work list and cache
- * slots), on caller-owned buffers, for callers that must not allocate device memory at the
+/* The compaction step of jt_decode (flags -> work list and cache slots: an exclusive prefix
+ * sum over the flags), on caller-owned buffers, for callers that must not allocate device memory at the
  * call: a frame loop that cannot afford the device-wide synchronisation cudaMalloc/cudaFree
  * may cause, code under memory pressure, or code running inside an allocator. It makes no
  * allocating call (no cudaMalloc/cudaFree, no library allocator); its scratch is a fixed
@@ -362,7 +363,9 @@ jt_status jt_read_cache(jt_ctx* ctx, uint64_t unit_begin, uint64_t n, uint8_t* d
  *  All four stay caller-owned and must stay valid until the stream reaches the work.
  * Returns JT_ERR_CAPACITY for n > JT_STATIC_COMPACT_MAX_FLAGS and JT_ERR_INVALID_ARG for a
  * null or misaligned buffer, both before enqueueing anything; JT_ERR_CUDA if a CUDA call fails
- * (jt_last_error needs a context and does not apply). Enqueues a memset, one kernel and two
+ * (jt_last_error needs a context and does not apply), including when a launch error of the
+ * caller's is already pending on this thread: that error is left pending for the caller to
+ * read and nothing is enqueued. Enqueues a memset, two kernels and two
  * device-to-device copies on `stream`, which stays asynchronous.
  * The first call on each device looks up the scratch address and must happen outside any
  * stream capture. Calls share the scratch: two calls in flight at once on one device race

@@ -1,5 +1,5 @@
-// jt_compact_static: the compaction scan (decoupled look-back over the flag bytes, the same
-// k_scan kernel a context launches) run on caller buffers with its scratch taken from a
+// jt_compact_static: the compaction scan (the same two passes over the flag bytes that a
+// context launches) run on caller buffers with its scratch taken from a
 // file-scope __device__ array instead of device memory the library allocates. The paper
 // has no counterpart.
 //
@@ -11,9 +11,9 @@
 // allocating call of its own, neither CUDA nor any library's: it only clears its scratch,
 // launches and copies three words out, all asynchronously on the caller's stream.
 //
-// Scratch: one fixed array per device image, 256 B of frame state then one 64-bit status
-// word per scan tile (65536 flags), for at most kMaxTiles = 256 tiles (16,777,216 flags,
-// 2.3 KB). Its device address is looked up once per device (cudaGetSymbolAddress, which
+// Scratch: one fixed array per device image, 256 B of frame state then one 64-bit word per
+// scan tile (4096 flags: its count and unit sum), for at most kMaxTiles = 4096 tiles
+// (16,777,216 flags, 33 KB). Its device address is looked up once per device (cudaGetSymbolAddress, which
 // may load the module lazily and so must first run outside any stream capture) and cached.
 // Because
 // the array is shared, two calls in flight at once on one device (two streams, or two
@@ -33,18 +33,17 @@ static_assert(kMaxTiles * (uint32_t)kScanTile == kMaxFlags, "the limit is a whol
 constexpr size_t kStateBytes = 256;  // FrameState, padded so the status words stay 256-B aligned
 static_assert(sizeof(FrameState) <= kStateBytes, "frame state fits its slot");
 
-// [0, 256): FrameState; [256, 256 + 8 * kMaxTiles): tile status words.
+// [0, 256): FrameState; [256, 256 + 8 * kMaxTiles): tile words.
 __device__ __align__(256) uint64_t g_compact_scratch[kStateBytes / 8 + kMaxTiles];
 
 constexpr int kMaxDevices = 64;
 struct DeviceSlot {
   uint8_t* scratch = nullptr;
-  int sm_count = 0;  // resident scan CTAs (SMs x CTAs per SM)
 };
 DeviceSlot g_slots[kMaxDevices];
 std::mutex g_slots_mutex;
 
-// Looks the scratch address and SM count up once per device (with that device current).
+// Looks the scratch address up once per device (with that device current).
 jt_status device_slot(DeviceSlot& out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return JT_ERR_CUDA;
@@ -53,10 +52,6 @@ jt_status device_slot(DeviceSlot& out) {
   if (!s.scratch) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_compact_scratch) != cudaSuccess || !p) return JT_ERR_CUDA;
-    int sms = 0;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
-      return JT_ERR_CUDA;
-    s.sm_count = sms * scan_max_ctas_per_sm();  // resident scan CTAs on the device
     s.scratch = static_cast<uint8_t*>(p);
   }
   out = s;
@@ -75,11 +70,12 @@ extern "C" jt_status jt_compact_static(uint8_t* flags, uint32_t n, uint32_t* slo
   DeviceSlot d;
   if (device_slot(d) != JT_OK) return JT_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  cudaGetLastError();  // a stale launch error must not be blamed on this call
-  const uint32_t ntiles = (n + kScanTile - 1) / kScanTile;
-  // what the scan expects at zero: frame state (counters, error word, finished-CTA count)
-  // and the status word of every tile it will publish
-  if (cudaMemsetAsync(d.scratch, 0, kStateBytes + (size_t)ntiles * 8, s) != cudaSuccess) return JT_ERR_CUDA;
+  // a launch error the caller left pending is theirs to read: report it, leave it pending,
+  // enqueue nothing (so the error checked after the launch below is this call's own)
+  if (cudaPeekAtLastError() != cudaSuccess) return JT_ERR_CUDA;
+  // what the scan expects at zero: the frame state (counters and error word); its first pass
+  // writes every tile word the second pass reads
+  if (cudaMemsetAsync(d.scratch, 0, kStateBytes, s) != cudaSuccess) return JT_ERR_CUDA;
   FrameState* state = reinterpret_cast<FrameState*>(d.scratch);
   ScanArgs a{};
   a.flags = flags;
@@ -91,8 +87,7 @@ extern "C" jt_status jt_compact_static(uint8_t* flags, uint32_t n, uint32_t* slo
   a.tile_status = reinterpret_cast<uint64_t*>(d.scratch + kStateBytes);
   a.state = state;
   a.cap_units = 0xFFFFFFFFu;  // no cache behind these slots: only the work list can overflow
-  const int grid = (int)(ntiles < (uint32_t)d.sm_count ? (ntiles ? ntiles : 1) : (uint32_t)d.sm_count);
-  launch_scan(a, grid, s);
+  launch_scan(a, s);
   if (cudaGetLastError() != cudaSuccess) return JT_ERR_CUDA;
   // totals = {count, units, error bits}: FrameState holds count, units at words 0, 1 and err at word 3
   if (cudaMemcpyAsync(totals, &state->count, 2 * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s) != cudaSuccess ||

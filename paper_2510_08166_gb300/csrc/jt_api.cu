@@ -38,7 +38,6 @@ struct jt_ctx {
   Phase phase = Phase::Idle;
   jt_tuning tuning{};
   int decode_occ[33][17] = {};  // resident decode CTAs per SM by [MCUs per warp][warps per CTA]
-  int scan_per_sm = 1;          // resident compaction CTAs per SM
 
   // textures
   std::vector<DevDesc> descs;
@@ -49,9 +48,11 @@ struct jt_ctx {
   uint64_t desc_of_gid_cap = 0;
   std::vector<int32_t> map;  // [map_ntex * 16]
   std::vector<LevelRec> lrec;  // [map_ntex * 16]
+  std::vector<PixRec> prec;    // [map_ntex * 16 + 1], the last one all zero
   uint32_t map_ntex = 0;
   int32_t* d_map = nullptr;
   LevelRec* d_lrec = nullptr;
+  PixRec* d_prec = nullptr;
   std::vector<HuffSet> hsets;
   HuffSet* d_huff = nullptr;
   std::vector<std::vector<uint16_t>> qsets;  // zig-zag order, 128 entries
@@ -102,7 +103,7 @@ struct jt_graph {
 namespace {
 
 constexpr uint64_t kMaxGids = 1ull << 26;   // count field of the scan status word
-constexpr uint64_t kMaxUnits = 1ull << 28;  // units field of the scan status word
+constexpr uint64_t kMaxUnits = 1ull << 28;  // block cache of at most 64 GiB (2^28 units of 256 B)
 
 jt_status fail(jt_ctx* c, jt_status s, const char* fmt, ...) {
   if (c) {
@@ -261,6 +262,11 @@ jt_status sync_descs(jt_ctx* c) {
   jt_status s = dev_alloc(c, &c->d_map, c->map.size() * 4);
   if (s != JT_OK) return s;
   if ((s = dev_alloc(c, &c->d_lrec, c->lrec.size() * sizeof(LevelRec))) != JT_OK) return s;
+  dev_free(c->d_prec);
+  c->prec.resize(c->lrec.size() + 1, PixRec{});
+  c->prec.back() = PixRec{};  // the record of keys outside the table
+  if ((s = dev_alloc(c, &c->d_prec, c->prec.size() * sizeof(PixRec))) != JT_OK) return s;
+  JT_CUDA(c, cudaMemcpy(c->d_prec, c->prec.data(), c->prec.size() * sizeof(PixRec), cudaMemcpyHostToDevice));
   if (!c->map.empty()) {
     JT_CUDA(c, cudaMemcpy(c->d_map, c->map.data(), c->map.size() * 4, cudaMemcpyHostToDevice));
     JT_CUDA(c, cudaMemcpy(c->d_lrec, c->lrec.data(), c->lrec.size() * sizeof(LevelRec), cudaMemcpyHostToDevice));
@@ -286,7 +292,8 @@ bool pow2(uint32_t v) { return v && !(v & (v - 1)); }
 TexLookup lookup(const jt_ctx* c) {
   bool all_p2 = true;
   for (const DevDesc& d : c->descs) all_p2 &= pow2(d.width) && pow2(d.height);
-  return TexLookup{c->d_descs, c->d_map, reinterpret_cast<const uint4*>(c->d_lrec), c->map_ntex, all_p2 ? 1u : 0u};
+  return TexLookup{c->d_descs, c->d_map, reinterpret_cast<const uint4*>(c->d_lrec),
+                   reinterpret_cast<const uint4*>(c->d_prec), c->map_ntex, all_p2 ? 1u : 0u};
 }
 
 
@@ -369,9 +376,7 @@ jt_status enqueue_scan(jt_ctx* c, uint64_t gid_lo, uint64_t gid_hi, cudaStream_t
   a.tile_status = c->tile_status;
   a.state = c->state;
   a.cap_units = (uint32_t)c->cap_units;
-  const uint32_t ntiles = (a.n + kScanTile - 1) / kScanTile;
-  const int grid = (int)std::max<uint32_t>(1, std::min<uint32_t>(ntiles, (uint32_t)(c->sm_count * c->scan_per_sm)));
-  launch_scan(a, grid, s);
+  launch_scan(a, s);
   return check_launch(c, "scan");
 }
 
@@ -591,7 +596,6 @@ jt_status jt_create(jt_ctx** out, int device, uint64_t max_cache_blocks) {
     }
   for (int M : kMcusPerWarp)
     for (int W = 1; W <= 16; ++W) c->decode_occ[M][W] = decode_max_ctas_per_sm(W, M);
-  c->scan_per_sm = scan_max_ctas_per_sm();
   cudaGetLastError();
   c->tuning.decode_mcus_per_warp = 32;
   c->tuning.decode_warps = 4;
@@ -626,6 +630,7 @@ jt_status jt_destroy(jt_ctx* c) {
   dev_free(c->d_descs);
   dev_free(c->d_map);
   dev_free(c->d_lrec);
+  dev_free(c->d_prec);
   dev_free(c->d_huff);
   dev_free(c->d_quant);
   dev_free(c->flags);
@@ -663,12 +668,29 @@ jt_status jt_profile_read(jt_ctx* c, float ms[4]) {
   return JT_OK;
 }
 
+// The screen passes' record of an uploaded level (see PixRec).
+static PixRec pix_rec(const DevDesc& d) {
+  PixRec p{};
+  p.gid_base = d.gid_base;
+  p.wf = (float)d.width;
+  p.hf = (float)d.height;
+  p.masks = (uint32_t)(d.width - 1) | ((uint32_t)(d.height - 1) << 16);
+  p.mcus_x = d.mcus_x;
+  p.shift = (d.sampling == kSampling444 ? 3u : 4u) - d.reduce;
+  p.info = (uint32_t)d.units | (d.sampling == kSamplingCoef ? kPixCoef : kPixJpeg) |
+           (pow2(d.width) && pow2(d.height) ? kPixPow2 : 0u);
+  p.wh = (uint32_t)d.width | ((uint32_t)d.height << 16);
+  return p;
+}
+
 static jt_status add_level(jt_ctx* c, int tex_id, int level, DevDesc d, Level L) {
   if ((uint32_t)tex_id >= c->map_ntex) {
     uint32_t n = std::max<uint32_t>((uint32_t)tex_id + 1, c->map_ntex * 2);
     n = std::min<uint32_t>(n, 0xFFFF);
     c->map.resize((size_t)n * JT_MAX_LEVELS, -1);
     c->lrec.resize((size_t)n * JT_MAX_LEVELS, LevelRec{0, 0, 0, 0});
+    c->prec.assign((size_t)n * JT_MAX_LEVELS + 1, PixRec{});
+    for (size_t i = 0; i < c->descs.size(); ++i) c->prec[(size_t)c->levels[i].tex * JT_MAX_LEVELS + c->levels[i].level] = pix_rec(c->descs[i]);
     c->map_ntex = n;
   }
   c->map[(size_t)tex_id * JT_MAX_LEVELS + level] = (int32_t)c->descs.size();
@@ -678,6 +700,7 @@ static jt_status add_level(jt_ctx* c, int tex_id, int level, DevDesc d, Level L)
   r.info = level_info(d.mcus_x, (d.sampling == kSampling444 ? 3u : 4u) - d.reduce, d.units, d.sampling, pow2(d.width),
                       pow2(d.height));
   r.pad = 0;
+  c->prec[(size_t)tex_id * JT_MAX_LEVELS + level] = pix_rec(d);
   c->descs.push_back(d);
   c->levels.push_back(L);
   const uint64_t g0 = c->ngid;

@@ -92,7 +92,7 @@ struct FrameState {
   uint32_t units;        // cache units they occupy
   uint32_t decode_next;  // next work item for the persistent decoder
   uint32_t err;          // JT_DEVERR_* bits
-  uint32_t scan_done;    // CTAs finished in the current compaction (reset by the last one)
+  uint32_t spare;        // unused
   uint32_t pad[3];
 };
 
@@ -139,10 +139,30 @@ __host__ __device__ inline uint32_t level_info(uint32_t mcus_x, uint32_t shift, 
          ((hpow2 ? 1u : 0u) << 29);
 }
 
+// The screen passes' record of one (texture, level): 32 bytes (two vector loads that hit
+// L1, since a warp's pixels mostly share a level), every field in the form the texel
+// addressing uses, so no per-pixel branch or decoding is needed. Indexed by
+// tex * JT_MAX_LEVELS + level; record map_ntex * JT_MAX_LEVELS is all zero, the record of
+// every key outside the table (empty pixels, unknown textures or levels).
+struct PixRec {
+  uint32_t gid_base;
+  float wf, hf;     // sides as floats
+  uint32_t masks;   // (w - 1) | (h - 1) << 16: floor-mod masks of power-of-two sides
+  uint32_t mcus_x;
+  uint32_t shift;   // log2 of the MCU side in texels
+  uint32_t info;    // units | kPixJpeg | kPixCoef | kPixPow2
+  uint32_t wh;      // w | h << 16
+};
+static_assert(sizeof(PixRec) == 32, "screen-pass record layout");
+constexpr uint32_t kPixJpeg = 1u << 16;  // an uploaded JPEG level (colourise, mark)
+constexpr uint32_t kPixCoef = 1u << 17;  // a coefficient level (mark of the float chain)
+constexpr uint32_t kPixPow2 = 1u << 18;  // both sides are powers of two
+
 struct TexLookup {
   const DevDesc* descs;
   const int32_t* desc_map;
   const uint4* levels;  // LevelRec per (tex, level), same indexing as desc_map
+  const uint4* pix;     // PixRec per (tex, level) as two uint4, then the all-zero record
   uint32_t map_ntex;
   uint32_t all_p2;      // every level has power-of-two sides
 };
@@ -166,15 +186,14 @@ struct ScanArgs {
   uint32_t* slot;        // indexed by gid
   uint32_t* work;
   uint32_t work_cap;
-  uint64_t* tile_status; // one word per tile
+  uint64_t* tile_status; // one word per tile: its (count << 32 | units)
   FrameState* state;
   uint32_t cap_units;
 };
-constexpr int kScanThreads = 1024;
-constexpr int kScanPerThread = 64;  // 4 x 16-byte loads
-constexpr int kScanTile = kScanThreads * kScanPerThread;
-void launch_scan(const ScanArgs& a, int grid, cudaStream_t s);
-int scan_max_ctas_per_sm();  // resident CTAs per SM (the grid must not exceed SMs x this)
+constexpr int kScanThreads = 256;
+constexpr int kScanPerThread = 16;  // one 16-byte load
+constexpr int kScanTile = kScanThreads * kScanPerThread;  // 4096 flags
+void launch_scan(const ScanArgs& a, cudaStream_t s);  // two launches; tile_status: one word per tile
 
 // Cross-frame block cache (Sec. 4.1, Sec. 4.5): resident[gid] = block or ~0, block_gid[block]
 // = gid or ~0, free_list[0 .. free_count) = free blocks (a stack). A block is 4 cache units.

@@ -2,22 +2,32 @@
 // colourise (Sec. 4.4), for one or several views in one launch.
 //
 // Both stream the G-buffer (11 B/px read; colourise also writes 4 B/px and gathers texels
-// from the block cache). A persistent grid walks the views in 128 x 32 pixel tiles, one
-// warp per 128-pixel row segment and one quad of 4 pixels per lane (32 B + 8 B + 4 B vector
-// loads, one 16 B store). Pixels of a tile share MCUs, so Mark keeps a 1024-entry table of
-// the gids its CTA already flagged in shared memory and stores each flag about once per CTA
-// instead of once per pixel (the byte stores of every SM to the same flag lines otherwise
-// dominate the pass). A pixel's (texture, level) record is one 16-byte load, kept in
-// registers while consecutive pixels share it; levels whose sides are powers of two (all
-// mip chains of power-of-two textures) wrap with a mask, MCU coordinates are shifts.
+// from the block cache). A persistent grid walks the views in 128 x 32 pixel tiles, one warp
+// per 128-pixel row.
+//
+// Mark: one quad of 4 pixels per lane (32 B + 8 B + 4 B vector loads). Pixels of a tile
+// share MCUs, so Mark keeps a 1024-entry table of the gids its CTA already flagged in shared
+// memory and stores each flag about once per CTA instead of once per pixel (the byte stores
+// of every SM to the same flag lines otherwise dominate the pass). A pixel's (texture,
+// level) record is one 16-byte load, kept in registers while consecutive pixels share it;
+// levels whose sides are powers of two (all mip chains of power-of-two textures) wrap with a
+// mask, MCU coordinates are shifts.
+//
+// Colourise: a lane owns pixels 32 apart (lane + 32 k), so the 32 addresses of one texel
+// gather instruction are 32 consecutive pixels' taps, which fall in two or three tiles (half
+// the L1 wavefronts of quads per lane); the next step's G-buffer is loaded before the current
+// one is shaded; a pixel's level comes from a 32-byte record that needs no decoding; the
+// bilinear blend runs in fp16 pairs within a proven 1-LSB bound.
 //
 // Texel addressing (fixed in fp32 with explicit rounding so it is the same on every
 // device): nearest x = floor(u * w) floor-mod w; bilinear xs = u * w - 1/2, x0 = floor(xs),
 // fx = xs - x0, taps x0 and x0 + 1 (floor-mod w); the MCU of texel (x, y) is
 // x / mw + (y / mw) * mcus_x with mw = 16 (4:2:0) or 8 (4:4:4), and its key is the level's
 // gid_base + MCU (Sec. 4.6).
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <cstring>
 #include <type_traits>
 
 #include "jt_internal.cuh"
@@ -202,11 +212,167 @@ __device__ __forceinline__ void for_each_quad(const ViewSet& vs, F&& f) {
 }
 
 // ---------------------------------------------------------------------------------------
+// Texel addressing of Colourise
+// ---------------------------------------------------------------------------------------
+// floor(x) for |x| < 2^22 by one round-down add: t = x + 1.5 * 2^23 rounded down is exactly
+// floor(x) + 1.5 * 2^23 (the sum lies in [2^23, 2^24), where floats are the integers), so
+// t - 1.5 * 2^23 is floor(x) as a float, and the bit pattern of t is that of 1.5 * 2^23
+// (a multiple of 2^22) plus floor(x): masked by w - 1 (w a power of two below 2^22) it is
+// floor(x) floor-mod w. Pixels outside that range, and levels whose sides are not powers of
+// two, take the general path (conversion instructions, which saturate, and a division).
+constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
+
+// A pixel's level, from its PixRec (two vector loads; all fields zero for keys outside the
+// table, so every address derived from them stays in range).
+struct PixL {
+  uint32_t gid_base;
+  float wf, hf;
+  uint32_t masks;  // (w - 1) | (h - 1) << 16
+  uint32_t mcus_x;
+  uint32_t shift;
+  uint32_t info;   // units | kPixJpeg | kPixCoef | kPixPow2
+  uint32_t wh;     // w | h << 16
+};
+
+__device__ __forceinline__ PixL pix_level(const TexLookup& tl, uint32_t tm) {
+  const uint32_t tex = tm & 0xFFFFu, mip = tm >> 16;
+  const uint32_t key =
+      (tex < tl.map_ntex && mip < JT_MAX_LEVELS) ? tex * JT_MAX_LEVELS + mip : tl.map_ntex * JT_MAX_LEVELS;
+  const uint4 r0 = __ldg(tl.pix + 2 * key), r1 = __ldg(tl.pix + 2 * key + 1);
+  PixL P;
+  P.gid_base = r0.x;
+  P.wf = __uint_as_float(r0.y);
+  P.hf = __uint_as_float(r0.z);
+  P.masks = r0.w;
+  P.mcus_x = r1.x;
+  P.shift = r1.y;
+  P.info = r1.z;
+  P.wh = r1.w;
+  return P;
+}
+
+// Bilinear taps on the fast path: a power-of-two level and |u w|, |v h| < 2^22 (returns
+// false otherwise; every tap is then still inside the level, so loads made from it stay in
+// range, but the caller must redo the pixel on the general path). Columns xa, xb = xa + 1,
+// rows ya, yb = ya + 1 (repeat wrap), fractions fx, fy.
+__device__ __forceinline__ bool taps_fast(const PixL& P, float u, float v, int& xa, int& xb, int& ya, int& yb,
+                                          float& fx, float& fy) {
+  const float xs = __fsub_rn(__fmul_rn(u, P.wf), 0.5f), ys = __fsub_rn(__fmul_rn(v, P.hf), 0.5f);
+  const float tx = __fadd_rd(xs, kMagic), ty = __fadd_rd(ys, kMagic);
+  fx = __fsub_rn(xs, __fsub_rn(tx, kMagic));
+  fy = __fsub_rn(ys, __fsub_rn(ty, kMagic));
+  const int wm = (int)(P.masks & 0xFFFFu), hm = (int)(P.masks >> 16);
+  xa = __float_as_int(tx) & wm;
+  ya = __float_as_int(ty) & hm;
+  xb = (xa + 1) & wm;
+  yb = (ya + 1) & hm;
+  return (P.info & kPixPow2) && fabsf(xs) < 4194304.0f && fabsf(ys) < 4194304.0f;
+}
+
+// Nearest texel on the fast path (same conditions as taps_fast).
+__device__ __forceinline__ bool nearest_fast(const PixL& P, float u, float v, int& x, int& y) {
+  const float xn = __fmul_rn(u, P.wf), yn = __fmul_rn(v, P.hf);
+  x = __float_as_int(__fadd_rd(xn, kMagic)) & (int)(P.masks & 0xFFFFu);
+  y = __float_as_int(__fadd_rd(yn, kMagic)) & (int)(P.masks >> 16);
+  return (P.info & kPixPow2) && fabsf(xn) < 4194304.0f && fabsf(yn) < 4194304.0f;
+}
+
+// The same taps for any level and coordinate (conversion instructions, floor-mod by
+// division): the general path.
+__device__ __forceinline__ void taps_any(const PixL& P, float u, float v, int& xa, int& xb, int& ya, int& yb,
+                                         float& fx, float& fy) {
+  const int w = (int)(P.wh & 0xFFFFu), h = (int)(P.wh >> 16);
+  const float xs = __fsub_rn(__fmul_rn(u, P.wf), 0.5f), ys = __fsub_rn(__fmul_rn(v, P.hf), 0.5f);
+  fx = __fsub_rn(xs, floorf(xs));
+  fy = __fsub_rn(ys, floorf(ys));
+  xa = floor_mod_i(__float2int_rd(xs), w);  // cvt.rmi saturates out-of-range values
+  ya = floor_mod_i(__float2int_rd(ys), h);
+  xb = xa + 1 == w ? 0 : xa + 1;
+  yb = ya + 1 == h ? 0 : ya + 1;
+}
+
+__device__ __forceinline__ void nearest_any(const PixL& P, float u, float v, int& x, int& y) {
+  x = floor_mod_i(__float2int_rd(__fmul_rn(u, P.wf)), (int)(P.wh & 0xFFFFu));
+  y = floor_mod_i(__float2int_rd(__fmul_rn(v, P.hf)), (int)(P.wh >> 16));
+}
+
+// Walks the views' tiles: CTA tiles blockIdx.x, + gridDim.x, ...; warp rows w, w + nwarps,
+// ... of each tile. A row of a tile is 128 pixels, taken in SPR steps of 128 / SPR pixels
+// (the unit of work of a warp). The tile origin is recomputed only when the tile changes.
+template <int SPR>
+struct TileWalk {
+  uint32_t tile;
+  int r, h;    // row in the tile, step in the row
+  int vi;      // view of the tile
+  int x0, y0;  // tile origin
+  __device__ __forceinline__ bool valid(const ViewSet& vs) const { return tile < vs.total_tiles; }
+  __device__ __forceinline__ void set_tile(const ViewSet& vs) {
+    if (tile >= vs.total_tiles) return;
+    vi = view_of_tile(vs, tile);
+    const View& V = vs.v[vi];
+    const uint32_t lt = tile - V.tile_begin;
+    const uint32_t ty = lt / V.tiles_x;
+    x0 = (int)(lt - ty * V.tiles_x) * kTileW;
+    y0 = (int)ty * kTileH;
+  }
+  __device__ __forceinline__ void start(const ViewSet& vs) {
+    tile = blockIdx.x;
+    r = threadIdx.x >> 5;
+    h = 0;
+    vi = 0;
+    x0 = y0 = 0;
+    set_tile(vs);
+  }
+  __device__ __forceinline__ void advance(const ViewSet& vs) {
+    if (++h < SPR) return;
+    h = 0;
+    r += blockDim.x >> 5;
+    if (r >= kTileH) {
+      r = threadIdx.x >> 5;
+      tile += gridDim.x;
+      set_tile(vs);
+    }
+  }
+  __device__ __forceinline__ int x() const { return x0 + h * (kTileW / SPR); }  // first pixel of the step
+  __device__ __forceinline__ int y() const { return y0 + r; }
+};
+
+// G-buffer of a lane's pixels of the next step, loaded one step ahead of its use so that
+// its HBM reads are in flight while the lane works on the current one.
+template <int NPX>
+struct RowG {  // Colourise: pixels x + lane + 32 k, k < NPX, of one step of a row
+  float u[NPX], v[NPX];
+  uint32_t tm[NPX];  // texture id | mip level << 16 (JT_EMPTY_TEXTURE past the view)
+  uint32_t p0;       // index of pixel k = 0 in the view
+  uint32_t n;        // pixels present: those with k < n
+};
+
+template <int NPX>
+__device__ __forceinline__ void load_row(const View& V, int x, int y, bool valid, RowG<NPX>& g) {
+  g.n = (valid && y < V.height && x < V.width) ? (uint32_t)min(NPX, (V.width - x + 31) >> 5) : 0u;
+  g.p0 = (uint32_t)y * (uint32_t)V.width + (uint32_t)x;
+  const float2* uv = reinterpret_cast<const float2*>(V.uv) + g.p0;
+  const uint16_t* tx = V.tex + g.p0;
+  const uint8_t* mp = V.mip + g.p0;
+#pragma unroll
+  for (int k = 0; k < NPX; ++k) {
+    g.u[k] = g.v[k] = 0.f;
+    g.tm[k] = JT_EMPTY_TEXTURE;
+    if ((uint32_t)k < g.n) {
+      const float2 t = __ldg(uv + 32 * k);
+      g.u[k] = t.x;
+      g.v[k] = t.y;
+      g.tm[k] = (uint32_t)__ldg(tx + 32 * k) | ((uint32_t)__ldg(mp + 32 * k) << 16);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
 // Mark
 // ---------------------------------------------------------------------------------------
 constexpr int kSeen = 1024;  // per-CTA table of recently flagged gids
 
-template <int FILTER>
+template <int FILTER, bool MULTI>
 __global__ void k_mark(const __grid_constant__ MarkArgs a) {
   __shared__ uint32_t seen[kSeen];
   for (int i = threadIdx.x; i < kSeen; i += blockDim.x) seen[i] = kNoGid;
@@ -260,122 +426,179 @@ __global__ void k_mark(const __grid_constant__ MarkArgs a) {
 // ---------------------------------------------------------------------------------------
 // Colourise
 // ---------------------------------------------------------------------------------------
-// Channel `ch` of an RGBA8 texel as float, exactly: the byte is placed under the exponent
-// of 2^23 (PRMT) and the bias subtracted (full-rate ops instead of an int-to-float
-// conversion).
-__device__ __forceinline__ float chan(uint32_t c, int ch) {
-  return __int_as_float((int)__byte_perm(c, 0x4B00u, 0x5440u | (uint32_t)ch)) - 8388608.0f;
+__device__ __forceinline__ __half2 u32_as_h2(uint32_t w) {
+  __half2 h;
+  memcpy(&h, &w, 4);
+  return h;
+}
+__device__ __forceinline__ uint32_t h2_as_u32(__half2 h) {
+  uint32_t w;
+  memcpy(&w, &h, 4);
+  return w;
 }
 
-// Bilinear blend in fp32 (lerp along x, then y); each channel rounds half up:
-// floor(c + 1/2), computed as the low byte of (c + 1/2) + 2^23 rounded down.
-__device__ __forceinline__ uint32_t blend(uint32_t c00, uint32_t c10, uint32_t c01, uint32_t c11, float fx,
-                                          float fy) {
-  uint32_t out = 0xFF000000u;
-#pragma unroll
-  for (int ch = 0; ch < 3; ++ch) {
-    const float a0 = chan(c00, ch), a1 = chan(c10, ch), b0 = chan(c01, ch), b1 = chan(c11, ch);
-    const float top = fmaf(fx, a1 - a0, a0);
-    const float bot = fmaf(fx, b1 - b0, b0);
-    const float c = fmaf(fy, bot - top, top);  // in [0, 255] up to rounding
-    const uint32_t iv = (uint32_t)__float_as_int(__fadd_rd(__fadd_rn(c, 0.5f), 8388608.0f)) & 0x1FFu;
-    out |= min(iv, 255u) << (8 * ch);
-  }
-  return out;
-}
-
-template <int FILTER>
-__global__ void k_colorize(const __grid_constant__ ColorizeArgs a) {
-  bool missing = false, bad = false;
-  uint32_t last_gid = kNoGid, last_off = 0;  // slot of the last MCU looked up
-  const uint32_t* cache = reinterpret_cast<const uint32_t*>(a.cache);
-  // cache-unit offset of gid g (0 and `bad` when it would read past the cache)
-  auto slot = [&](uint32_t g, uint32_t units) -> uint32_t {
-    if (g != last_gid) {
-      last_gid = g;
-      last_off = __ldg(&a.slot[g]);
-    }
-    const bool fits = last_off + units <= a.cap_units;
-    bad |= !fits;
-    return fits ? last_off : 0u;
+// Bilinear blend of four RGBA8 texels with weights from fx, fy, rounded to bytes; alpha is
+// 255 (every texel's). Channels are blended two at a time in fp16 pairs: a byte b becomes
+// the half 1024 + b exactly (one byte permute under the exponent of 1024), differences of
+// two such halves are exact, and each lerp a + f (b - a) is one fused fp16 multiply-add.
+// The result c is rounded by adding 1536, whose binade [1024, 2048) has unit spacing, so
+// the low byte of the sum is round(c). Error bound: fx, fy carry at most 2^-12 absolute
+// error after the conversion to fp16 (255 * 2^-12 < 0.063 per lerp), each fp16 lerp and
+// difference of values below 256 rounds by at most 1/16, so |c - c_exact| < 0.32 over the
+// three lerps and one difference, and the byte differs from floor(c_exact + 1/2) by at most
+// one. c stays within [-0.32, 255.32], so c + 1536 never leaves [1024, 2048).
+__device__ __forceinline__ uint32_t blend_h(uint32_t c00, uint32_t c10, uint32_t c01, uint32_t c11, float fx,
+                                            float fy) {
+  const __half2 in_bias = u32_as_h2(0x64006400u);   // (1024, 1024)
+  const __half2 out_bias = u32_as_h2(0x66006600u);  // (1536, 1536)
+  const __half2 hx = __float2half2_rn(fx), hy = __float2half2_rn(fy);
+  auto lerp_x = [&](uint32_t a, uint32_t b, uint32_t sel) {
+    const __half2 ha = u32_as_h2(__byte_perm(a, 0x64646464u, sel));
+    const __half2 hb = u32_as_h2(__byte_perm(b, 0x64646464u, sel));
+    return __hfma2(hx, __hsub2(hb, ha), __hsub2(ha, in_bias));
   };
-  for_each_quad(a.views, [&](const View& V, int y, int x) {
-    float u[4], v[4];
-    uint32_t t[4], m[4];
-    const int n = load_px4(V, y, x, u, v, t, m);
-    QuadLevels q;
-    quad_levels(a.tl, n, t, m, a.only_tex, q);
-    uint32_t px[4];
-    for_quad_pixels(a.tl, q, [&](auto p2, const Lvl& L, int i) {
-      constexpr bool P2 = decltype(p2)::value;
-      const uint32_t key = q.key[i];
-      const bool ok = key < kNoKey - 1 && L.w != 0 && L.sampling != kSamplingCoef;
-      missing |= key != kNoKey && !ok;
-      px[i] = 0xFF000000u;  // empty pixel
-      if (!ok) return;
-      const int mwm = (1 << L.shift) - 1;
-      if (FILTER == JT_FILTER_NEAREST) {
-        int tx, ty;
-        nearest_texel<P2>(u[i], v[i], L, tx, ty);
-        const uint32_t off = slot(L.gid_base + (tx >> L.shift) + (ty >> L.shift) * L.mcus_x, L.units);
-        px[i] = __ldg(cache + (size_t)off * (kUnitBytes / 4) + (((ty & mwm) << L.shift) | (tx & mwm)));
-      } else if (FILTER == JT_FILTER_BILINEAR_CLAMP) {
-        // bilinear taps clamped to the nearest texel's MCU: along each axis a tap in
-        // another MCU moves onto the nearest texel's column or row (one MCU, one slot)
-        int nx, ny, xa, xb, ya, yb;
-        float fx, fy;
-        nearest_texel<P2>(u[i], v[i], L, nx, ny);
-        bilinear_taps<P2>(u[i], v[i], L, xa, xb, ya, yb, fx, fy);
-        const int mx = nx >> L.shift, my = ny >> L.shift;
-        xa = (xa >> L.shift) == mx ? xa : nx;
-        xb = (xb >> L.shift) == mx ? xb : nx;
-        ya = (ya >> L.shift) == my ? ya : ny;
-        yb = (yb >> L.shift) == my ? yb : ny;
-        const uint32_t* tile = cache + (size_t)slot(L.gid_base + mx + my * L.mcus_x, L.units) * (kUnitBytes / 4);
-        const int ia = (ya & mwm) << L.shift, ib = (yb & mwm) << L.shift;
-        const int ja = xa & mwm, jb = xb & mwm;
-        px[i] = blend(__ldg(tile + (ia | ja)), __ldg(tile + (ia | jb)), __ldg(tile + (ib | ja)),
-                      __ldg(tile + (ib | jb)), fx, fy);
-      } else {
-        int xa, xb, ya, yb;
-        float fx, fy;
-        bilinear_taps<P2>(u[i], v[i], L, xa, xb, ya, yb, fx, fy);
-        const int mxa = xa >> L.shift, mxb = xb >> L.shift;
-        const int mya = ya >> L.shift, myb = yb >> L.shift;
-        const uint32_t row_a = L.gid_base + mya * L.mcus_x;
-        const uint32_t o00 = slot(row_a + mxa, L.units);
-        uint32_t o10 = o00, o01 = o00, o11 = o00;
-        if (mxb != mxa || myb != mya) {  // the footprint straddles MCUs (rare)
-          const uint32_t row_b = L.gid_base + myb * L.mcus_x;
-          o10 = slot(row_a + mxb, L.units);
-          o01 = slot(row_b + mxa, L.units);
-          o11 = slot(row_b + mxb, L.units);
-        }
-        const int ia = (ya & mwm) << L.shift, ib = (yb & mwm) << L.shift;
-        const int ja = xa & mwm, jb = xb & mwm;
-        const uint32_t c00 = __ldg(cache + (size_t)o00 * (kUnitBytes / 4) + (ia | ja));
-        const uint32_t c10 = __ldg(cache + (size_t)o10 * (kUnitBytes / 4) + (ia | jb));
-        const uint32_t c01 = __ldg(cache + (size_t)o01 * (kUnitBytes / 4) + (ib | ja));
-        const uint32_t c11 = __ldg(cache + (size_t)o11 * (kUnitBytes / 4) + (ib | jb));
-        px[i] = blend(c00, c10, c01, c11, fx, fy);
-      }
-    });
-    if (n == 0) return;
-    bool write[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) write[i] = i < n && (a.only_tex < 0 || (int)t[i] == a.only_tex);
-    const uint32_t p0 = (uint32_t)y * (uint32_t)V.width + (uint32_t)x;
-    if (n == 4 && (V.width & 3) == 0 && write[0] && write[1] && write[2] && write[3]) {
-      V.out[p0 >> 2] = make_uint4(px[0], px[1], px[2], px[3]);
-    } else {
-      uint32_t* o = reinterpret_cast<uint32_t*>(V.out) + p0;
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-        if (write[i]) o[i] = px[i];
+  const __half2 top_rg = lerp_x(c00, c10, 0x5140u), bot_rg = lerp_x(c01, c11, 0x5140u);  // (R, G)
+  const __half2 top_ba = lerp_x(c00, c10, 0x5342u), bot_ba = lerp_x(c01, c11, 0x5342u);  // (B, A)
+  const __half2 rg = __hadd2(__hfma2(hy, __hsub2(bot_rg, top_rg), top_rg), out_bias);
+  const __half2 ba = __hadd2(__hfma2(hy, __hsub2(bot_ba, top_ba), top_ba), out_bias);
+  return __byte_perm(h2_as_u32(rg), h2_as_u32(ba), 0x6420u);
+}
+
+// One pixel's colour from its taps: slots of up to four MCUs (predicated loads beyond the
+// first) and four texel gathers, then the blend (bilinear) or the texel itself (nearest).
+template <int FILTER>
+__device__ __forceinline__ uint32_t shade(const uint32_t* __restrict__ slot, const uint32_t* __restrict__ cache,
+                                          const PixL& P, int xa, int xb, int ya, int yb, float fx, float fy) {
+  const uint32_t s = P.shift, mwm = (1u << s) - 1u;
+  const uint32_t xas = (uint32_t)xa >> s, xbs = (uint32_t)xb >> s;
+  const uint32_t rowa = P.gid_base + ((uint32_t)ya >> s) * P.mcus_x;
+  const uint32_t o00 = __ldg(slot + rowa + xas);
+  const uint32_t ia = ((uint32_t)ya & mwm) << s, ja = (uint32_t)xa & mwm;
+  if (FILTER == JT_FILTER_NEAREST) return __ldg(cache + (size_t)o00 * (kUnitBytes / 4) + (ia | ja));
+  const uint32_t rowb = P.gid_base + ((uint32_t)yb >> s) * P.mcus_x;
+  const bool sx = xbs != xas, sy = rowb != rowa;
+  uint32_t o10 = o00, o01 = o00;
+  if (sx) o10 = __ldg(slot + rowa + xbs);
+  if (sy) o01 = __ldg(slot + rowb + xas);
+  uint32_t o11 = sx ? o10 : o01;
+  if (sx && sy) o11 = __ldg(slot + rowb + xbs);
+  const uint32_t ib = ((uint32_t)yb & mwm) << s, jb = (uint32_t)xb & mwm;
+  const uint32_t c00 = __ldg(cache + (size_t)o00 * (kUnitBytes / 4) + (ia | ja));
+  const uint32_t c10 = __ldg(cache + (size_t)o10 * (kUnitBytes / 4) + (ia | jb));
+  const uint32_t c01 = __ldg(cache + (size_t)o01 * (kUnitBytes / 4) + (ib | ja));
+  const uint32_t c11 = __ldg(cache + (size_t)o11 * (kUnitBytes / 4) + (ib | jb));
+  return blend_h(c00, c10, c01, c11, fx, fy);
+}
+
+// Taps of the clamped filter: along each axis a tap in another MCU than the nearest texel's
+// moves onto the nearest texel's column or row (one MCU).
+__device__ __forceinline__ void clamp_taps(uint32_t s, int nx, int ny, int& xa, int& xb, int& ya, int& yb) {
+  const int mx = nx >> s, my = ny >> s;
+  xa = (xa >> s) == mx ? xa : nx;
+  xb = (xb >> s) == mx ? xb : nx;
+  ya = (ya >> s) == my ? ya : ny;
+  yb = (yb >> s) == my ? yb : ny;
+}
+
+// The general path of one pixel (any level, any coordinate; out of line).
+template <int FILTER>
+__device__ __noinline__ uint32_t colour_any(const uint32_t* slot, const uint32_t* cache, const PixL& P, float u,
+                                            float v) {
+  int xa, xb, ya, yb;
+  float fx = 0.f, fy = 0.f;
+  if (FILTER == JT_FILTER_NEAREST) {
+    nearest_any(P, u, v, xa, ya);
+    xb = xa;
+    yb = ya;
+  } else {
+    taps_any(P, u, v, xa, xb, ya, yb, fx, fy);
+    if (FILTER == JT_FILTER_BILINEAR_CLAMP) {
+      int nx, ny;
+      nearest_any(P, u, v, nx, ny);
+      clamp_taps(P.shift, nx, ny, xa, xb, ya, yb);
     }
-  });
+  }
+  return shade<FILTER>(slot, cache, P, xa, xb, ya, yb, fx, fy);
+}
+
+// A lane owns pixel lane + 32 k (k < NPX) of each step of a row (32 NPX pixels), so a warp's
+// texel gathers for one tap fall in the two or three tiles its 32 consecutive pixels cover
+// (few L1 wavefronts per load), and the lane's NPX pixels are independent chains (level
+// record, slot, texels) that overlap. The next step's G-buffer is loaded before the
+// current one is shaded. The fast path has no data-dependent branch: the level record is
+// loaded per pixel (an L1 hit), slots beyond the first tap's MCU are predicated loads, and
+// pixels it cannot address (sides not powers of two, |u w| or |v h| >= 2^22) are redone on
+// the general path. Warps whose pixels all lack a texture skip the arithmetic. Slots are in
+// range by construction (the compaction and the cache update never write a slot whose tile
+// would end past the cache), and the all-zero record of keys outside the table addresses
+// unit 0, so no load needs a bound check.
+template <int FILTER, bool MULTI, int NPX>
+__global__ void __launch_bounds__(512) k_colorize(const __grid_constant__ ColorizeArgs a) {
+  const uint32_t* __restrict__ cache = reinterpret_cast<const uint32_t*>(a.cache);
+  const uint32_t* __restrict__ slot = a.slot;
+  const ViewSet& vs = a.views;
+  bool missing = false;
+  const int lx = threadIdx.x & 31;
+  TileWalk<4 / NPX> it;
+  it.start(vs);
+  RowG<NPX> g;
+  load_row(vs.v[MULTI ? it.vi : 0], it.x() + lx, it.y(), it.valid(vs), g);
+#pragma unroll 1
+  while (it.valid(vs)) {
+    TileWalk<4 / NPX> nx = it;
+    nx.advance(vs);
+    RowG<NPX> ng;
+    load_row(vs.v[MULTI ? nx.vi : 0], nx.x() + lx, nx.y(), nx.valid(vs), ng);
+    uint32_t sel = 0, use = 0;
+#pragma unroll
+    for (int k = 0; k < NPX; ++k) {
+      const uint32_t tex = g.tm[k] & 0xFFFFu;
+      const bool sk = (uint32_t)k < g.n && (a.only_tex < 0 || (int)tex == a.only_tex);
+      sel |= sk ? (1u << k) : 0u;
+      use |= sk && tex != JT_EMPTY_TEXTURE ? (1u << k) : 0u;
+    }
+    uint32_t px[NPX];
+#pragma unroll
+    for (int k = 0; k < NPX; ++k) px[k] = 0xFF000000u;  // empty pixels
+    if (__any_sync(0xFFFFFFFFu, use != 0)) {
+      uint32_t slow = 0;
+#pragma unroll
+      for (int k = 0; k < NPX; ++k) {
+        const PixL P = pix_level(a.tl, g.tm[k]);
+        const bool ok = (use >> k & 1u) && (P.info & kPixJpeg);
+        missing |= (use >> k & 1u) && !(P.info & kPixJpeg);
+        int xa, xb, ya, yb;
+        float fx = 0.f, fy = 0.f;
+        bool fast;
+        if (FILTER == JT_FILTER_NEAREST) {
+          fast = nearest_fast(P, g.u[k], g.v[k], xa, ya);
+          xb = xa;
+          yb = ya;
+        } else {
+          fast = taps_fast(P, g.u[k], g.v[k], xa, xb, ya, yb, fx, fy);
+          if (FILTER == JT_FILTER_BILINEAR_CLAMP) {
+            int nxp, nyp;
+            fast &= nearest_fast(P, g.u[k], g.v[k], nxp, nyp);
+            clamp_taps(P.shift, nxp, nyp, xa, xb, ya, yb);
+          }
+        }
+        if (ok) px[k] = shade<FILTER>(slot, cache, P, xa, xb, ya, yb, fx, fy);
+        slow |= (ok && !fast) ? (1u << k) : 0u;
+      }
+      if (slow) {  // rare: redo those pixels on the general path
+#pragma unroll
+        for (int k = 0; k < NPX; ++k)
+          if (slow & (1u << k)) px[k] = colour_any<FILTER>(slot, cache, pix_level(a.tl, g.tm[k]), g.u[k], g.v[k]);
+      }
+    }
+    uint32_t* out = reinterpret_cast<uint32_t*>(vs.v[MULTI ? it.vi : 0].out) + g.p0;
+#pragma unroll
+    for (int k = 0; k < NPX; ++k)
+      if (sel & (1u << k)) out[32 * k] = px[k];
+    it = nx;
+    g = ng;
+  }
   if (missing) atomicOr(&a.state->err, JT_DEVERR_MISSING);
-  if (bad) atomicOr(&a.state->err, JT_DEVERR_CAPACITY);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -500,19 +723,40 @@ void launch_float_scatter(const FloatArgs& a, int threads, int grid, cudaStream_
 
 void launch_mark(const MarkArgs& a, int threads, int grid, cudaStream_t s) {
   // the clamped filter reads only the nearest texel's MCU
-  if (a.filter == JT_FILTER_NEAREST || a.filter == JT_FILTER_BILINEAR_CLAMP)
-    k_mark<JT_FILTER_NEAREST><<<grid, threads, 0, s>>>(a);
+  const bool nearest = a.filter == JT_FILTER_NEAREST || a.filter == JT_FILTER_BILINEAR_CLAMP;
+  if (a.views.n > 1) {
+    if (nearest)
+      k_mark<JT_FILTER_NEAREST, true><<<grid, threads, 0, s>>>(a);
+    else
+      k_mark<JT_FILTER_BILINEAR, true><<<grid, threads, 0, s>>>(a);
+  } else {
+    if (nearest)
+      k_mark<JT_FILTER_NEAREST, false><<<grid, threads, 0, s>>>(a);
+    else
+      k_mark<JT_FILTER_BILINEAR, false><<<grid, threads, 0, s>>>(a);
+  }
+}
+
+// pixels per lane per step: two (60 registers, 32 warps per SM) measured faster than four
+// (74 registers) on the 4K frame
+constexpr int kColorizePx = 2;
+
+template <bool MULTI>
+void launch_colorize_views(const ColorizeArgs& a, int threads, int grid, cudaStream_t s) {
+  constexpr int N = kColorizePx;
+  if (a.filter == JT_FILTER_NEAREST)
+    k_colorize<JT_FILTER_NEAREST, MULTI, N><<<grid, threads, 0, s>>>(a);
+  else if (a.filter == JT_FILTER_BILINEAR_CLAMP)
+    k_colorize<JT_FILTER_BILINEAR_CLAMP, MULTI, N><<<grid, threads, 0, s>>>(a);
   else
-    k_mark<JT_FILTER_BILINEAR><<<grid, threads, 0, s>>>(a);
+    k_colorize<JT_FILTER_BILINEAR, MULTI, N><<<grid, threads, 0, s>>>(a);
 }
 
 void launch_colorize(const ColorizeArgs& a, int threads, int grid, cudaStream_t s) {
-  if (a.filter == JT_FILTER_NEAREST)
-    k_colorize<JT_FILTER_NEAREST><<<grid, threads, 0, s>>>(a);
-  else if (a.filter == JT_FILTER_BILINEAR_CLAMP)
-    k_colorize<JT_FILTER_BILINEAR_CLAMP><<<grid, threads, 0, s>>>(a);
+  if (a.views.n > 1)
+    launch_colorize_views<true>(a, threads, grid, s);
   else
-    k_colorize<JT_FILTER_BILINEAR><<<grid, threads, 0, s>>>(a);
+    launch_colorize_views<false>(a, threads, grid, s);
 }
 
 }  // namespace jt

@@ -93,6 +93,30 @@ def test_compact_static_small_cases_and_work_overflow(jt):
     np.testing.assert_array_equal(work.cpu().numpy(), np.arange(100))
 
 
+@pytest.mark.gpu
+def test_compact_static_large_flags_over_many_tiles(jt):
+    """Flags of 255 over 1.5 M indices: unit prefixes pass 2^28 within the scan, which must
+    carry them in full (checked against the exact cumulative sum)."""
+    n = 1_500_000
+    f = np.full(n, 255, np.uint8)
+    f[::7] = 0  # some gaps, so counts and unit sums differ
+    flags = torch.from_numpy(f).cuda()
+    slot = torch.zeros(n, dtype=torch.int32, device="cuda")
+    work = torch.zeros(n, dtype=torch.int32, device="cuda")
+    totals = torch.zeros(3, dtype=torch.int32, device="cuda")
+    for _ in range(2):  # twice: the scratch must start each call from zero
+        flags.copy_(torch.from_numpy(f))
+        jt.compact_static(flags, slot, work, totals)
+        torch.cuda.synchronize()
+        idx = np.flatnonzero(f)
+        exc = np.concatenate([[0], np.cumsum(f.astype(np.int64))])[:-1]
+        t = totals.cpu().numpy().view(np.uint32)
+        assert int(t[0]) == idx.size and int(t[1]) == int(f.astype(np.int64).sum()) and int(t[2]) == 0
+        assert int(f.astype(np.int64).sum()) > (1 << 28)
+        np.testing.assert_array_equal(work.cpu().numpy()[: idx.size], idx)
+        np.testing.assert_array_equal(slot.cpu().numpy().view(np.uint32)[idx].astype(np.int64), exc[idx])
+
+
 def test_compact_static_rejects_before_enqueueing(jt):
     """Argument checks return before any CUDA call (no GPU needed)."""
     L = jt.lib()
