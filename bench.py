@@ -170,33 +170,156 @@ def oracle_baseline(ts, gb, budget_s: float = 10.0):
                       f"access in {secs:.1f} s (single-threaded C++ -O2)"}
 
 
+# ---------------------------------------------------------------------------------------
+# The oracle on all host cores: a pool of worker processes, forked before the first CUDA
+# call (the workers inherit the workload and never touch CUDA), each holding its own oracle
+# texture set. A frame is split into row bands taken by the workers; every band decodes the
+# MCUs its pixels need from a cold tile cache, so MCUs shared by two bands are decoded twice.
+# ---------------------------------------------------------------------------------------
+_CPU = {}
+
+
+def _cpu_band(rows):
+    if "o" not in _CPU:  # built on a worker's first task, so idle workers cost nothing
+        import oracle
+        _CPU["o"] = oracle.texset_from(_CPU["ts"])
+    return oracle_frame_band(_CPU["o"], _CPU["gb"], slice(rows[0], rows[1]))
+
+
+def _cpu_decode4(i):
+    """Sequential full decode of config-4 texture i (one 4096^2 level); (seconds, MCUs, bytes)."""
+    import oracle
+    e = _CPU["ts4"][i]
+    t0 = time.perf_counter()
+    d = oracle.Decoded(e.jfif)
+    dt = time.perf_counter() - t0
+    return dt, e.nmcu, int(d.rgba.size)
+
+
+class CpuPool:
+    def __init__(self, ts, gb, ts4, n: int):
+        import multiprocessing
+        _CPU.update(ts=ts, gb=gb, ts4=ts4)
+        self.n = n
+        self.pool = multiprocessing.get_context("fork").Pool(n)
+
+    def frame(self, H: int, needed: int, budget_s: float = 10.0):
+        """Whole frames split into 4 n row bands over the n workers, repeated for about
+        budget_s of wall time: needed blocks (of the whole frame) per wall second."""
+        nb = 4 * self.n
+        bands = [(H * i // nb, H * (i + 1) // nb) for i in range(nb)]
+        self.pool.map(_cpu_band, bands, chunksize=1)  # warm-up: the workers build their texture sets
+        frames, wall, decoded = 0, 0.0, 0
+        while wall < budget_s or frames == 0:
+            t0 = time.perf_counter()
+            res = self.pool.map(_cpu_band, bands, chunksize=1)
+            wall += time.perf_counter() - t0
+            decoded += sum(r[1] for r in res)
+            frames += 1
+        return {"value": frames * needed / wall, "frames": frames, "wall_s": wall,
+                "decoded_per_frame": decoded / frames}
+
+    def decode4(self, nt: int):
+        """Config-4 full decode: the n workers each decode textures round-robin from nt."""
+        t0 = time.perf_counter()
+        res = self.pool.map(_cpu_decode4, [i % nt for i in range(self.n)], chunksize=1)
+        wall = time.perf_counter() - t0
+        mcus = sum(r[1] for r in res)
+        out = sum(r[2] for r in res)
+        return {"blocks_per_s": mcus / wall, "gbs": out / wall / 1e9, "textures": self.n, "wall_s": wall}
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def config4_cpu_textures():
+    """One 4096^2 level of each sampling at quality 90 (the config-4 texture shape)."""
+    import synth
+    ts = synth.config4_textures(ntex=2)  # texture 0 at 4:4:4, texture 1 at 4:2:0
+    return [lv[0] for lv in ts.levels]
+
+
+def oracle_all(pool, ts, ts4, gb, needed):
+    """The CPU baseline: the 4K frame on 1 core (the line's value) and on all cores; config 4's
+    sequential full decode on 1 core and on all cores; config 5's FP64 backward on a band
+    (1 core)."""
+    import oracle
+    import synth
+    one = oracle_baseline(ts, gb)
+    fa = pool.frame(gb.height, needed)
+    one.update(value_all_cores=fa["value"], cores_all=pool.n, cpu_model=cpu_model(), nproc=os.cpu_count(),
+               sample_all_cores=f"{fa['frames']} whole frames, each split into {4 * pool.n} row bands over "
+                                f"{pool.n} processes (cold tile cache per band: {fa['decoded_per_frame']:.0f} MCU "
+                                f"decodes per frame for {needed} needed)")
+    res = {}
+    # config 4, one core: both samplings decoded in the main process
+    t, mc, ob = 0.0, 0, 0
+    for e in ts4:
+        t0 = time.perf_counter()
+        d = oracle.Decoded(e.jfif)
+        t += time.perf_counter() - t0
+        mc += e.nmcu
+        ob += int(d.rgba.size)
+    res["full_decode_1_core"] = {"blocks_per_s": mc / t, "gbs": ob / t / 1e9,
+                                 "sample": "one 4096^2 Q90 texture at 4:4:4 and one at 4:2:0"}
+    res["full_decode_all_cores"] = dict(pool.decode4(len(ts4)), sample="one 4096^2 Q90 texture per core, "
+                                        "alternating 4:4:4 and 4:2:0")
+    # config 5, one core: FP64 loss and gradient over a band of 1/16 of the rows
+    ts5, coef, gb5, target = synth.config5()
+    r = gb5.height // 16
+    band = synth.GBuffer(gb5.width, r, gb5.uv[:r], gb5.tex_id[:r], gb5.mip[:r])
+    t0 = time.perf_counter()
+    oracle.float_loss_grad(coef, band, target[:r])
+    dt = time.perf_counter() - t0
+    res["adjoint_fp64_1_core"] = {"band_ms": 1000 * dt, "rows": r, "of_rows": gb5.height,
+                                  "full_frame_ms_scaled": 1000 * dt * gb5.height / r,
+                                  "sample": f"FP64 loss and gradient of the 1920x1080 plane's first {r} rows "
+                                            f"(the full frame scaled by rows)"}
+    return one, res
+
+
 def run_reference(args, rank, world):
+    """The oracle (plain C++, as it stands) on all host cores: each step is one whole 4K frame
+    split into row bands over one worker process per core."""
     if rank != 0:
         return 0
-    ts, gb = workload()
     import oracle
+    ts, gb = workload()
     o = oracle.texset_from(ts)
-    # per-step sample: a band of rows sized so warm-up + steps fit in ~120 s
-    dt, _ = oracle_frame_band(o, gb, slice(gb.height // 2, gb.height // 2 + 16))
-    per_row = max(dt / 16, 1e-4)
-    budget = 120.0 / max(1, args.steps + args.warmup)
-    rows = int(max(1, min(gb.height, budget / per_row)))
-    t_total, b_total = 0.0, 0
+    needed = int(o.compact(o.mark(gb, 1)).size)
+    del o
+    n = len(os.sched_getaffinity(0))
+    pool = CpuPool(ts, gb, None, n)
+    nb = 4 * n
+    bands = [(gb.height * i // nb, gb.height * (i + 1) // nb) for i in range(nb)]
+    t_total = 0.0
     for s in range(args.warmup + args.steps):
-        r0 = (s * rows) % gb.height
-        r1 = min(gb.height, r0 + rows)
-        dt, nb = oracle_frame_band(o, gb, slice(r0, r1))
+        t0 = time.perf_counter()
+        pool.pool.map(_cpu_band, bands, chunksize=1)
         if s >= args.warmup:
-            t_total += dt
-            b_total += nb
-    value = b_total / t_total
+            t_total += time.perf_counter() - t0
+    pool.close()
+    value = args.steps * needed / t_total
+    sample = (f"each step: the whole 3840x2160 frame ({needed} needed MCUs), mark + random-access decode + "
+              f"bilinear colourise, split into {nb} row bands over {n} processes")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t_total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
             "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "n/a (host)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"each step: {rows} rows of the 3840x2160 frame (cycling), mark + "
-                                       f"random-access decode + bilinear colourise"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": n, "kind": "oracle", "sample": sample,
+                             "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -276,6 +399,10 @@ def run_views(ctx, ts, jt, dev, flush, stream, steps):
     st = ctx.stats()
     union = int(st["needed_blocks"])
     ref = [o.clone() for o in outs]
+    # the same five launches issued one by one (no graph): the graph's own gain
+    ms_eager = timed(lambda: ctx.frame(pairs, jt.FILTER_BILINEAR), steps, 3, stream, flush)
+    ctx.stats()
+    eager_same = all(bool(torch.equal(a, b)) for a, b in zip(ref, outs))
     per_view = []
     for d, o in pairs:  # needed blocks of each view alone
         ctx.frame([(d, o)], jt.FILTER_BILINEAR)
@@ -285,11 +412,63 @@ def run_views(ctx, ts, jt, dev, flush, stream, steps):
     same = all(bool(torch.equal(a, b)) for a, b in zip(ref, outs))
     ctx.graph_destroy(g)
     px = sum(v.width * v.height for v in views)
-    return {"workload": "8 views 1280x720, 1920x1080, 2560x1440, 3840x2160, 2x2 VR 2064x2208 (two stereo poses), "
-                        "same 64 textures, bilinear", "pixels": px, "needed_blocks_union": union,
-            "needed_blocks_per_view": per_view, "batched_graph_ms": ms_graph, "plain_ms": ms_plain,
-            "speedup": ms_plain / ms_graph, "same_output": same,
+    span = max(per_view) / max(1, min(per_view))
+    return {"workload": "8 views 1280x720 (looking up: sky and 6 quads), 1920x1080, 2560x1440, 3840x2160, "
+                        "2x2 VR 2064x2208 (two stereo poses), same 64 textures, bilinear", "pixels": px,
+            "needed_blocks_union": union, "needed_blocks_per_view": per_view, "span": span,
+            "span_over_50": span > 50, "batched_graph_ms": ms_graph, "eager_ms": ms_eager,
+            "graph_speedup_over_eager": ms_eager / ms_graph, "plain_ms": ms_plain,
+            "speedup": ms_plain / ms_graph, "same_output": same and eager_same,
             "blocks_per_s": union / (ms_graph * 1e-3)}
+
+
+def run_e2e_pipelined(ctx, jt, host, W, H, dev, frames):
+    """Frames streamed from host buffers with the copies overlapped: two device G-buffers and
+    framebuffers (one CUDA graph each); frame k's upload runs on an upload stream while frame
+    k - 1 renders, and frame k - 1's download on a download stream while frame k renders.
+    Returns ms per frame over `frames` frames (first upload to last download) and whether the
+    downloaded frames equal the reference. Every frame's G-buffer is freshly uploaded, and
+    the two buffer sets with their framebuffers (250 MB) exceed L2."""
+    import torch
+    uv_h, tex_h, mip_h, out_ref = host
+    gbs = [jt.DeviceGBuffer.empty(W, H, dev) for _ in range(2)]
+    outs = [torch.empty((H, W, 4), dtype=torch.uint8, device=dev) for _ in range(2)]
+    outs_h = [torch.empty((H, W, 4), dtype=torch.uint8).pin_memory() for _ in range(2)]
+    graphs = [ctx.frame_graph([(gbs[i], outs[i])], jt.FILTER_BILINEAR) for i in range(2)]
+    s_gpu = torch.cuda.current_stream(dev)
+    s_up, s_dn = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    ev_up = [torch.cuda.Event() for _ in range(2)]
+    ev_done = [torch.cuda.Event() for _ in range(2)]
+    ev_dn = [torch.cuda.Event() for _ in range(2)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(s_up)
+    for k in range(frames):
+        i = k & 1
+        if k >= 2:
+            s_up.wait_event(ev_done[i])  # frame k - 2 has finished reading this G-buffer
+        with torch.cuda.stream(s_up):
+            gbs[i].uv.copy_(uv_h, non_blocking=True)
+            gbs[i].tex_id.copy_(tex_h, non_blocking=True)
+            gbs[i].mip.copy_(mip_h, non_blocking=True)
+        ev_up[i].record(s_up)
+        s_gpu.wait_event(ev_up[i])
+        if k >= 2:
+            s_gpu.wait_event(ev_dn[i])  # frame k - 2's framebuffer has been downloaded
+        ctx.graph_launch(graphs[i], s_gpu)
+        ev_done[i].record(s_gpu)
+        s_dn.wait_event(ev_done[i])
+        with torch.cuda.stream(s_dn):
+            outs_h[i].copy_(outs[i], non_blocking=True)
+        ev_dn[i].record(s_dn)
+    t1.record(s_dn)
+    t1.synchronize()
+    ms = t0.elapsed_time(t1) / frames
+    ctx.stats()
+    same = all(bool(torch.equal(o, out_ref)) for o in outs_h)
+    for g in graphs:
+        ctx.graph_destroy(g)
+    return ms, same
 
 
 def run_clamped(ctx, jt, dgb, out, flush, stream, steps):
@@ -556,27 +735,38 @@ def run_adjoint(jt, dev, flush, stream, steps, peak):
     ms_bwd = timed(lambda: ctx.colorize_backward(dgb, gF, gc), steps, 3, stream, flush)
     ctx.stats()
     npx = gb.width * gb.height
-    # algorithmic HBM bytes: every gradient written once; G-buffer read by mark and scatter,
-    # the frame gradient once; per needed MCU its texel-gradient tile zeroed and read back.
-    # Forward: G-buffer twice, F written, per needed MCU its coefficients read and its float
-    # tile written, four 16-byte texel taps per pixel
-    bwd_bytes = 4.0 * c.numel() + 2 * 11.0 * npx + 12.0 * npx + needed * (2 * 4096.0)
-    fwd_bytes = 2 * 11.0 * npx + 12.0 * npx + needed * (1536.0 + 4096.0) + 4 * 16.0 * npx
+    # the method's HBM bytes: the backward writes every coefficient's gradient once (the map
+    # is affine, so the coefficients themselves are not read), reads the G-buffer twice (the
+    # needed set's mark and the scatter) and the frame gradient once. The forward reads the
+    # G-buffer twice, each needed MCU's coefficients once and writes the frame.
+    bwd_bytes = 4.0 * c.numel() + 2 * 11.0 * npx + 12.0 * npx
+    fwd_bytes = 2 * 11.0 * npx + needed * 1536.0 + 12.0 * npx
+    # the intermediate texel-gradient (backward) / texel (forward) tiles of 4 KiB per needed
+    # MCU: zeroed and read back, or written and gathered; kept out of the method's bytes
+    tile_bytes = needed * 2 * 4096.0
     ctx.close()
     ach = bwd_bytes / (ms_bwd * 1e-3) / 1e9
     return {"workload": "16 coefficient textures 2048^2 4:2:0 (float32 [16,128,128,6,64]), 1920x1080 plane, "
                         "bilinear", "needed_blocks": needed, "forward_ms": ms_fwd, "backward_ms": ms_bwd,
             "backward_roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                                  "algorithmic_bytes": bwd_bytes},
-            "forward_achieved_gbs": fwd_bytes / (ms_fwd * 1e-3) / 1e9}
+                                  "algorithmic_bytes": bwd_bytes, "intermediate_tile_bytes": tile_bytes},
+            "forward_roofline": {"bound": "hbm", "achieved": fwd_bytes / (ms_fwd * 1e-3) / 1e9, "peak": peak,
+                                 "unit": "GB/s", "frac": fwd_bytes / (ms_fwd * 1e-3) / 1e9 / peak,
+                                 "algorithmic_bytes": fwd_bytes, "intermediate_tile_bytes": tile_bytes}}
+
 
 def run_gpu(args, rank, world, local_rank):
     import torch
     import paper_2510_08166_gb300 as jt
 
+    ts, gb = workload(compact=not args.no_extra)
+    pool = ts4 = None
+    if rank == 0 and world == 1 and not args.no_cpu and not args.quick:
+        # the CPU baseline's workers are forked here, before the first CUDA call
+        ts4 = config4_cpu_textures()
+        pool = CpuPool(ts, gb, ts4, len(os.sched_getaffinity(0)))
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    ts, gb = workload(compact=not args.no_extra)
     ctx = jt.Context(local_rank, max_cache_blocks=1 << 18)
     ctx.upload_set(ts)
     dgb = jt.DeviceGBuffer.from_host(gb, dev)
@@ -667,6 +857,9 @@ def run_gpu(args, rank, world, local_rank):
             e2e_ms.append(a0.elapsed_time(a1))
     h2d = uv_h.numel() * 4 + tex_h.numel() * 2 + mip_h.numel()
     d2h = out_h.numel()
+    # the same frames with the copies overlapped with rendering (the serving pattern)
+    pipe_ms, pipe_same = run_e2e_pipelined(ctx, jt, (uv_h, tex_h, mip_h, out.cpu()), gb.width, gb.height, dev,
+                                           max(10, min(args.steps, 200)))
 
     # the per-texture "plain" pipeline for comparison (same output)
     ref_out = out.clone()
@@ -699,7 +892,7 @@ def run_gpu(args, rank, world, local_rank):
     e2e_value = world * nblocks / (statistics.mean(e2e_ms) * 1e-3)
 
     if rank == 0:
-        cpu = oracle_baseline(ts, gb) if (world == 1 and not args.no_cpu) else None
+        cpu, cpu_legs = oracle_all(pool, ts, ts4, gb, nblocks) if pool is not None else (None, None)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": frame_ms, "higher_is_better": True, "scaling": "weak",
@@ -716,13 +909,20 @@ def run_gpu(args, rank, world, local_rank):
             "frame_roofline": {"achieved": sum(alg.values()) / (frame_ms * 1e-3) / 1e9, "unit": "GB/s",
                                "frac": sum(alg.values()) / (frame_ms * 1e-3) / 1e9 / peak},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "ms_per_step": statistics.mean(e2e_ms)},
+                    "ms_per_step": statistics.mean(e2e_ms),
+                    "copies": "pinned host buffers copied by torch around the library's graph launch, "
+                              "L2 flushed between steps, one stream (serial)"},
+            "e2e_pipelined": {"value": world * nblocks / (pipe_ms * 1e-3), "unit": UNIT, "ms_per_step": pipe_ms,
+                              "same_output": pipe_same, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                              "how": "double-buffered G-buffers and framebuffers, uploads and downloads on their "
+                                     "own streams overlapped with the previous / next frame's graph"},
             "plain": {"ms_per_frame": statistics.mean(plain_ms), "same_output": plain_same,
                       "graph_speedup": statistics.mean(plain_ms) / frame_ms},
             "gpu_launches": LAUNCHES_PER_FRAME * args.steps,
             "clocks": clk,
             "wall_s": wall,
             "cpu_baseline": cpu,
+            "cpu_legs": cpu_legs,
         }
         if tuned:
             line["tuning"] = tuned
@@ -738,6 +938,8 @@ def run_gpu(args, rank, world, local_rank):
             line["motion"] = run_motion(jt, ts, dev, flush, stream)
             line["motion_vr"] = run_motion(jt, ts, dev, flush, stream, stereo=True)
         print(json.dumps(line), flush=True)
+    if pool is not None:
+        pool.close()
     ctx.close()
     return 0
 

@@ -437,16 +437,24 @@ def config1():
     return ts, gb
 
 
-def config2_textures(ntex: int = 64, threads: int | None = None, compact: bool = False) -> TextureSet:
-    """64 textures, sizes uniform in {1024,2048,4096}^2, Q uniform in [50,95], 4:2:0,
-    full mip chains each level encoded separately."""
+def config2_draws(ntex: int = 64):
+    """Sizes (uniform in {1024,2048,4096}^2) and qualities (uniform in [50,95]) of the
+    64 scene textures, without encoding them."""
     seed = SEED_BASE + 2
     sizes, quals = [], []
     for t in range(ntex):
         s = mix_seed(seed, 200, t)
         sizes.append((1024 << (s % 3),) * 2)
         quals.append(50 + int((s >> 8) % 46))
-    return make_texture_set(seed, sizes, quals, [420] * ntex, full_chain=True, threads=threads, compact=compact)
+    return sizes, quals
+
+
+def config2_textures(ntex: int = 64, threads: int | None = None, compact: bool = False) -> TextureSet:
+    """64 textures, sizes uniform in {1024,2048,4096}^2, Q uniform in [50,95], 4:2:0,
+    full mip chains each level encoded separately."""
+    sizes, quals = config2_draws(ntex)
+    return make_texture_set(SEED_BASE + 2, sizes, quals, [420] * ntex, full_chain=True, threads=threads,
+                            compact=compact)
 
 
 def config2_pose() -> Pose:
@@ -460,16 +468,23 @@ def config2_gbuffer(ts: TextureSet, W: int = 3840, H: int = 2160) -> GBuffer:
 
 def config3_views(ts: TextureSet):
     """8 views: 1280x720, 1920x1080, 2560x1440, 3840x2160 and VR stereo 2x(2064x2208) at two
-    poses (eye separation 0.064 m). The 720p view pitches up towards the sky."""
+    poses (eye separation 0.064 m). The 720p view pitches up 35 degrees, above the ground, and
+    holds six screen quads, so that the views' needed-block counts span more than 50x (the
+    tests check the span on the needed sets)."""
+    return config3_views_for(ts.sizes, ts.nlevels)
+
+
+def config3_views_for(sizes, nlevels):
+    """config3_views from the textures' sizes and level counts alone."""
     seed = SEED_BASE + 3
     qs = mix_seed(seed, 300, 0)
     views = []
-    flat = [((1280, 720), Pose((0.0, 1.7, 0.0), 10.0, 4.0, 60.0, qs, 0.0)),
-            ((1920, 1080), Pose((3.0, 1.7, 5.0), 40.0, -20.0, 60.0, mix_seed(seed, 300, 1), 0.0)),
-            ((2560, 1440), Pose((-4.0, 1.7, 2.0), -30.0, -30.0, 60.0, mix_seed(seed, 300, 2), 0.0)),
-            ((3840, 2160), Pose((1.0, 1.7, -3.0), 75.0, -35.0, 60.0, mix_seed(seed, 300, 3), 0.0))]
-    for (w, h), p in flat:
-        views.append(gbuffer_scene(seed, w, h, ts.sizes, ts.nlevels, p, nquads=200))
+    flat = [((1280, 720), Pose((0.0, 1.7, 0.0), 10.0, 35.0, 60.0, qs, 0.0), 6),
+            ((1920, 1080), Pose((3.0, 1.7, 5.0), 40.0, -20.0, 60.0, mix_seed(seed, 300, 1), 0.0), 200),
+            ((2560, 1440), Pose((-4.0, 1.7, 2.0), -30.0, -30.0, 60.0, mix_seed(seed, 300, 2), 0.0), 200),
+            ((3840, 2160), Pose((1.0, 1.7, -3.0), 75.0, -35.0, 60.0, mix_seed(seed, 300, 3), 0.0), 200)]
+    for (w, h), p, nq in flat:
+        views.append(gbuffer_scene(seed, w, h, sizes, nlevels, p, nquads=nq))
     for k, (yaw, pitch) in enumerate([(120.0, -30.0), (200.0, -40.0)]):
         base = np.array([2.0 * k, 1.7, -1.0 * k])
         right = np.array([np.cos(np.radians(yaw)), 0.0, -np.sin(np.radians(yaw))])
@@ -477,7 +492,7 @@ def config3_views(ts: TextureSet):
         for eye, sgn in enumerate((-1.0, 1.0)):
             cam = tuple(base + sgn * 0.032 * right)
             p = Pose(cam, yaw, pitch, 90.0, qseed, -sgn * 0.008)
-            views.append(gbuffer_scene(seed, 2064, 2208, ts.sizes, ts.nlevels, p, nquads=200))
+            views.append(gbuffer_scene(seed, 2064, 2208, sizes, nlevels, p, nquads=200))
     return views
 
 

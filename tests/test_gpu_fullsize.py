@@ -194,3 +194,28 @@ def test_4k_frame_reduced_mips(jt):
     assert _sampled_pixels(o, gb, out.cpu().numpy(), 50000, 6) <= 1
     ctx.graph_destroy(g)
     ctx.close()
+
+
+def test_batched_views_full_size(jt):
+    """The 8 batched views (720p looking up, 1080p, 1440p, 4K and two VR stereo pairs) in one
+    graph over the scene textures: the work list equals the oracle's union of the views'
+    needed sets, and sampled pixels of every view are within 1 LSB of the oracle."""
+    ts = synth.config2_textures()
+    views = synth.config3_views(ts)
+    ctx = jt.Context(0, max_cache_blocks=1 << 18)
+    ctx.upload_set(ts)
+    dv = [jt.DeviceGBuffer.from_host(v) for v in views]
+    outs = [torch.empty((v.height, v.width, 4), dtype=torch.uint8, device="cuda") for v in views]
+    g = ctx.frame_graph(list(zip(dv, outs)), jt.FILTER_BILINEAR)
+    ctx.graph_launch(g)
+    ctx.stats()
+    o = oracle.texset_from(ts)
+    flags = None
+    for v in views:
+        f = o.mark(v, 1)
+        flags = f if flags is None else np.maximum(flags, f)
+    np.testing.assert_array_equal(ctx.work_list(), o.compact(flags))
+    for i, (v, out) in enumerate(zip(views, outs)):
+        assert _sampled_pixels(o, v, out.cpu().numpy(), 10000, 20 + i) <= 1, f"view {i}"
+    ctx.graph_destroy(g)
+    ctx.close()
