@@ -11,7 +11,7 @@
 // between CTAs of one launch:
 //   k_tile_sums    every tile's (count, units) into one 64-bit word, count << 32 | units;
 //   k_scan_scatter every tile adds up its predecessors' words (up to ntiles / 256 loads
-//                  per thread, all independent, from L2), scans its own flags, writes slots
+//                  per thread, independent, four in flight, from L2), scans its own flags, writes slots
 //                  and work-list entries and clears the flags; the last tile writes the
 //                  totals into the frame state.
 // A single-pass scan with decoupled look-back was measured slower here: with a few
@@ -79,10 +79,18 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_scatter(const __grid_cons
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t ntiles = (a.n + kScanTile - 1) / kScanTile;
   for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    // predecessors' totals: thread i adds tiles i, i + 256, ... below this one
-    uint64_t pre = 0;
-    for (uint32_t t = tid; t < tile; t += kScanThreads) pre += a.tile_status[t];
-    pre = block_sum(pre, s_part);
+    // predecessors' totals: thread i adds tiles i, i + 256, ... below this one, four loads in
+    // flight at a time
+    uint64_t p0 = 0, p1 = 0, p2 = 0, p3 = 0;
+    uint32_t t = tid;
+    for (; t + 3 * kScanThreads < tile; t += 4 * kScanThreads) {
+      p0 += a.tile_status[t];
+      p1 += a.tile_status[t + kScanThreads];
+      p2 += a.tile_status[t + 2 * kScanThreads];
+      p3 += a.tile_status[t + 3 * kScanThreads];
+    }
+    for (; t < tile; t += kScanThreads) p0 += a.tile_status[t];
+    const uint64_t pre = block_sum((p0 + p1) + (p2 + p3), s_part);
     const uint32_t first = tile * kScanTile + tid * kScanPerThread;  // relative to gid_lo
     uint32_t w[4], cnt = 0, sum = 0;
     load_flags(a, first, w);
