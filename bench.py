@@ -41,7 +41,12 @@ WORKLOAD = "4K frame 3840x2160, 64 JPEG textures 1024-4096^2 Q50-95 4:2:0 full m
 # DRAM bytes (read + write) per launch of each pass's kernel in an ncu capture of this workload
 # with the current kernel code (the summaries under profiles/). A kernel changed since its
 # capture must be set back to None.
-NCU_TRAFFIC = {"mark": 93.81e6, "compact": None, "decode": 2.08e6, "colorize": None}
+NCU_TRAFFIC = {"mark": 93.88e6, "compact": 5.45e6, "decode": 2.08e6, "colorize": 133.97e6}
+# From one ncu capture of k_decode on the 4K frame in the decode shape the autotuner picks
+# (16 MCUs per warp, 12 warps per CTA, 1 CTA per SM): warp instructions executed, issue
+# slots busy (% of active cycles) and the frame's symbols; None until captured for the
+# current kernel code (see profiles/).
+NCU_DECODE = {"warp_instructions": 27287440, "issue_active_pct": 58.18, "symbols": 1257771}
 
 
 # kernels one frame launches: mark, the compaction's two passes, decode, colourise
@@ -66,6 +71,12 @@ def workload(compact: bool = False):
     ts = synth.config2_textures(compact=compact)
     gb = synth.config2_gbuffer(ts)
     return ts, gb
+
+
+def frame_symbols(ts, work: np.ndarray) -> int:
+    """Huffman symbols (DC, AC, ZRL, EOB) of the listed MCUs, as the encoder coded them."""
+    sym = np.concatenate([e.symbols.astype(np.int64) for _, _, e in ts.uploads()])
+    return int(sym[work.astype(np.int64)].sum())
 
 
 def compressed_bytes(ts, work: np.ndarray) -> float:
@@ -895,6 +906,18 @@ def run_gpu(args, rank, world, local_rank):
     mean = {k: float(np.mean(v)) for k, v in passes.items()}
     npx = gb.width * gb.height
     cbytes = compressed_bytes(ts, work)
+    symbols = frame_symbols(ts, work)
+    dec_ms = mean["decode"]
+    decode_roofline = {
+        "bound": "issue", "kernel": "decode", "symbols_per_frame": symbols,
+        "symbols_per_s": symbols / (dec_ms * 1e-3), "ns_per_symbol_per_gpu": dec_ms * 1e6 / symbols,
+        "instructions_per_symbol": (NCU_DECODE["warp_instructions"] * 32.0 / NCU_DECODE["symbols"]
+                                    if NCU_DECODE["warp_instructions"] else None),
+        "warp_instructions_per_symbol": (NCU_DECODE["warp_instructions"] / NCU_DECODE["symbols"]
+                                         if NCU_DECODE["warp_instructions"] else None),
+        "issue_active_pct": NCU_DECODE["issue_active_pct"],
+        "source": "symbols from the encoder's per-MCU counts over the work list; instructions and issue "
+                  "activity from one ncu capture of k_decode (profiles/)"}
     alg = {  # algorithmic HBM bytes per launch
         "mark": 11.0 * npx,
         "compact": float(st["total_blocks"]) + 8.0 * nblocks,
@@ -923,6 +946,7 @@ def run_gpu(args, rank, world, local_rank):
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(dom), "peak_kind": peak_kind,
                          "algorithmic_bytes": alg[dom]},
+            "decode_roofline": decode_roofline,
             "frame_roofline": {"achieved": sum(alg.values()) / (frame_ms * 1e-3) / 1e9, "unit": "GB/s",
                                "frac": sum(alg.values()) / (frame_ms * 1e-3) / 1e9 / peak},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

@@ -66,6 +66,7 @@ def lib():
         L.syn_jpeg_du_count.restype = ctypes.c_int64
         L.syn_jpeg_du_count.argtypes = [P]
         L.syn_jpeg_du_copy.argtypes = [P, P]
+        L.syn_jpeg_symbols_copy.argtypes = [P, P]
         L.syn_jpeg_compact_copy.argtypes = [P, P, P, P, P]
         L.syn_gbuffer_affine.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                          ctypes.c_int, P, P, P]
@@ -180,6 +181,7 @@ class Encoded:
     qcoef: np.ndarray | None = None  # int16 [nmcu, ndu, 64] natural order
     compact: Compact | None = None  # the paper's compact form (when asked for)
     du_offsets: np.ndarray | None = None  # uint16 [nmcu, ndu - 1]: data-unit starts within each MCU
+    symbols: np.ndarray | None = None  # uint16 [nmcu]: Huffman symbols (DC, AC, ZRL, EOB) per MCU
 
     @property
     def nmcu(self) -> int:
@@ -225,10 +227,12 @@ def _collect(h, quality, keep, compact=False) -> Encoded:
         cp = _collect_compact(h) if compact else None
         du = np.empty(int(L.syn_jpeg_du_count(h)), np.uint16)
         L.syn_jpeg_du_copy(h, _p(du))
+        sym = np.empty(mx * my, np.uint16)
+        L.syn_jpeg_symbols_copy(h, _p(sym))
     finally:
         L.syn_jpeg_free(h)
     return Encoded(w, hh, samp, mx, my, quality, jfif, scan, nbits, index, qt, bits, vals, qc, cp,
-                   du.reshape(mx * my, ndu - 1))
+                   du.reshape(mx * my, ndu - 1), sym)
 
 
 def encode(rgb: np.ndarray, quality: int, sampling: int = 420, keep_coefs: bool = False,

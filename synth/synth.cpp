@@ -342,11 +342,15 @@ struct Encoded {
   Compact compact;
   // start bit of data units 1..ndu-1 of each MCU relative to the MCU's first bit
   std::vector<uint16_t> du_offsets;  // [mcu][ndu - 1]
+  // Huffman symbols the standard stream codes per MCU: DC categories, AC (run, size)
+  // values, ZRL and EOB codes (a property of the input, for issue-rate accounting)
+  std::vector<uint16_t> symbols;  // [mcu]
   int status = 0;
 };
 
 // Writes one data unit of quantised coefficients (natural order) to the standard stream bw
 // and to the compact stream cw, which leaves out the DC difference when dc_absolute.
+// Returns the number of Huffman symbols of the standard stream, or -1.
 int encode_du(BitWriter& bw, BitWriter& cw, bool dc_absolute, uint64_t& dc_removed, const int16_t* q, int& pred,
               const HuffEnc& dc, const HuffEnc& ac) {
   auto put = [&](uint32_t v, int n) {
@@ -359,6 +363,7 @@ int encode_du(BitWriter& bw, BitWriter& cw, bool dc_absolute, uint64_t& dc_remov
   if (s > 11 || dc.len[s] == 0) return -1;
   bw.put(dc.code[s], dc.len[s]);
   bw.put(magnitude_bits(diff, s), s);
+  int nsym = 1;
   if (dc_absolute) {
     dc_removed += (uint64_t)(dc.len[s] + s);
   } else {
@@ -375,6 +380,7 @@ int encode_du(BitWriter& bw, BitWriter& cw, bool dc_absolute, uint64_t& dc_remov
     while (run > 15) {
       put(ac.code[0xF0], ac.len[0xF0]);
       run -= 16;
+      ++nsym;
     }
     int sz = category(v);
     if (sz > 10) return -1;
@@ -383,9 +389,13 @@ int encode_du(BitWriter& bw, BitWriter& cw, bool dc_absolute, uint64_t& dc_remov
     put(ac.code[sym], ac.len[sym]);
     put(magnitude_bits(v, sz), sz);
     run = 0;
+    ++nsym;
   }
-  if (run > 0) put(ac.code[0x00], ac.len[0x00]);
-  return 0;
+  if (run > 0) {
+    put(ac.code[0x00], ac.len[0x00]);
+    ++nsym;
+  }
+  return nsym;
 }
 
 void put_bits(std::vector<uint32_t>& a, uint64_t at, uint32_t v, int n) {
@@ -415,6 +425,7 @@ void entropy_and_container(Encoded& e, const int16_t* qcoef) {
   int pred[3] = {0, 0, 0};
   e.index.resize(nmcu);
   e.du_offsets.assign((size_t)nmcu * (ndu - 1), 0);
+  e.symbols.assign((size_t)nmcu, 0);
   for (int m = 0; m < nmcu; ++m) {
     BlockIndex bi;
     bi.bit_offset = (uint32_t)bw.nbits;
@@ -427,6 +438,7 @@ void entropy_and_container(Encoded& e, const int16_t* qcoef) {
       C.status = -1;
     else
       C.rel[(m / 9) * 8 + m % 9 - 1] = (uint16_t)(byte - C.abs[m / 9]);
+    uint32_t nsym = 0;
     for (int d = 0; d < ndu; ++d) {
       int comp = d < ndu - 2 ? 0 : (d == ndu - 2 ? 1 : 2);
       int tab = comp == 0 ? 0 : 1;
@@ -441,11 +453,14 @@ void entropy_and_container(Encoded& e, const int16_t* qcoef) {
         if (q[0] < -2048 || q[0] > 2047) C.status = -1;
         put_bits(C.dc, (uint64_t)m * 36 + 12 * comp, (uint32_t)q[0] & 0xFFFu, 12);
       }
-      if (encode_du(bw, cw, absolute, C.dc_bits_removed, q, pred[comp], enc[tab * 2], enc[tab * 2 + 1]) != 0) {
+      const int ns = encode_du(bw, cw, absolute, C.dc_bits_removed, q, pred[comp], enc[tab * 2], enc[tab * 2 + 1]);
+      if (ns < 0) {
         e.status = -2;
         return;
       }
+      nsym += (uint32_t)ns;
     }
+    e.symbols[m] = (uint16_t)nsym;
     C.pad_bits += cw.nacc ? (uint64_t)(8 - cw.nacc) : 0u;
     cw.flush_ones();
   }
@@ -833,6 +848,10 @@ void syn_jpeg_compact_copy(void* hnd, uint8_t* scan, uint32_t* abs, uint16_t* re
 
 // Data-unit start offsets: [mcu][ndu - 1] uint16 (bits from the MCU's first bit).
 int64_t syn_jpeg_du_count(void* hnd) { return (int64_t) static_cast<Encoded*>(hnd)->du_offsets.size(); }
+void syn_jpeg_symbols_copy(void* hnd, uint16_t* out) {
+  const Encoded* e = static_cast<Encoded*>(hnd);
+  std::memcpy(out, e->symbols.data(), e->symbols.size() * 2);
+}
 void syn_jpeg_du_copy(void* hnd, uint16_t* out) {
   const Encoded* e = static_cast<Encoded*>(hnd);
   std::memcpy(out, e->du_offsets.data(), e->du_offsets.size() * 2);
