@@ -5,15 +5,26 @@
 //
 // The paper keys a GPU hash map by a packed 32-bit MCU key. Our keys are the dense global
 // MCU ids (gids, one range per uploaded level), so the map is a direct array resident[gid]
-// (block index or kNone), with its inverse block_gid[block] and a stack of free blocks.
+// (a block index), valid where the gid's bit in the residency bitmap is set. Free blocks sit
+// in a ring: positions [head, head + free_count) modulo the block count.
 //
-// Per frame, after the mark pass has set flags[gid] (cache units needed, 0 = not needed):
-//   k_cache_evict  every resident block whose gid is not flagged returns to the free stack
-//   k_cache_alloc  every flagged gid: if resident, its slot is its block; else it takes a
-//                  free block and joins the decode work list. Flags are cleared.
-// The decode and colourise passes then run unchanged on the work list and slot map.
+// Per frame, after the mark pass has set flags[gid] (cache units needed, 0 = not needed), ONE
+// launch updates the cache. Each thread owns 16 gids (16 flag bytes and a 16-bit word of the
+// bitmap), so the decisions for one gid never race:
+//   flagged and resident      its slot is its block (a hit);
+//   flagged, not resident     it takes the next free block of the ring and joins the work
+//                             list (a miss);
+//   resident, not flagged     its block goes back to the ring, behind the blocks that were
+//                             free when the frame began (an eviction).
+// Misses take blocks that were free at the start of the frame; evictions are pushed behind
+// them, so the two never touch the same ring entry. Misses beyond the free blocks are
+// deferred: the last CTA to finish (a completion counter) hands them the blocks this frame
+// evicted, then moves the ring's head, writes the frame's totals and resets the counters for
+// the next frame. The frame therefore fits whenever its needed set fits in the cache, as with
+// an evict-then-allocate order, without a second launch. The flags are cleared on the way.
 // Work-list order and block numbers depend on atomic order (the decoded tiles and pixels do
-// not); a frame that needs more blocks than are free sets JT_DEVERR_CAPACITY.
+// not); a frame that needs more blocks than the cache holds sets JT_DEVERR_CAPACITY, and its
+// MCUs that found no block are neither decoded nor given a slot outside the cache.
 #include <cuda_runtime.h>
 
 #include "jt_internal.cuh"
@@ -21,33 +32,18 @@
 namespace jt {
 namespace {
 
-constexpr uint32_t kNone = 0xFFFFFFFFu;
-
-__global__ void k_cache_evict(const __grid_constant__ CacheArgs a) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    a.state->count = 0;
-    a.state->decode_next = 0;
-    a.cs->taken = 0;
-    a.cs->visible = 0;
-  }
-  uint32_t evicted = 0;
-  for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < a.nblocks; b += gridDim.x * blockDim.x) {
-    const uint32_t g = a.block_gid[b];
-    if (g != kNone && a.flags[g] == 0) {
-      a.resident[g] = kNone;
-      a.block_gid[b] = kNone;
-      a.free_list[atomicAdd(&a.cs->free_count, 1u)] = b;
-      ++evicted;
-    }
-  }
-  if (evicted) atomicAdd(&a.cs->evicted, evicted);
+// Ring entry at position p < 2 nblocks (every position used is head plus less than nblocks).
+__device__ __forceinline__ uint32_t* ring_at(const CacheArgs& a, uint32_t p) {
+  return a.ring + (p >= a.nblocks ? p - a.nblocks : p);
 }
 
-__global__ void k_cache_alloc(const __grid_constant__ CacheArgs a) {
-  const uint32_t free_now = a.cs->free_count;  // after the eviction pass (stream order)
+__global__ void __launch_bounds__(kCacheThreads) k_cache_update(const __grid_constant__ CacheArgs a) {
+  __shared__ bool s_last;
+  const uint32_t head = a.cs->head, free0 = a.cs->free_count;  // fixed until the last CTA
   uint32_t visible = 0;
-  bool over = false;
-  for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w * 16 < a.n; w += gridDim.x * blockDim.x) {
+  bool over = false, wrote = false;
+  const uint32_t nw = (a.n + 15) / 16;
+  for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += gridDim.x * blockDim.x) {
     const uint32_t first = w * 16;
     uint4 v;
     if (first + 16 <= a.n) {
@@ -57,54 +53,133 @@ __global__ void k_cache_alloc(const __grid_constant__ CacheArgs a) {
       for (uint32_t i = 0; first + i < a.n; ++i) t[i >> 2] |= (uint32_t)a.flags[first + i] << (8 * (i & 3));
       v = make_uint4(t[0], t[1], t[2], t[3]);
     }
-    if ((v.x | v.y | v.z | v.w) == 0) continue;
+    const uint32_t rb = a.resbits[w];
+    const bool any_flag = (v.x | v.y | v.z | v.w) != 0;
+    if (!any_flag && rb == 0) continue;
+    // masks over the 16 gids: flagged, hit, miss, eviction
+    uint32_t fm = 0;
     const uint32_t words[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      if (((words[i >> 2] >> (8 * (i & 3))) & 255) == 0) continue;
-      const uint32_t g = first + i;
-      ++visible;
-      uint32_t b = a.resident[g];
-      if (b == kNone) {
-        const uint32_t pos = atomicAdd(&a.cs->taken, 1u);
-        if (pos >= free_now) {
-          over = true;
-          continue;
-        }
-        b = a.free_list[free_now - 1 - pos];
-        a.resident[g] = b;
-        a.block_gid[b] = g;
-        const uint32_t item = atomicAdd(&a.state->count, 1u);
-        if (item < a.work_cap)
-          a.work[item] = g;
-        else
-          over = true;
-      }
-      a.slot[g] = b * 4;  // a block is 4 cache units
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t nz = __vcmpne4(words[q], 0u);
+      fm |= (((nz >> 7) & 1u) | ((nz >> 14) & 2u) | ((nz >> 21) & 4u) | ((nz >> 28) & 8u)) << (4 * q);
     }
-    // clear for the next frame
-    if (first + 16 <= a.n)
-      reinterpret_cast<uint4*>(a.flags)[w] = make_uint4(0, 0, 0, 0);
-    else
-      for (uint32_t i = 0; first + i < a.n; ++i) a.flags[first + i] = 0;
+    const uint32_t hit = fm & rb, miss = fm & ~rb, evm = rb & ~fm;
+    visible += __popc(fm);
+    // the 16 gids' blocks in one go (resident is padded to whole groups of 16)
+    uint32_t res[16];
+    if (rb) {
+      const uint4* rp = reinterpret_cast<const uint4*>(a.resident + first);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint4 r4 = rp[q];
+        res[4 * q] = r4.x;
+        res[4 * q + 1] = r4.y;
+        res[4 * q + 2] = r4.z;
+        res[4 * q + 3] = r4.w;
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 16; ++q) res[q] = 0;
+    }
+    // one counter update per thread and kind: misses take ring positions pos0, pos0 + 1, ...
+    // (the first ones, below free0, at once, at the same places of the work list; the rest
+    // are deferred), evictions e0, e0 + 1, ...
+    const uint32_t nmiss = __popc(miss), nev = __popc(evm);
+    const uint32_t pos0 = nmiss ? atomicAdd(&a.cs->taken, nmiss) : 0u;
+    const uint32_t e0 = nev ? atomicAdd(&a.cs->evict_n, nev) : 0u;
+    const uint32_t nnow = pos0 < free0 ? min(nmiss, free0 - pos0) : 0u;
+    wrote = true;
+    uint32_t nrb = rb & ~evm;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const uint32_t bit = 1u << i, g = first + i;
+      if (hit & bit) a.slot[g] = res[i] * 4;  // a block is 4 cache units
+      if (miss & bit) {
+        const uint32_t rank = __popc(miss & (bit - 1u)), pos = pos0 + rank;
+        if (rank < nnow) {
+          const uint32_t b = *ring_at(a, head + pos);
+          a.resident[g] = b;
+          a.slot[g] = b * 4;
+          nrb |= bit;
+          if (pos < a.work_cap)
+            a.work[pos] = g;
+          else
+            over = true;
+        } else if (pos - free0 < a.nblocks) {
+          a.deferred[pos - free0] = g;  // the last CTA gives it a block evicted by this update
+        } else {
+          a.slot[g] = 0;
+          over = true;
+        }
+      }
+      if (evm & bit) *ring_at(a, head + free0 + e0 + __popc(evm & (bit - 1u))) = res[i];
+    }
+    if (nrb != rb) a.resbits[w] = (uint16_t)nrb;
+    if (any_flag) {  // clear for the next frame
+      if (first + 16 <= a.n)
+        reinterpret_cast<uint4*>(a.flags)[w] = make_uint4(0, 0, 0, 0);
+      else
+        for (uint32_t i = 0; first + i < a.n; ++i) a.flags[first + i] = 0;
+    }
   }
-  if (visible) atomicAdd(&a.cs->visible, visible);
-  if (over) atomicOr(&a.state->err, JT_DEVERR_CAPACITY);
-}
+  visible = __reduce_add_sync(0xFFFFFFFFu, visible);
+  if ((threadIdx.x & 31) == 0 && visible) atomicAdd(&a.cs->visible_acc, visible);
+  if (__any_sync(0xFFFFFFFFu, over) && (threadIdx.x & 31) == 0) atomicOr(&a.state->err, JT_DEVERR_CAPACITY);
 
-// Pops the blocks taken by the allocation pass off the free stack.
-__global__ void k_cache_commit(const __grid_constant__ CacheArgs a) {
-  const uint32_t taken = min(a.cs->taken, a.cs->free_count);
-  a.cs->free_count -= taken;
-  a.state->units = 4 * a.state->count;
+  // ---- the last CTA to finish: deferred misses, ring head, totals, counters ----
+  if (wrote || visible || over) __threadfence();  // this thread's writes before the count
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&a.cs->done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  volatile CacheState* cs = a.cs;
+  const uint32_t taken = cs->taken, ev = cs->evict_n, items = min(taken, free0);
+  const uint32_t nd = taken > free0 ? min(taken - free0, a.nblocks) : 0u;  // deferred misses stored
+  const uint32_t served = min(nd, ev);
+  bool dover = false;
+  for (uint32_t j = threadIdx.x; j < nd; j += blockDim.x) {
+    const uint32_t g = a.deferred[j];
+    if (j < served) {
+      const uint32_t b = *ring_at(a, head + free0 + j);
+      a.resident[g] = b;
+      a.slot[g] = b * 4;
+      atomicOr(&a.resbits32[g >> 5], 1u << (g & 31));
+      if (items + j < a.work_cap)
+        a.work[items + j] = g;
+      else
+        dover = true;
+    } else {
+      a.slot[g] = 0;
+      dover = true;
+    }
+  }
+  if (dover) atomicOr(&a.state->err, JT_DEVERR_CAPACITY);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const uint32_t popped = min(taken, free0) + served;  // ring entries handed out this frame
+    const uint32_t count = min(items + served, a.work_cap);
+    cs->head = head + popped >= a.nblocks ? head + popped - a.nblocks : head + popped;
+    cs->free_count = free0 + ev - popped;
+    cs->visible = cs->visible_acc;
+    cs->evicted += ev;
+    cs->taken = 0;
+    cs->evict_n = 0;
+    cs->visible_acc = 0;
+    cs->done = 0;
+    a.state->count = count;
+    a.state->units = 4 * count;
+    a.state->decode_next = 0;
+  }
 }
 
 }  // namespace
 
-void launch_cache_update(const CacheArgs& a, int grid, cudaStream_t s) {
-  k_cache_evict<<<grid, 256, 0, s>>>(a);
-  k_cache_alloc<<<grid, 256, 0, s>>>(a);
-  k_cache_commit<<<1, 1, 0, s>>>(a);
+void launch_cache_update(const CacheArgs& a, int max_grid, cudaStream_t s) {
+  const uint32_t nw = (a.n + 15) / 16;
+  const int grid = (int)std::max<uint32_t>(1, std::min<uint32_t>((nw + kCacheThreads - 1) / kCacheThreads, (uint32_t)max_grid));
+  k_cache_update<<<grid, kCacheThreads, 0, s>>>(a);
 }
 
 }  // namespace jt

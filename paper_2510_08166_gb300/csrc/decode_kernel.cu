@@ -6,10 +6,12 @@
 // Sec. 5.2, is prior art here):
 //  * persistent grid; each warp takes batches of m_eff work items (one per lane), m_eff the
 //    smallest power of two up to M (4, 8, 16 or 32, the buffer width) that covers the list
-//    in one batch per warp: a short list (a frame under motion with a warm block cache)
-//    runs one MCU per warp, spread first over the SMs, and a long one fills the lanes. The
-//    first batch of each warp is fixed by its rank, later ones come from a device counter,
-//    so uneven MCU sizes balance dynamically and the count never goes to the host;
+//    in one batch per warp, and a long list fills the lanes. A short list (a frame under
+//    motion with a warm block cache: at most kWarpMcuMax MCUs per warp) goes one MCU at a
+//    time, each decoded by the whole warp (decode_mcu_warp, mcu_warp_pixels), spread first
+//    over the SMs. The first batch of each warp is fixed by its rank, later ones come from a
+//    device counter, so uneven MCU sizes balance dynamically and the count never goes to
+//    the host;
 //  * entropy phase: lane m < m_eff runs MCU m's serial entropy chain over all its data
 //    units from a byte-swapped copy of its words staged in shared memory (a per-warp pool
 //    shared out by a prefix sum). Per symbol: one funnel shift of a two-word window, one
@@ -340,6 +342,172 @@ __device__ __forceinline__ uint32_t decode_unit(const Words& W, uint32_t bit0, c
   return (bad || k < 64) ? 0xFFFFFFFFu : widx * 32 + pos;
 }
 
+// ---- one MCU decoded by a whole warp (short work lists) ----
+//
+// A warp that holds a single MCU would run its serial chain on one lane, and every step of
+// that chain (window cut, LUT read, length, position, coefficient store) waits for the one
+// before. Here the 32 lanes instead decode, for every bit offset of a 256-bit window of the
+// stream, the AC symbol that would start there (entries independent of each other, 8 per
+// lane, loads issued before any store), and the chain that remains is one shared-memory read
+// and one add per symbol: the entry at the current position holds the byte offset of the
+// entry after its symbol (code + value bits), its run and its value. All lanes follow the chain in
+// step, so its state is warp-uniform; symbol s of a data unit is kept in registers by lane
+// s mod 32, and the coefficients are stored once the data unit ends (a store on the chain
+// would hold the next table read behind it). The DC symbol of each data unit is decoded
+// directly on the chain. The window is rebuilt when the position leaves it or the component
+// class (luma, chroma) changes.
+constexpr int kWinBits = 256;    // window of symbol entries, bits
+constexpr int kWarpMcuMax = 4;   // lists of at most this many MCUs per warp are decoded MCU by MCU
+
+// LUT entry of the code at the top of w in table ti (0 when it has none).
+template <bool SH>
+__device__ __forceinline__ uint32_t lut_entry(const Tables<SH>& T, uint32_t ti, uint32_t f, uint32_t n, uint32_t w) {
+  const uint32_t b = T.base(ti);
+  const uint32_t e1 = T.lut_at(b, w >> (32 - kLutBits));
+  const uint32_t j = (w >> 16) - f;
+  const uint32_t e2 = T.lut2_at(b, min(j, (uint32_t)kLut2Size - 1u));
+  return (e1 & 31u) ? e1 : (j < n ? e2 : 0u);
+}
+
+// Signed value of the sz bits after the l-bit code at the top of w (T.81 EXTEND).
+__device__ __forceinline__ int symbol_value(uint32_t w, uint32_t l, uint32_t sz) {
+  const uint32_t tw = w << l;
+  return (int)__funnelshift_l(tw, 0u, sz) + (int)(~((int)tw >> 31) & (int)(1u - (1u << sz)));
+}
+
+// Window entry (two words) of symbol entry e read at w, window offset o. First word: byte
+// offset in the window of the entry after the symbol, clamped to the last entry (bits 0-10),
+// run (11-16), value bits present (17), the next symbol starts past the window (18), the next
+// symbol's window offset (19-27); 0 for no symbol (an invalid code), never 0 otherwise (the
+// next offset is at least 1). Second word: the value.
+__device__ __forceinline__ uint2 win_entry(uint32_t e, uint32_t w, uint32_t o) {
+  const uint32_t l = e & 31u, sz = (e >> 5) & 15u, r = e >> 9, nx = o + l + sz;
+  const uint32_t x = (min(nx, (uint32_t)kWinBits - 1u) * 8u) | (r << 11) | (sz ? 1u << 17 : 0u) |
+                     (nx >= (uint32_t)kWinBits ? 1u << 18 : 0u) | (nx << 19);
+  return e ? make_uint2(x, (uint32_t)symbol_value(w, l, sz)) : make_uint2(0u, 0u);
+}
+
+__device__ __forceinline__ uint2 lds_u64(uint32_t saddr) {
+  uint2 v;
+  asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(saddr));
+  return v;
+}
+
+// Stream words of a warp-decoded MCU that is staged whole (every word its symbols can reach
+// is in shared memory): reads need no bounds branch; an index past the stage (only an invalid
+// coding gets there) is clamped into the stage.
+struct StagedWords {
+  uint32_t st, last;  // shared address of the staged words, index of the last one
+  __device__ __forceinline__ uint32_t operator()(uint32_t i) const { return lds_u32(st + 4 * min(i, last)); }
+};
+
+// The 32 stream bits from bit position p on (relative to the first staged word).
+template <class WS>
+__device__ __forceinline__ uint32_t bits32w(const WS& W, uint32_t p) {
+  return __funnelshift_l(W((p >> 5) + 1), W(p >> 5), p & 31u);
+}
+
+// Entropy-decodes all data units of one MCU with the whole warp (every lane calls it with the
+// same arguments). Coefficients go to cc[du * 64 + k] (contiguous, zig-zag k; zero on entry);
+// tbl_sa is the 8-byte aligned shared address of 2 kWinBits words of scratch. Same results and the same
+// invalid codings as decode_mcu. Returns the bit position after the MCU relative to the first
+// staged word, or 0xFFFFFFFF on an invalid coding.
+template <bool SH, bool CPT, class WS>
+__device__ __forceinline__ uint32_t decode_mcu_warp(const WS& W, uint32_t bit0, const Tables<SH>& T, int ndu,
+                                                    int p0, int p1, int p2, int16_t* cc, uint32_t tbl_sa,
+                                                    int lane) {
+  const uint32_t F0 = T.first16(0), F1 = T.first16(1), F2 = T.first16(2), F3 = T.first16(3);
+  const uint32_t N0 = T.n2(0), N1 = T.n2(1), N2 = T.n2(2), N3 = T.n2(3);
+  int pred0 = p0, pred1 = p1, pred2 = p2;
+  uint32_t pos = bit0, wb = 0;
+  int wcls = -1;  // component class of the window's entries (none yet)
+  bool bad = false;
+#pragma unroll 1
+  for (int du = 0; du < ndu && !bad; ++du) {
+    const int comp = du < ndu - 2 ? 0 : (du == ndu - 2 ? 1 : 2);
+    const int cls = comp ? 1 : 0;
+    const uint32_t tdc = cls ? 2u : 0u, tac = tdc | 1u;
+    const uint32_t fdc = cls ? F2 : F0, ndc = cls ? N2 : N0, fac = cls ? F3 : F1, nac = cls ? N3 : N1;
+    int16_t* cd = cc + du * 64;
+    int pv = comp == 0 ? pred0 : (comp == 1 ? pred1 : pred2);
+    if (!(CPT && (du == 0 || comp != 0))) {  // the compact form stores these DCs, no difference
+      const uint32_t w = bits32w(W, pos);
+      uint32_t e = lut_entry(T, tdc, fdc, ndc, w);
+      if (e == 0) e = walk_symbol(T.hs + tdc, w, true);
+      if (e == 0) {
+        bad = true;
+        break;
+      }
+      const uint32_t l = e & 31u, sz = (e >> 5) & 15u;
+      pv = (int16_t)(uint16_t)(pv + symbol_value(w, l, sz));  // DC values wrap modulo 2^16
+      pos += l + sz;
+    }
+    pred0 = comp == 0 ? pv : pred0;
+    pred1 = comp == 1 ? pv : pred1;
+    pred2 = comp == 2 ? pv : pred2;
+    // AC symbols: symbol s of the unit is kept by lane s % 32 as k << 16 | value (0: none)
+    uint32_t keep0 = 0, keep1 = 0;
+    int k = 1, s = 0, kst = 0;
+#pragma unroll 1
+    while (true) {
+      if (wcls != cls || pos - wb >= (uint32_t)kWinBits) {
+        // rebuild the window at pos: every lane's loads first, then its entries
+        __syncwarp();  // every lane has read the old window
+        wb = pos;
+        wcls = cls;
+        uint32_t w[kWinBits / 32], e[kWinBits / 32];
+#pragma unroll
+        for (int j = 0; j < kWinBits / 32; ++j) w[j] = bits32w(W, wb + (uint32_t)(lane + 32 * j));
+        bool none = false;
+#pragma unroll
+        for (int j = 0; j < kWinBits / 32; ++j) {
+          e[j] = lut_entry(T, tac, fac, nac, w[j]);
+          none |= e[j] == 0;
+        }
+        if (none) {  // codes without a LUT entry: the MAXCODE walk decodes or rejects them
+#pragma unroll
+          for (int j = 0; j < kWinBits / 32; ++j)
+            if (e[j] == 0) e[j] = walk_symbol(T.hs + tac, w[j], false);
+        }
+#pragma unroll
+        for (int j = 0; j < kWinBits / 32; ++j) {
+          const uint32_t o = (uint32_t)(lane + 32 * j);
+          const uint2 we = win_entry(e[j], w[j], o);
+          asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(tbl_sa + 8 * o), "r"(we.x), "r"(we.y));
+        }
+        __syncwarp();
+      }
+      // symbols while the position stays in the window: one branch per symbol, and the next
+      // entry's read goes out before this one is taken apart (a lone warp issues in order, so
+      // the work on an entry would otherwise add to the chain); a read past the window is
+      // clamped into it and dropped
+      uint2 ent = lds_u64(tbl_sa + 8 * (pos - wb));
+      uint32_t nofs = pos - wb;  // window offset of the next symbol
+      bool more;
+      do {
+        const uint2 nxt = lds_u64(tbl_sa + (ent.x & 2047u));
+        kst = k + (int)((ent.x >> 11) & 63u);
+        const bool val = (ent.x & (1u << 17)) != 0;  // a coefficient (value bits present)
+        const uint32_t kv = val ? ((uint32_t)kst << 16) | (ent.y & 0xFFFFu) : 0u;
+        keep0 = s == lane ? kv : keep0;
+        keep1 = s == lane + 32 ? kv : keep1;
+        bad |= ent.x == 0 || (val && kst > 63);
+        k = kst + 1;
+        ++s;
+        nofs = ent.x >> 19;
+        more = kst < 63 && !bad && (ent.x & (1u << 18)) == 0;
+        ent = nxt;
+      } while (more);
+      pos = wb + nofs;
+      if (kst >= 63 || bad) break;
+    }
+    if (lane == 0) cd[0] = (int16_t)pv;
+    if (keep0 != 0 && (keep0 >> 16) <= 63u) cd[keep0 >> 16] = (int16_t)(keep0 & 0xFFFFu);
+    if (keep1 != 0 && (keep1 >> 16) <= 63u) cd[keep1 >> 16] = (int16_t)(keep1 & 0xFFFFu);
+  }
+  return bad ? 0xFFFFFFFFu : pos;
+}
+
 __device__ __forceinline__ uint32_t ycc_pixel(uint32_t Y, int ro, int go, int bo) {
   return clamp255((int)Y + ro) | (clamp255((int)Y + go) << 8) | (clamp255((int)Y + bo) << 16) | 0xFF000000u;
 }
@@ -453,6 +621,79 @@ __device__ __forceinline__ void idct_full(int16_t* blk, const uint16_t* Qd) {
   }
 }
 
+// IDCT and colour of one full-size MCU held by a whole warp (after decode_mcu_warp): the
+// column passes are shared out over the lanes as (data unit, column) pairs, the row passes as
+// (data unit, row) pairs, the tile as half rows of texels; same arithmetic as idct_full and
+// the per-MCU colour stores. cc: quantised coefficients [ndu][64] in zig-zag order; tmp
+// (16-byte aligned, [ndu][64] int16) and pix ([ndu][64] bytes) are scratch in natural order;
+// Q: the MCU's quantisation tables (luma, then chroma, zig-zag order); tile: its cache block.
+__device__ __forceinline__ void mcu_warp_pixels(const int16_t* cc, int16_t* tmp, uint8_t* pix, int ndu, bool s420,
+                                                const uint16_t* Q, uint8_t* tile, int lane) {
+  const int nluma = s420 ? 4 : 1;
+#pragma unroll 1
+  for (int q = lane; q < 8 * ndu; q += 32) {  // column u of data unit d, dequantised on load
+    const int d = q >> 3, u = q & 7;
+    const uint16_t* Qd = Q + (d < nluma ? 0 : 64);
+    int in[8], out[8];
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+      const int k = zz_pos(v, u);
+      in[v] = sat16(cc[d * 64 + k] * (int)__ldg(Qd + k));
+    }
+    idct8(in, out);
+#pragma unroll
+    for (int v = 0; v < 8; ++v) tmp[d * 64 + v * 8 + u] = (int16_t)sat16((out[v] + 256) >> 9);
+  }
+  __syncwarp();
+#pragma unroll 1
+  for (int q = lane; q < 8 * ndu; q += 32) {  // row y of data unit d
+    const int d = q >> 3, y = q & 7;
+    const uint4 r = *reinterpret_cast<const uint4*>(tmp + d * 64 + y * 8);
+    const uint32_t rw[4] = {r.x, r.y, r.z, r.w};
+    int in[8], out[8];
+#pragma unroll
+    for (int x = 0; x < 8; ++x) in[x] = (int16_t)(uint16_t)(rw[x >> 1] >> (16 * (x & 1)));
+    idct8(in, out);
+    uint32_t lo = 0, hi = 0;
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+      lo |= clamp255(((out[x] + (1 << 18)) >> 19) + 128) << (8 * x);
+      hi |= clamp255(((out[x + 4] + (1 << 18)) >> 19) + 128) << (8 * x);
+    }
+    *reinterpret_cast<uint2*>(pix + d * 64 + y * 8) = make_uint2(lo, hi);
+  }
+  __syncwarp();
+  if (s420) {  // 16 x 16 texels: lane = (row ty, half h), texels x = 8h .. 8h + 7
+    const int ty = lane >> 1, h = lane & 1;
+    const uint2 yv = *reinterpret_cast<const uint2*>(pix + ((ty >> 3) * 2 + h) * 64 + (ty & 7) * 8);
+    const uint32_t cbv = *reinterpret_cast<const uint32_t*>(pix + 4 * 64 + (ty >> 1) * 8 + 4 * h);
+    const uint32_t crv = *reinterpret_cast<const uint32_t*>(pix + 5 * 64 + (ty >> 1) * 8 + 4 * h);
+    uint32_t o[8];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {  // chroma sample c covers texels 2c, 2c + 1
+      int ro, go, bo;
+      chroma_offsets((cbv >> (8 * c)) & 255u, (crv >> (8 * c)) & 255u, ro, go, bo);
+      const uint32_t yw = c < 2 ? yv.x : yv.y;
+      o[2 * c] = ycc_pixel((yw >> (16 * (c & 1))) & 255u, ro, go, bo);
+      o[2 * c + 1] = ycc_pixel((yw >> (16 * (c & 1) + 8)) & 255u, ro, go, bo);
+    }
+    uint4* dst = reinterpret_cast<uint4*>(tile + (ty * 16 + 8 * h) * 4);
+    dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
+    dst[1] = make_uint4(o[4], o[5], o[6], o[7]);
+  } else {  // 8 x 8 texels, Y Cb Cr data units 0 1 2: lane = (row ty, texels x0, x0 + 1)
+    const int ty = lane >> 2, x0 = (lane & 3) * 2;
+    uint32_t o[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int i = ty * 8 + x0 + e;
+      int ro, go, bo;
+      chroma_offsets(pix[64 + i], pix[128 + i], ro, go, bo);
+      o[e] = ycc_pixel(pix[i], ro, go, bo);
+    }
+    *reinterpret_cast<uint2*>(tile + (ty * 8 + x0) * 4) = make_uint2(o[0], o[1]);
+  }
+}
+
 // UNITS: the variant for contexts with data-unit starts. Each MCU of a batch then takes six
 // lanes, lane 6m + d decoding data unit d of MCU m from its own start (levels without
 // starts are decoded whole by lane 6m); MCUs per batch are at most 4.
@@ -482,8 +723,11 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
   // warp, so short lists spread one MCU per warp (latency) and long ones fill the lanes
   const uint32_t total_warps = gridDim.x * (blockDim.x >> 5);
   const uint32_t per_warp = (count + total_warps - 1) / total_warps;
+  // (up to kWarpMcuMax MCUs per warp they go one at a time, each decoded by the whole warp:
+  // a lone lane's chain is several times longer than the warp's)
   int lmeff = 0;
-  while ((1u << lmeff) < per_warp && (1 << lmeff) < kMaxBatch) ++lmeff;
+  if (UNITS || M < 4 || per_warp > (uint32_t)kWarpMcuMax)
+    while ((1u << lmeff) < per_warp && (1 << lmeff) < kMaxBatch) ++lmeff;
   const int meff = 1 << lmeff;
   // first batch by rank, interleaved over the CTAs (one warp per SM first), then dynamic
   const uint32_t wrank = (uint32_t)warp * gridDim.x + blockIdx.x;
@@ -623,7 +867,62 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
       // a data unit must end at or before the next one's start
       if (end == 0xFFFFFFFFu || (uint64_t)w0 * 32 + end > endbit) any_bad = true;
     }
-    if (act && !unit) {
+    bool warp_done = false;  // the MCU's tile was written by the whole warp
+    if (!UNITS && M >= 4 && meff == 1) {
+      // one MCU per warp: the whole warp runs lane 0's chain (coefficients contiguous in
+      // the buffer's first 768 B, the window's entries in the next 1 KiB); a full-size tile
+      // is then transformed and stored by the whole warp, any other is scattered into lane
+      // 0's column for the per-lane passes
+      if (__shfl_sync(0xFFFFFFFFu, act ? 1 : 0, 0)) {
+        const Words W{(uint32_t)__cvta_generic_to_shared(stage), __shfl_sync(0xFFFFFFFFu, nst, 0),
+                      reinterpret_cast<const uint32_t*>(
+                          __shfl_sync(0xFFFFFFFFu, reinterpret_cast<unsigned long long>(words + w0), 0)),
+                      __shfl_sync(0xFFFFFFFFu, nwords > w0 ? nwords - w0 : 0u, 0)};
+        const HuffTable* hw = reinterpret_cast<const HuffTable*>(
+            __shfl_sync(0xFFFFFFFFu, reinterpret_cast<unsigned long long>(hs), 0));
+        const uint32_t b0 = __shfl_sync(0xFFFFFFFFu, bitpos - w0 * 32, 0);
+        const int nd = __shfl_sync(0xFFFFFFFFu, ndu, 0);
+        const bool cw = __shfl_sync(0xFFFFFFFFu, cpt ? 1 : 0, 0) != 0;
+        const int q0 = __shfl_sync(0xFFFFFFFFu, (int)pr0, 0), q1 = __shfl_sync(0xFFFFFFFFu, (int)pr1, 0),
+                  q2 = __shfl_sync(0xFFFFFFFFu, (int)pr2, 0);
+        const uint32_t tsa = (uint32_t)__cvta_generic_to_shared(coef) + 768u;
+        const Tables<true> TS{hw, (uint32_t)__cvta_generic_to_shared(sh->t)};
+        const Tables<false> TG{hw, 0u};
+        // staged whole: every word up to the next MCU's start plus the look-ahead
+        const uint32_t nst0 = __shfl_sync(0xFFFFFFFFu, nst, 0);
+        const bool whole = nst0 > 0 && nst0 >= __shfl_sync(0xFFFFFFFFu, want, 0);
+        const StagedWords SW{W.st, nst0 - 1};
+        uint32_t end;
+        if (whole && hw == sh->t)
+          end = cw ? decode_mcu_warp<true, true>(SW, b0, TS, nd, q0, q1, q2, coef, tsa, lane)
+                   : decode_mcu_warp<true, false>(SW, b0, TS, nd, q0, q1, q2, coef, tsa, lane);
+        else if (whole)
+          end = cw ? decode_mcu_warp<false, true>(SW, b0, TG, nd, q0, q1, q2, coef, tsa, lane)
+                   : decode_mcu_warp<false, false>(SW, b0, TG, nd, q0, q1, q2, coef, tsa, lane);
+        else if (hw == sh->t)
+          end = cw ? decode_mcu_warp<true, true>(W, b0, TS, nd, q0, q1, q2, coef, tsa, lane)
+                   : decode_mcu_warp<true, false>(W, b0, TS, nd, q0, q1, q2, coef, tsa, lane);
+        else
+          end = cw ? decode_mcu_warp<false, true>(W, b0, TG, nd, q0, q1, q2, coef, tsa, lane)
+                   : decode_mcu_warp<false, false>(W, b0, TG, nd, q0, q1, q2, coef, tsa, lane);
+        if (lane == 0 && (end == 0xFFFFFFFFu || (uint64_t)w0 * 32 + end > (cpt ? endbit : nbits))) any_bad = true;
+        __syncwarp();
+        if (__shfl_sync(0xFFFFFFFFu, (red == 0 && store) ? 1 : 0, 0)) {
+          const bool s4 = __shfl_sync(0xFFFFFFFFu, s420 ? 1 : 0, 0) != 0;
+          const uint32_t qs0 = __shfl_sync(0xFFFFFFFFu, qs, 0), off0 = __shfl_sync(0xFFFFFFFFu, off, 0);
+          mcu_warp_pixels(coef, coef + 384, reinterpret_cast<uint8_t*>(coef) + 1536, nd, s4,
+                          a.quant + (size_t)qs0 * 128, a.cache + (size_t)off0 * kUnitBytes, lane);
+          warp_done = true;
+        } else {
+          int16_t v[12];
+#pragma unroll
+          for (int i = 0; i < 12; ++i) v[i] = coef[lane + 32 * i];
+          __syncwarp();
+#pragma unroll
+          for (int i = 0; i < 12; ++i) coef[(lane + 32 * i) * M] = v[i];
+        }
+      }
+    } else if (act && !unit) {
       const Words W{(uint32_t)__cvta_generic_to_shared(stage + sbeg), nst, words + w0,
                     nwords > w0 ? nwords - w0 : 0u};
       const Tables<true> TS{hs, (uint32_t)__cvta_generic_to_shared(sh->t)};
@@ -664,7 +963,7 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
         (act ? 1u : 0u) | (s420 ? 2u : 0u) | ((uint32_t)red << 2) | (store ? 16u : 0u) | (qs << 8);
     __syncwarp();  // every lane's coefficients are visible to the warp
 #pragma unroll 1
-    for (int r0 = 0; r0 < 6 * meff; r0 += 32) {
+    for (int r0 = 0; r0 < (warp_done ? 0 : 6 * meff); r0 += 32) {
       const int q = r0 + lane;
       const int d = q >> lmeff, m = q & (meff - 1);
       const uint32_t im = __shfl_sync(0xFFFFFFFFu, minfo, UNITS ? 6 * m : m);
@@ -688,7 +987,7 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
     // (MCU m, column group c2 of 4 texels), 16-byte stores; 4:4:4 and reduced tiles are
     // written by their own lane ----
 #pragma unroll 1
-    for (int r0 = 0; r0 < 4 * meff; r0 += 32) {
+    for (int r0 = 0; r0 < (warp_done ? 0 : 4 * meff); r0 += 32) {
       const int q = r0 + lane;
       const int m = (q >> 2) & (meff - 1), c2 = q & 3;
       const uint32_t im = __shfl_sync(0xFFFFFFFFu, minfo, UNITS ? 6 * m : m);
@@ -718,9 +1017,9 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
         }
       }
     }
-    if (act && ld == 0 && store && red != 0)
+    if (!warp_done && act && ld == 0 && store && red != 0)
       colour_reduced<M>(col, s420, red, reinterpret_cast<uint32_t*>(a.cache + (size_t)off * kUnitBytes));
-    if (act && ld == 0 && store && red == 0 && !s420) {  // 4:4:4, 8x8 texels, Y Cb Cr data units 0 1 2
+    if (!warp_done && act && ld == 0 && store && red == 0 && !s420) {  // 4:4:4, 8x8 texels, Y Cb Cr data units 0 1 2
       uint8_t* tile = a.cache + (size_t)off * kUnitBytes;
 #pragma unroll 1
       for (int ty = 0; ty < 8; ++ty) {

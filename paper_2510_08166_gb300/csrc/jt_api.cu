@@ -72,8 +72,9 @@ struct jt_ctx {
   bool persistent = false;
   bool unit_mode = false;  // some level has data-unit starts
   uint32_t* resident = nullptr;   // [ngid]
-  uint32_t* block_gid = nullptr;  // [nblocks]
-  uint32_t* free_list = nullptr;  // [nblocks]
+  uint32_t* resbits = nullptr;    // residency bitmap, one bit per gid
+  uint32_t* ring = nullptr;       // [nblocks] free blocks
+  uint32_t* deferred = nullptr;   // [nblocks]
   uint32_t nblocks = 0;
   uint64_t resident_ngid = 0;     // gids covered by `resident`
   CacheState* cstate = nullptr;
@@ -383,8 +384,9 @@ jt_status enqueue_scan(jt_ctx* c, uint64_t gid_lo, uint64_t gid_hi, cudaStream_t
 // Frees the cross-frame block cache's arrays.
 void cache_free(jt_ctx* c) {
   dev_free(c->resident);
-  dev_free(c->block_gid);
-  dev_free(c->free_list);
+  dev_free(c->resbits);
+  dev_free(c->ring);
+  dev_free(c->deferred);
   dev_free(c->cstate);
   c->nblocks = 0;
   c->resident_ngid = 0;
@@ -396,16 +398,21 @@ jt_status cache_reset(jt_ctx* c) {
   c->nblocks = (uint32_t)(c->cap_units / 4);
   c->resident_ngid = c->ngid;
   jt_status s;
-  if ((s = dev_alloc(c, &c->resident, std::max<uint64_t>(1, c->ngid) * 4)) != JT_OK) return s;
-  if ((s = dev_alloc(c, &c->block_gid, std::max<uint32_t>(1, c->nblocks) * 4)) != JT_OK) return s;
-  if ((s = dev_alloc(c, &c->free_list, std::max<uint32_t>(1, c->nblocks) * 4)) != JT_OK) return s;
+  if (c->nblocks == 0) return fail(c, JT_ERR_INVALID_ARG, "the block cache needs at least one block");
+  const uint64_t nbits = std::max<uint64_t>(1, (c->ngid + 31) / 32) * 4;  // whole 32-bit words
+  const uint64_t nres = std::max<uint64_t>(1, (c->ngid + 15) / 16) * 16;  // whole groups of 16 gids
+  if ((s = dev_alloc(c, &c->resident, nres * 4)) != JT_OK) return s;
+  if ((s = dev_alloc(c, &c->resbits, nbits)) != JT_OK) return s;
+  if ((s = dev_alloc(c, &c->ring, (size_t)c->nblocks * 4)) != JT_OK) return s;
+  if ((s = dev_alloc(c, &c->deferred, (size_t)c->nblocks * 4)) != JT_OK) return s;
   if ((s = dev_alloc(c, &c->cstate, sizeof(CacheState))) != JT_OK) return s;
   std::vector<uint32_t> fl(c->nblocks);
-  for (uint32_t i = 0; i < c->nblocks; ++i) fl[i] = c->nblocks - 1 - i;  // pops give 0, 1, 2, ...
-  const CacheState cs{c->nblocks, 0, 0, 0};
-  JT_CUDA(c, cudaMemset(c->resident, 0xFF, std::max<uint64_t>(1, c->ngid) * 4));
-  JT_CUDA(c, cudaMemset(c->block_gid, 0xFF, std::max<uint32_t>(1, c->nblocks) * 4));
-  JT_CUDA(c, cudaMemcpy(c->free_list, fl.data(), (size_t)c->nblocks * 4, cudaMemcpyHostToDevice));
+  for (uint32_t i = 0; i < c->nblocks; ++i) fl[i] = i;  // blocks are handed out 0, 1, 2, ...
+  CacheState cs{};
+  cs.free_count = c->nblocks;
+  JT_CUDA(c, cudaMemset(c->resident, 0xFF, nres * 4));
+  JT_CUDA(c, cudaMemset(c->resbits, 0, nbits));
+  JT_CUDA(c, cudaMemcpy(c->ring, fl.data(), (size_t)c->nblocks * 4, cudaMemcpyHostToDevice));
   JT_CUDA(c, cudaMemcpy(c->cstate, &cs, sizeof cs, cudaMemcpyHostToDevice));
   return JT_OK;
 }
@@ -422,8 +429,10 @@ jt_status enqueue_cache_update(jt_ctx* c, cudaStream_t s) {
   a.flags = c->flags;
   a.n = (uint32_t)c->ngid;
   a.resident = c->resident;
-  a.block_gid = c->block_gid;
-  a.free_list = c->free_list;
+  a.resbits = reinterpret_cast<uint16_t*>(c->resbits);
+  a.resbits32 = c->resbits;
+  a.ring = c->ring;
+  a.deferred = c->deferred;
   a.nblocks = c->nblocks;
   a.slot = c->slot;
   a.work = c->work;

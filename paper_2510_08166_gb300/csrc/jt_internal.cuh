@@ -195,20 +195,29 @@ constexpr int kScanPerThread = 16;  // one 16-byte load
 constexpr int kScanTile = kScanThreads * kScanPerThread;  // 4096 flags
 void launch_scan(const ScanArgs& a, cudaStream_t s);  // two launches; tile_status: one word per tile
 
-// Cross-frame block cache (Sec. 4.1, Sec. 4.5): resident[gid] = block or ~0, block_gid[block]
-// = gid or ~0, free_list[0 .. free_count) = free blocks (a stack). A block is 4 cache units.
+// Cross-frame block cache (Sec. 4.1, Sec. 4.5): resident[gid] = the gid's block where its bit
+// in the residency bitmap is set; free blocks in a ring, positions [head, head + free_count)
+// modulo nblocks. A block is 4 cache units. Every counter but head, free_count, visible and
+// evicted is zero between frames.
 struct CacheState {
-  uint32_t free_count;  // blocks on the free stack
-  uint32_t taken;       // blocks the current allocation pass has taken from its top
-  uint32_t visible;     // MCUs the last frame needed
-  uint32_t evicted;     // blocks evicted since the counter was last cleared
+  uint32_t head;         // ring position of the first free block
+  uint32_t free_count;   // free blocks
+  uint32_t taken;        // misses of the current update (blocks asked for)
+  uint32_t spare;        // (unused)
+  uint32_t evict_n;      // blocks evicted by the current update
+  uint32_t visible_acc;  // MCUs the current update has seen needed
+  uint32_t done;         // CTAs of the current update that have finished
+  uint32_t visible;      // MCUs the last frame needed
+  uint32_t evicted;      // blocks evicted since the counter was last cleared
 };
 struct CacheArgs {
-  uint8_t* flags;  // flags[gid], cleared by the allocation pass
+  uint8_t* flags;  // flags[gid], cleared by the update
   uint32_t n;      // gids
-  uint32_t* resident;
-  uint32_t* block_gid;
-  uint32_t* free_list;
+  uint32_t* resident;   // [n]
+  uint16_t* resbits;    // residency bitmap, 16 gids per word ...
+  uint32_t* resbits32;  // ... the same memory as 32-bit words (a whole number of them)
+  uint32_t* ring;       // [nblocks] free blocks
+  uint32_t* deferred;   // [nblocks] misses waiting for a block evicted by the same update
   uint32_t nblocks;
   uint32_t* slot;
   uint32_t* work;
@@ -216,7 +225,8 @@ struct CacheArgs {
   FrameState* state;
   CacheState* cs;
 };
-void launch_cache_update(const CacheArgs& a, int grid, cudaStream_t s);
+constexpr int kCacheThreads = 256;
+void launch_cache_update(const CacheArgs& a, int max_grid, cudaStream_t s);  // one launch
 
 // Scene rasteriser (geometry-pass stand-in): one quad, laid out as jt_scene_quad.
 struct SceneQuad {

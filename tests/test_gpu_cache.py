@@ -102,3 +102,35 @@ def test_cache_capacity_is_reported(jt, scene):
         ctx.frame_plain([(jt.DeviceGBuffer.from_host(views[0]),
                           torch.zeros((views[0].height, views[0].width, 4), dtype=torch.uint8, device="cuda"))], 1)
     ctx.close()
+
+
+def test_tight_cache_reuses_blocks_evicted_by_the_same_frame(jt, scene):
+    """A cache exactly the size of the largest needed set: a frame's misses outnumber the
+    blocks free when it starts, so some of them must take blocks the same frame evicts."""
+    ts, views = scene
+    o = oracle.texset_from(ts)
+    gm = GidMap(ts)
+    needed = [set(o.compact(o.mark(v, 1)).tolist()) for v in views]
+    cap = max(len(n) for n in needed)
+    order = list(range(len(views))) + list(range(len(views) - 2, -1, -1))  # forward, then back
+    assert any(len(needed[a] | needed[b]) > cap for a, b in zip(order, order[1:]))
+    per = jt.Context(0, 1 << 14)
+    per.upload_set(ts)
+    tight = jt.Context(0, cap)
+    tight.upload_set(ts)
+    tight.set_block_cache(True)
+    previous = set()
+    for k in order:
+        dv = jt.DeviceGBuffer.from_host(views[k])
+        a = frame(per, dv, 1, torch)
+        per.stats()
+        b = frame(tight, dv, 1, torch)
+        st = tight.stats()  # raises on a capacity error
+        assert torch.equal(a, b), k
+        assert st["resident_blocks"] == len(needed[k])
+        assert st["needed_blocks"] == len(needed[k] - previous)
+        assert st["evicted_blocks"] == len(previous - needed[k])
+        check_tiles(tight, o, gm, sorted(needed[k]))
+        previous = needed[k]
+    per.close()
+    tight.close()
