@@ -124,6 +124,10 @@ typedef struct {
   int32_t decode_ctas_per_sm;   /* resident decode CTAs per SM of the persistent grid (>= 1) */
   int32_t pixel_threads;        /* threads per CTA of mark and colourise (64..1024, mult. of 32) */
   int32_t pixel_ctas_per_sm;    /* CTAs per SM of the grid-stride mark and colourise grids */
+  int32_t decode_short_lists;   /* 1: a frame whose work list has at most 4 MCUs per decode warp
+                                   decodes it one MCU per warp, each by the whole warp (a
+                                   separate kernel); 0: one MCU per lane always; -1 (default):
+                                   1 with the cross-frame block cache, 0 without */
 } jt_tuning;
 
 /* ---- context ------------------------------------------------------------------------- */

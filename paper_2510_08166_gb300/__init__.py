@@ -79,7 +79,7 @@ class jt_stats(ctypes.Structure):
 class jt_tuning(ctypes.Structure):
     _fields_ = [("decode_mcus_per_warp", ctypes.c_int32), ("decode_warps", ctypes.c_int32),
                 ("decode_ctas_per_sm", ctypes.c_int32), ("pixel_threads", ctypes.c_int32),
-                ("pixel_ctas_per_sm", ctypes.c_int32)]
+                ("pixel_ctas_per_sm", ctypes.c_int32), ("decode_short_lists", ctypes.c_int32)]
 
 
 assert ctypes.sizeof(jt_block_index) == 10

@@ -697,7 +697,9 @@ __device__ __forceinline__ void mcu_warp_pixels(const int16_t* cc, int16_t* tmp,
 // UNITS: the variant for contexts with data-unit starts. Each MCU of a batch then takes six
 // lanes, lane 6m + d decoding data unit d of MCU m from its own start (levels without
 // starts are decoded whole by lane 6m); MCUs per batch are at most 4.
-template <int M, bool UNITS>
+// SHORT: the variant that decodes short lists MCU by MCU with whole warps (a separate kernel,
+// so that the lane-per-MCU variant is compiled without that code).
+template <int M, bool UNITS, bool SHORT>
 __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   HuffSet* sh = reinterpret_cast<HuffSet*>(smem);
@@ -726,7 +728,7 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
   // (up to kWarpMcuMax MCUs per warp they go one at a time, each decoded by the whole warp:
   // a lone lane's chain is several times longer than the warp's)
   int lmeff = 0;
-  if (UNITS || M < 4 || per_warp > (uint32_t)kWarpMcuMax)
+  if (!SHORT || M < 4 || per_warp > (uint32_t)kWarpMcuMax)
     while ((1u << lmeff) < per_warp && (1 << lmeff) < kMaxBatch) ++lmeff;
   const int meff = 1 << lmeff;
   // first batch by rank, interleaved over the CTAs (one warp per SM first), then dynamic
@@ -868,7 +870,7 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
       if (end == 0xFFFFFFFFu || (uint64_t)w0 * 32 + end > endbit) any_bad = true;
     }
     bool warp_done = false;  // the MCU's tile was written by the whole warp
-    if (!UNITS && M >= 4 && meff == 1) {
+    if (SHORT && !UNITS && M >= 4 && meff == 1) {
       // one MCU per warp: the whole warp runs lane 0's chain (coefficients contiguous in
       // the buffer's first 768 B, the window's entries in the next 1 KiB); a full-size tile
       // is then transformed and stored by the whole warp, any other is scattered into lane
@@ -1048,27 +1050,28 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
 
 size_t smem_bytes(int warps, int M) { return sizeof(HuffSet) + 64 + (size_t)warps * warp_smem(M); }
 
-template <int M, bool UNITS>
+template <int M, bool UNITS, bool SHORT>
 int occupancy_of(int warps) {
   const size_t smem = smem_bytes(warps, M);
   if (smem > 227 * 1024) return 0;
-  if (cudaFuncSetAttribute(k_decode<M, UNITS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+  if (cudaFuncSetAttribute(k_decode<M, UNITS, SHORT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_decode<M, UNITS>, warps * 32, smem) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_decode<M, UNITS, SHORT>, warps * 32, smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   return n;
 }
 
-// resident CTAs per SM that both variants reach (the launch picks one per frame)
+// resident CTAs per SM that every variant reaches (the launch picks one per frame)
 template <int M>
 int occupancy(int warps) {
-  return min(occupancy_of<M, false>(warps), occupancy_of<M, true>(warps));
+  return min(min(occupancy_of<M, false, false>(warps), occupancy_of<M, true, false>(warps)),
+             occupancy_of<M, false, true>(warps));
 }
 
 }  // namespace
@@ -1081,18 +1084,27 @@ void launch_decode(const DecodeArgs& a, int warps, int grid, cudaStream_t s) {
   const size_t smem = smem_bytes(warps, a.mcus_per_warp);
   if (a.unit_mode) {
     switch (a.mcus_per_warp) {
-      case 4: k_decode<4, true><<<grid, warps * 32, smem, s>>>(a); break;
-      case 8: k_decode<8, true><<<grid, warps * 32, smem, s>>>(a); break;
-      case 16: k_decode<16, true><<<grid, warps * 32, smem, s>>>(a); break;
-      default: k_decode<32, true><<<grid, warps * 32, smem, s>>>(a); break;
+      case 4: k_decode<4, true, false><<<grid, warps * 32, smem, s>>>(a); break;
+      case 8: k_decode<8, true, false><<<grid, warps * 32, smem, s>>>(a); break;
+      case 16: k_decode<16, true, false><<<grid, warps * 32, smem, s>>>(a); break;
+      default: k_decode<32, true, false><<<grid, warps * 32, smem, s>>>(a); break;
+    }
+    return;
+  }
+  if (a.short_lists) {
+    switch (a.mcus_per_warp) {
+      case 4: k_decode<4, false, true><<<grid, warps * 32, smem, s>>>(a); break;
+      case 8: k_decode<8, false, true><<<grid, warps * 32, smem, s>>>(a); break;
+      case 16: k_decode<16, false, true><<<grid, warps * 32, smem, s>>>(a); break;
+      default: k_decode<32, false, true><<<grid, warps * 32, smem, s>>>(a); break;
     }
     return;
   }
   switch (a.mcus_per_warp) {
-    case 4: k_decode<4, false><<<grid, warps * 32, smem, s>>>(a); break;
-    case 8: k_decode<8, false><<<grid, warps * 32, smem, s>>>(a); break;
-    case 16: k_decode<16, false><<<grid, warps * 32, smem, s>>>(a); break;
-    default: k_decode<32, false><<<grid, warps * 32, smem, s>>>(a); break;
+    case 4: k_decode<4, false, false><<<grid, warps * 32, smem, s>>>(a); break;
+    case 8: k_decode<8, false, false><<<grid, warps * 32, smem, s>>>(a); break;
+    case 16: k_decode<16, false, false><<<grid, warps * 32, smem, s>>>(a); break;
+    default: k_decode<32, false, false><<<grid, warps * 32, smem, s>>>(a); break;
   }
 }
 

@@ -455,6 +455,7 @@ jt_status enqueue_decode(jt_ctx* c, cudaStream_t s) {
   a.desc_of_gid = c->d_desc_of_gid;
   a.mcus_per_warp = c->tuning.decode_mcus_per_warp;
   a.unit_mode = c->unit_mode ? 1 : 0;
+  a.short_lists = c->tuning.decode_short_lists < 0 ? (c->persistent ? 1 : 0) : c->tuning.decode_short_lists;
   a.huff = c->d_huff;
   a.quant = c->d_quant;
   a.work = c->work;
@@ -519,7 +520,7 @@ bool valid_tuning(const jt_ctx* c, const jt_tuning& t) {
   const bool w_ok = W >= 1 && W <= 16;
   return m_ok && w_ok && c->decode_occ[M][W] > 0 && t.decode_ctas_per_sm >= 1 && t.pixel_threads >= 64 &&
          t.pixel_threads <= 1024 && t.pixel_threads % 32 == 0 && t.pixel_ctas_per_sm >= 1 &&
-         t.pixel_ctas_per_sm <= 32;
+         t.pixel_ctas_per_sm <= 32 && t.decode_short_lists >= -1 && t.decode_short_lists <= 1;
 }
 
 // Shared set-up of the two float calls: checks, the view, the float-chain arguments.
@@ -611,6 +612,7 @@ jt_status jt_create(jt_ctx** out, int device, uint64_t max_cache_blocks) {
   c->tuning.decode_ctas_per_sm = std::max(1, c->decode_occ[32][4]);
   c->tuning.pixel_threads = 256;
   c->tuning.pixel_ctas_per_sm = 8;
+  c->tuning.decode_short_lists = -1;
   c->cap_units = max_cache_blocks * 4;
   if (dev_alloc(c, &c->cache, c->cap_units * kUnitBytes) != JT_OK || dev_alloc(c, &c->state, sizeof(FrameState)) != JT_OK ||
       cudaMemset(c->state, 0, sizeof(FrameState)) != cudaSuccess || cudaMemset(c->cache, 0, c->cap_units * kUnitBytes) != cudaSuccess ||

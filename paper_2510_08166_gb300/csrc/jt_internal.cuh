@@ -257,6 +257,7 @@ struct DecodeArgs {
   const uint32_t* desc_of_gid;  // descriptor index of each gid
   int mcus_per_warp;      // M, the buffer width: 4, 8, 16 or 32 (batches may be smaller)
   int unit_mode;          // some level has data-unit starts: the kernel that decodes them in parallel
+  int short_lists;        // the kernel that decodes short lists MCU by MCU with whole warps
   const HuffSet* huff;    // set 0 is staged in shared memory
   const uint16_t* quant;  // [nq][2][64] zig-zag order
   const uint32_t* work;

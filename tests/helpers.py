@@ -87,3 +87,10 @@ def mcu_grid_gbuffer(ts, width: int = 2048) -> synth.GBuffer:
     M = np.zeros(h * width, np.uint8)
     U[:n], T[:n], M[:n] = uv, np.concatenate(texs), np.concatenate(mips)
     return synth.GBuffer(width, h, U.reshape(h, width, 2), T.reshape(h, width), M.reshape(h, width))
+
+
+def set_short_lists(ctx, on: int):
+    """Short work lists decoded MCU by MCU by whole warps (1) or one MCU per lane (0)."""
+    t = ctx.tuning()
+    t["decode_short_lists"] = int(on)
+    ctx.set_tuning(**t)

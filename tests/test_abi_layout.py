@@ -19,7 +19,7 @@ STRUCTS = {
     "jt_gbuffer": ["uv", "tex_id", "mip", "width", "height"],
     "jt_view": ["g", "out_rgba"],
     "jt_tuning": ["decode_mcus_per_warp", "decode_warps", "decode_ctas_per_sm", "pixel_threads",
-                  "pixel_ctas_per_sm"],
+                  "pixel_ctas_per_sm", "decode_short_lists"],
     "jt_scene_quad": ["cx", "cy", "ex", "ey", "h", "rep", "cs", "sn", "ou", "ov", "tex", "x0", "y0", "x1", "y1"],
     "jt_scene": ["width", "height", "cam", "rot", "ax", "ay", "tan_x", "tan_y", "max_t", "kx", "ky", "shift",
                  "cell_seed", "ntex", "use_mips", "tex_w", "tex_h", "tex_levels", "quads", "nquads", "reserved"],

@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 import synth
-from helpers import GidMap, check_tiles, concat_gbuffers, frame, texel_grid_gbuffer
+from helpers import GidMap, check_tiles, concat_gbuffers, frame, set_short_lists, texel_grid_gbuffer
 
 pytestmark = pytest.mark.gpu
 
@@ -24,13 +24,15 @@ def jt():
 @pytest.mark.parametrize("size,sampling,q", [((16, 16), 420, 80), ((33, 17), 420, 50), ((40, 24), 444, 90),
                                              ((1, 1), 420, 75), ((9, 3), 444, 60), ((200, 136), 444, 100),
                                              ((256, 144), 420, 100), ((256, 128), 420, 30)])
-def test_every_mcu_compact(jt, size, sampling, q):
+@pytest.mark.parametrize("short", [0, 1])
+def test_every_mcu_compact(jt, size, sampling, q, short):
     """Every MCU of the level (144 = 9 x 16 rows of MCUs: whole offset groups and a tail)."""
     w, h = size
     rgb = synth.texture(synth.mix_seed(23, w, h), w, h)
     ts = synth.TextureSet([[synth.encode(rgb, q, sampling, compact=True)]])
     gb = texel_grid_gbuffer(w, h)
     ctx = jt.Context(0, max_cache_blocks=1 << 14)
+    set_short_lists(ctx, short)
     ctx.upload_set(ts, compact=True)
     o = oracle.texset_from(ts, compact=True)
     out = frame(ctx, jt.DeviceGBuffer.from_host(gb), 0, torch).cpu().numpy()

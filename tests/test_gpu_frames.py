@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 import synth
-from helpers import GidMap, check_tiles, frame
+from helpers import GidMap, check_tiles, frame, set_short_lists
 
 pytestmark = pytest.mark.gpu
 
@@ -131,13 +131,14 @@ def test_autotune_keeps_results(jt, scene):
 
 @pytest.mark.parametrize("mcus,warps,per_sm", [(4, 2, 1), (8, 8, 2), (4, 16, 1), (16, 4, 1), (32, 2, 1),
                                                (16, 2, 2), (32, 7, 1), (16, 13, 1), (8, 3, 2)])
-def test_decode_shapes_bit_exact(jt, scene, mcus, warps, per_sm):
+@pytest.mark.parametrize("short", [0, 1])
+def test_decode_shapes_bit_exact(jt, scene, mcus, warps, per_sm, short):
     ts, views = scene
     ctx = jt.Context(0, 1 << 15)
     ctx.upload_set(ts)
     t = ctx.tuning()
     t.update(decode_mcus_per_warp=mcus, decode_warps=warps, decode_ctas_per_sm=per_sm, pixel_threads=128,
-             pixel_ctas_per_sm=2)
+             pixel_ctas_per_sm=2, decode_short_lists=short)
     ctx.set_tuning(**t)
     o = oracle.texset_from(ts)
     dv = jt.DeviceGBuffer.from_host(views[0])
@@ -150,12 +151,14 @@ def test_decode_shapes_bit_exact(jt, scene, mcus, warps, per_sm):
 
 # ---- errors: returned as statuses, never a trap ----
 
-def test_corrupt_stream_reports_status(jt):
+@pytest.mark.parametrize("short", [0, 1])
+def test_corrupt_stream_reports_status(jt, short):
     rgb = synth.texture(3, 64, 64)
     enc = synth.encode(rgb, 80, 420)
     bad = synth.Encoded(**{k: getattr(enc, k) for k in enc.__dataclass_fields__})
     bad.scan = np.full_like(enc.scan, 0xFF)  # sixteen one-bits match no AC/DC code
     ctx = jt.Context(0, 1 << 10)
+    set_short_lists(ctx, short)
     ctx.upload(0, 0, bad)
     from helpers import texel_grid_gbuffer
     dv = jt.DeviceGBuffer.from_host(texel_grid_gbuffer(64, 64))
@@ -171,13 +174,15 @@ def test_corrupt_stream_reports_status(jt):
     ctx.close()
 
 
-def test_truncated_stream_reports_status(jt):
+@pytest.mark.parametrize("short", [0, 1])
+def test_truncated_stream_reports_status(jt, short):
     rgb = synth.texture(4, 64, 64)
     enc = synth.encode(rgb, 90, 420)
     bad = synth.Encoded(**{k: getattr(enc, k) for k in enc.__dataclass_fields__})
     bad.scan = enc.scan[: len(enc.scan) // 2].copy()
     bad.scan_bits = len(bad.scan) * 8
     ctx = jt.Context(0, 1 << 10)
+    set_short_lists(ctx, short)
     ctx.upload(0, 0, bad)
     from helpers import texel_grid_gbuffer
     frame(ctx, jt.DeviceGBuffer.from_host(texel_grid_gbuffer(64, 64)), 0, torch)

@@ -9,7 +9,7 @@ import pytest
 
 import oracle
 import synth
-from helpers import concat_gbuffers, frame, texel_grid_gbuffer
+from helpers import concat_gbuffers, frame, set_short_lists, texel_grid_gbuffer
 
 pytestmark = pytest.mark.gpu
 
@@ -54,10 +54,12 @@ class Registry:
 
 @pytest.mark.parametrize("size,sampling,q", [((64, 64), 420, 80), ((33, 17), 420, 50), ((40, 24), 444, 95),
                                              ((96, 48), 444, 60), ((256, 128), 420, 100)])
-def test_every_reduced_mcu(jt, size, sampling, q):
+@pytest.mark.parametrize("short", [0, 1])
+def test_every_reduced_mcu(jt, size, sampling, q, short):
     w, h = size
     e = synth.encode(synth.texture(synth.mix_seed(41, w, h), w, h), q, sampling)
     ctx = jt.Context(0, max_cache_blocks=1 << 14)
+    set_short_lists(ctx, short)
     reg = Registry(ctx)
     reg.upload(0, 0, e)
     gbs = []
