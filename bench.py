@@ -783,10 +783,27 @@ def run_adjoint(jt, dev, flush, stream, steps, peak):
                                  "algorithmic_bytes": fwd_bytes, "intermediate_tile_bytes": tile_bytes}}
 
 
+def run_only_motion(args, local_rank):
+    """The motion legs alone (also the command the cache-update profile was taken with)."""
+    import torch
+    import paper_2510_08166_gb300 as jt
+    ts, _ = workload()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    flush = L2Flush(dev)
+    stream = torch.cuda.current_stream(dev)
+    out = {"motion": run_motion(jt, ts, dev, flush, stream, reps=args.motion_reps),
+           "motion_vr": run_motion(jt, ts, dev, flush, stream, reps=args.motion_reps, stereo=True)}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     import paper_2510_08166_gb300 as jt
 
+    if args.only == "motion":
+        return run_only_motion(args, local_rank) if rank == 0 else 0
     ts, gb = workload(compact=not args.no_extra)
     pool = ts4 = None
     if rank == 0 and world == 1 and not args.no_cpu and not args.quick:
@@ -976,8 +993,8 @@ def run_gpu(args, rank, world, local_rank):
             line["batched_views"] = run_views(ctx, ts, jt, dev, flush, stream, 20)
             line["adjoint"] = run_adjoint(jt, dev, flush, stream, 20, peak)
             line["full_decode"] = run_full_decode(jt, dev, flush, stream, 5, peak, ctx.tuning(), args.full_decode_textures)
-            line["motion"] = run_motion(jt, ts, dev, flush, stream)
-            line["motion_vr"] = run_motion(jt, ts, dev, flush, stream, stereo=True)
+            line["motion"] = run_motion(jt, ts, dev, flush, stream, reps=args.motion_reps)
+            line["motion_vr"] = run_motion(jt, ts, dev, flush, stream, reps=args.motion_reps, stereo=True)
         print(json.dumps(line), flush=True)
     if pool is not None:
         pool.close()
@@ -1000,6 +1017,10 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the batched-views and adjoint measurements")
     ap.add_argument("--full-decode-textures", type=int, default=256,
                     help="textures of the full-decode leg (256 is the stated configuration)")
+    ap.add_argument("--only", choices=["motion"], default=None,
+                    help="run one leg alone and print its JSON (motion: the 1080p and VR motion legs)")
+    ap.add_argument("--motion-reps", type=int, default=100,
+                    help="turns of the motion legs after the warm-up turn (100 is the paper's protocol)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
