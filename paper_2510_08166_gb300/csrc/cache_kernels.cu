@@ -39,6 +39,8 @@ __device__ __forceinline__ uint32_t* ring_at(const CacheArgs& a, uint32_t p) {
 
 __global__ void __launch_bounds__(kCacheThreads) k_cache_update(const __grid_constant__ CacheArgs a) {
   __shared__ bool s_last;
+  pdl_launch_dependents();
+  pdl_wait();  // the flags come from the mark pass
   const uint32_t head = a.cs->head, free0 = a.cs->free_count;  // fixed until the last CTA
   uint32_t visible = 0;
   bool over = false, wrote = false;
@@ -179,7 +181,7 @@ __global__ void __launch_bounds__(kCacheThreads) k_cache_update(const __grid_con
 void launch_cache_update(const CacheArgs& a, int max_grid, cudaStream_t s) {
   const uint32_t nw = (a.n + 15) / 16;
   const int grid = (int)std::max<uint32_t>(1, std::min<uint32_t>((nw + kCacheThreads - 1) / kCacheThreads, (uint32_t)max_grid));
-  k_cache_update<<<grid, kCacheThreads, 0, s>>>(a);
+  launch_pdl(k_cache_update, grid, kCacheThreads, 0, s, a);
 }
 
 }  // namespace jt

@@ -712,12 +712,14 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
   int16_t* col = coef + (lm < M ? lm : 0);  // this lane's MCU column
   constexpr int kMaxBatch = UNITS ? (M < 4 ? M : 4) : M;
 
-  {  // stage Huffman set 0
+  pdl_launch_dependents();
+  {  // stage Huffman set 0 (written at upload, so before the wait for the kernel before)
     const uint4* src = reinterpret_cast<const uint4*>(a.huff);
     uint4* dst = reinterpret_cast<uint4*>(sh);
     for (int i = threadIdx.x; i < (int)(sizeof(HuffSet) / 16); i += blockDim.x) dst[i] = __ldg(src + i);
   }
   __syncthreads();
+  pdl_wait();  // the work list, slots and counts come from the compaction or the cache update
 
   const uint32_t count = min(*(volatile uint32_t*)&a.state->count, a.work_cap);
   bool any_bad = false;
@@ -1084,27 +1086,27 @@ void launch_decode(const DecodeArgs& a, int warps, int grid, cudaStream_t s) {
   const size_t smem = smem_bytes(warps, a.mcus_per_warp);
   if (a.unit_mode) {
     switch (a.mcus_per_warp) {
-      case 4: k_decode<4, true, false><<<grid, warps * 32, smem, s>>>(a); break;
-      case 8: k_decode<8, true, false><<<grid, warps * 32, smem, s>>>(a); break;
-      case 16: k_decode<16, true, false><<<grid, warps * 32, smem, s>>>(a); break;
-      default: k_decode<32, true, false><<<grid, warps * 32, smem, s>>>(a); break;
+      case 4: launch_pdl(k_decode<4, true, false>, grid, warps * 32, smem, s, a); break;
+      case 8: launch_pdl(k_decode<8, true, false>, grid, warps * 32, smem, s, a); break;
+      case 16: launch_pdl(k_decode<16, true, false>, grid, warps * 32, smem, s, a); break;
+      default: launch_pdl(k_decode<32, true, false>, grid, warps * 32, smem, s, a); break;
     }
     return;
   }
   if (a.short_lists) {
     switch (a.mcus_per_warp) {
-      case 4: k_decode<4, false, true><<<grid, warps * 32, smem, s>>>(a); break;
-      case 8: k_decode<8, false, true><<<grid, warps * 32, smem, s>>>(a); break;
-      case 16: k_decode<16, false, true><<<grid, warps * 32, smem, s>>>(a); break;
-      default: k_decode<32, false, true><<<grid, warps * 32, smem, s>>>(a); break;
+      case 4: launch_pdl(k_decode<4, false, true>, grid, warps * 32, smem, s, a); break;
+      case 8: launch_pdl(k_decode<8, false, true>, grid, warps * 32, smem, s, a); break;
+      case 16: launch_pdl(k_decode<16, false, true>, grid, warps * 32, smem, s, a); break;
+      default: launch_pdl(k_decode<32, false, true>, grid, warps * 32, smem, s, a); break;
     }
     return;
   }
   switch (a.mcus_per_warp) {
-    case 4: k_decode<4, false, false><<<grid, warps * 32, smem, s>>>(a); break;
-    case 8: k_decode<8, false, false><<<grid, warps * 32, smem, s>>>(a); break;
-    case 16: k_decode<16, false, false><<<grid, warps * 32, smem, s>>>(a); break;
-    default: k_decode<32, false, false><<<grid, warps * 32, smem, s>>>(a); break;
+    case 4: launch_pdl(k_decode<4, false, false>, grid, warps * 32, smem, s, a); break;
+    case 8: launch_pdl(k_decode<8, false, false>, grid, warps * 32, smem, s, a); break;
+    case 16: launch_pdl(k_decode<16, false, false>, grid, warps * 32, smem, s, a); break;
+    default: launch_pdl(k_decode<32, false, false>, grid, warps * 32, smem, s, a); break;
   }
 }
 

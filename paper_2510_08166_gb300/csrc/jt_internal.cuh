@@ -15,11 +15,40 @@
 //   state      FrameState            counts, work counter, error word
 #pragma once
 
+#include <cuda_runtime.h>
+
 #include <cstdint>
 
 #include "jt.h"
 
 namespace jt {
+
+// ---- programmatic dependent launch ----
+// The frame's kernels after the first are launched with programmatic stream serialisation:
+// a kernel may start while the one before it in the stream is still running, and waits on
+// the device (pdl_wait) before it reads or writes anything an earlier kernel of the stream
+// produces or consumes. Each kernel lets its dependents launch as soon as it starts
+// (pdl_launch_dependents); a dependent's CTAs are only scheduled once every CTA of the
+// running grid has started, so they never hold resources that grid still needs. Without
+// the attribute (or after a non-kernel operation) both instructions are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
 
 constexpr int kLutBits = 10;                 // first-level Huffman LUT: next 10 bits
 constexpr int kLutSize = 1 << kLutBits;

@@ -62,6 +62,8 @@ __device__ __forceinline__ uint64_t block_sum(uint64_t v, uint64_t* s_part) {
 
 __global__ void __launch_bounds__(kScanThreads) k_tile_sums(const __grid_constant__ ScanArgs a) {
   __shared__ uint64_t s_part[kScanThreads / 32];
+  pdl_launch_dependents();
+  pdl_wait();  // the flags come from the kernel before
   const uint32_t ntiles = (a.n + kScanTile - 1) / kScanTile;
   for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     uint32_t w[4], cnt = 0, sum = 0;
@@ -78,6 +80,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_scatter(const __grid_cons
   __shared__ uint32_t s_cnt[kScanThreads / 32], s_sum[kScanThreads / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t ntiles = (a.n + kScanTile - 1) / kScanTile;
+  pdl_launch_dependents();
+  pdl_wait();  // the tile sums come from k_tile_sums
   for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     // predecessors' totals: thread i adds tiles i, i + 256, ... below this one, four loads in
     // flight at a time
@@ -167,8 +171,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_scatter(const __grid_cons
 void launch_scan(const ScanArgs& a, cudaStream_t s) {
   const uint32_t ntiles = (a.n + kScanTile - 1) / kScanTile;
   const int grid = (int)(ntiles ? ntiles : 1);
-  k_tile_sums<<<grid, kScanThreads, 0, s>>>(a);
-  k_scan_scatter<<<grid, kScanThreads, 0, s>>>(a);
+  launch_pdl(k_tile_sums, grid, kScanThreads, 0, s, a);
+  launch_pdl(k_scan_scatter, grid, kScanThreads, 0, s, a);
 }
 
 }  // namespace jt
