@@ -349,14 +349,15 @@ __device__ __forceinline__ uint32_t decode_unit(const Words& W, uint32_t bit0, c
 // before. Here the 32 lanes instead decode, for every bit offset of a 256-bit window of the
 // stream, the AC symbol that would start there (entries independent of each other, 8 per
 // lane, loads issued before any store), and the chain that remains is one shared-memory read
-// and one add per symbol: the entry at the current position holds the byte offset of the
-// entry after its symbol (code + value bits), its run and its value. All lanes follow the chain in
+// per one or two symbols: the slot at the current position holds the byte offset of the slot
+// after its symbol (code + value bits), its run and its value, and the same for the symbol
+// after it, so a read serves two symbols unless the first ends the data unit. All lanes follow the chain in
 // step, so its state is warp-uniform; symbol s of a data unit is kept in registers by lane
 // s mod 32, and the coefficients are stored once the data unit ends (a store on the chain
 // would hold the next table read behind it). The DC symbol of each data unit is decoded
 // directly on the chain. The window is rebuilt when the position leaves it or the component
 // class (luma, chroma) changes.
-constexpr int kWinBits = 256;    // window of symbol entries, bits
+constexpr int kWinBits = 256;    // window of symbol entries, bits (128 when the buffer is 4 MCUs wide)
 constexpr int kWarpMcuMax = 4;   // lists of at most this many MCUs per warp are decoded MCU by MCU
 
 // LUT entry of the code at the top of w in table ti (0 when it has none).
@@ -375,21 +376,27 @@ __device__ __forceinline__ int symbol_value(uint32_t w, uint32_t l, uint32_t sz)
   return (int)__funnelshift_l(tw, 0u, sz) + (int)(~((int)tw >> 31) & (int)(1u - (1u << sz)));
 }
 
-// Window entry (two words) of symbol entry e read at w, window offset o. First word: byte
-// offset in the window of the entry after the symbol, clamped to the last entry (bits 0-10),
-// run (11-16), value bits present (17), the next symbol starts past the window (18), the next
-// symbol's window offset (19-27); 0 for no symbol (an invalid code), never 0 otherwise (the
-// next offset is at least 1). Second word: the value.
+// Window slot of symbol entry e read at w, window offset o, in a window of WIN bits (16-byte
+// slots). First word: byte offset in the window of the slot after the symbol, clamped to the
+// last slot (bits 0-11), run (12-17), value bits present (18), the next symbol starts past
+// the window (19), the next symbol's window offset (20-28); 0 for no symbol (an invalid
+// code), never 0 otherwise (the next offset is at least 1). Second word: the value.
+template <int WIN>
 __device__ __forceinline__ uint2 win_entry(uint32_t e, uint32_t w, uint32_t o) {
   const uint32_t l = e & 31u, sz = (e >> 5) & 15u, r = e >> 9, nx = o + l + sz;
-  const uint32_t x = (min(nx, (uint32_t)kWinBits - 1u) * 8u) | (r << 11) | (sz ? 1u << 17 : 0u) |
-                     (nx >= (uint32_t)kWinBits ? 1u << 18 : 0u) | (nx << 19);
+  const uint32_t x = (min(nx, (uint32_t)WIN - 1u) * 16u) | (r << 12) | (sz ? 1u << 18 : 0u) |
+                     (nx >= (uint32_t)WIN ? 1u << 19 : 0u) | (nx << 20);
   return e ? make_uint2(x, (uint32_t)symbol_value(w, l, sz)) : make_uint2(0u, 0u);
 }
 
 __device__ __forceinline__ uint2 lds_u64(uint32_t saddr) {
   uint2 v;
   asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(saddr));
+  return v;
+}
+__device__ __forceinline__ uint4 lds_u128(uint32_t saddr) {
+  uint4 v;
+  asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(saddr));
   return v;
 }
 
@@ -409,13 +416,16 @@ __device__ __forceinline__ uint32_t bits32w(const WS& W, uint32_t p) {
 
 // Entropy-decodes all data units of one MCU with the whole warp (every lane calls it with the
 // same arguments). Coefficients go to cc[du * 64 + k] (contiguous, zig-zag k; zero on entry);
-// tbl_sa is the 8-byte aligned shared address of 2 kWinBits words of scratch. Same results and the same
-// invalid codings as decode_mcu. Returns the bit position after the MCU relative to the first
-// staged word, or 0xFFFFFFFF on an invalid coding.
-template <bool SH, bool CPT, class WS>
+// tbl_sa is the 16-byte aligned shared address of WIN 16-byte slots of scratch. Slot o holds
+// the symbol starting at window offset o and, when it stays in the window, the symbol right
+// after it, so one read serves two symbols unless the first ends the data unit. Same
+// results and the same invalid codings as decode_mcu. Returns the bit position after the
+// MCU relative to the first staged word, or 0xFFFFFFFF on an invalid coding.
+template <bool SH, bool CPT, int WIN, class WS>
 __device__ __forceinline__ uint32_t decode_mcu_warp(const WS& W, uint32_t bit0, const Tables<SH>& T, int ndu,
                                                     int p0, int p1, int p2, int16_t* cc, uint32_t tbl_sa,
                                                     int lane) {
+  constexpr int J = WIN / 32;  // slots per lane
   const uint32_t F0 = T.first16(0), F1 = T.first16(1), F2 = T.first16(2), F3 = T.first16(3);
   const uint32_t N0 = T.n2(0), N1 = T.n2(1), N2 = T.n2(2), N3 = T.n2(3);
   int pred0 = p0, pred1 = p1, pred2 = p2;
@@ -450,52 +460,70 @@ __device__ __forceinline__ uint32_t decode_mcu_warp(const WS& W, uint32_t bit0, 
     int k = 1, s = 0, kst = 0;
 #pragma unroll 1
     while (true) {
-      if (wcls != cls || pos - wb >= (uint32_t)kWinBits) {
+      if (wcls != cls || pos - wb >= (uint32_t)WIN) {
         // rebuild the window at pos: every lane's loads first, then its entries
         __syncwarp();  // every lane has read the old window
         wb = pos;
         wcls = cls;
-        uint32_t w[kWinBits / 32], e[kWinBits / 32];
+        uint32_t w[J], e[J];
 #pragma unroll
-        for (int j = 0; j < kWinBits / 32; ++j) w[j] = bits32w(W, wb + (uint32_t)(lane + 32 * j));
+        for (int j = 0; j < J; ++j) w[j] = bits32w(W, wb + (uint32_t)(lane + 32 * j));
         bool none = false;
 #pragma unroll
-        for (int j = 0; j < kWinBits / 32; ++j) {
+        for (int j = 0; j < J; ++j) {
           e[j] = lut_entry(T, tac, fac, nac, w[j]);
           none |= e[j] == 0;
         }
         if (none) {  // codes without a LUT entry: the MAXCODE walk decodes or rejects them
 #pragma unroll
-          for (int j = 0; j < kWinBits / 32; ++j)
+          for (int j = 0; j < J; ++j)
             if (e[j] == 0) e[j] = walk_symbol(T.hs + tac, w[j], false);
         }
+        uint2 we[J];
 #pragma unroll
-        for (int j = 0; j < kWinBits / 32; ++j) {
+        for (int j = 0; j < J; ++j) {
           const uint32_t o = (uint32_t)(lane + 32 * j);
-          const uint2 we = win_entry(e[j], w[j], o);
-          asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(tbl_sa + 8 * o), "r"(we.x), "r"(we.y));
+          we[j] = win_entry<WIN>(e[j], w[j], o);
+          asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(tbl_sa + 16 * o), "r"(we[j].x), "r"(we[j].y));
         }
         __syncwarp();
+        // second halves: the symbol after each slot's symbol, when it starts in the window
+        uint2 nb[J];
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+          const bool in = we[j].x != 0 && (we[j].x & (1u << 19)) == 0;
+          nb[j] = lds_u64(tbl_sa + (we[j].x & 4095u));  // a slot in the window either way
+          nb[j] = in ? nb[j] : make_uint2(0u, 0u);
+        }
+#pragma unroll
+        for (int j = 0; j < J; ++j)
+          asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(tbl_sa + 16 * (uint32_t)(lane + 32 * j) + 8),
+                       "r"(nb[j].x), "r"(nb[j].y));
+        __syncwarp();
       }
-      // symbols while the position stays in the window: one branch per symbol, and the next
-      // entry's read goes out before this one is taken apart (a lone warp issues in order, so
-      // the work on an entry would otherwise add to the chain); a read past the window is
-      // clamped into it and dropped
-      uint2 ent = lds_u64(tbl_sa + 8 * (pos - wb));
+      // symbols while the position stays in the window, one or two per read; the next
+      // slot's read goes out before this one is taken apart (a lone warp issues in order);
+      // a read past the window is clamped into it and dropped
+      uint4 ent = lds_u128(tbl_sa + 16 * (pos - wb));
       uint32_t nofs = pos - wb;  // window offset of the next symbol
       bool more;
       do {
-        const uint2 nxt = lds_u64(tbl_sa + (ent.x & 2047u));
-        kst = k + (int)((ent.x >> 11) & 63u);
-        const bool val = (ent.x & (1u << 17)) != 0;  // a coefficient (value bits present)
-        const uint32_t kv = val ? ((uint32_t)kst << 16) | (ent.y & 0xFFFFu) : 0u;
-        keep0 = s == lane ? kv : keep0;
-        keep1 = s == lane + 32 ? kv : keep1;
-        bad |= ent.x == 0 || (val && kst > 63);
+        const int kstA = k + (int)((ent.x >> 12) & 63u);
+        const bool two = kstA < 63 && ent.z != 0;  // the second symbol belongs to this unit
+        const uint4 nxt = lds_u128(tbl_sa + ((two ? ent.z : ent.x) & 4095u));
+        const bool valA = (ent.x & (1u << 18)) != 0, valB = (ent.z & (1u << 18)) != 0;
+        const int kstB = kstA + 1 + (int)((ent.z >> 12) & 63u);
+        const uint32_t kvA = valA ? ((uint32_t)kstA << 16) | (ent.y & 0xFFFFu) : 0u;
+        const uint32_t kvB = (two && valB) ? ((uint32_t)kstB << 16) | (ent.w & 0xFFFFu) : 0u;
+        keep0 = s == lane ? kvA : (s + 1 == lane ? kvB : keep0);
+        keep1 = s == lane + 32 ? kvA : (s + 1 == lane + 32 ? kvB : keep1);
+        bad |= ent.x == 0 || (valA && kstA > 63) || (two && valB && kstB > 63);
+        kst = two ? kstB : kstA;
+        s += two ? 2 : 1;
         k = kst + 1;
-        ++s;
-        nofs = ent.x >> 19;
-        more = kst < 63 && !bad && (ent.x & (1u << 18)) == 0;
+        const uint32_t last = two ? ent.z : ent.x;
+        nofs = last >> 20;
+        more = kst < 63 && !bad && (last & (1u << 19)) == 0;
         ent = nxt;
       } while (more);
       pos = wb + nofs;
@@ -874,7 +902,7 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
     bool warp_done = false;  // the MCU's tile was written by the whole warp
     if (SHORT && !UNITS && M >= 4 && meff == 1) {
       // one MCU per warp: the whole warp runs lane 0's chain (coefficients contiguous in
-      // the buffer's first 768 B, the window's entries in the next 1 KiB); a full-size tile
+      // the buffer's first 768 B, the window's slots after them); a full-size tile
       // is then transformed and stored by the whole warp, any other is scattered into lane
       // 0's column for the per-lane passes
       if (__shfl_sync(0xFFFFFFFFu, act ? 1 : 0, 0)) {
@@ -890,6 +918,8 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
         const int q0 = __shfl_sync(0xFFFFFFFFu, (int)pr0, 0), q1 = __shfl_sync(0xFFFFFFFFu, (int)pr1, 0),
                   q2 = __shfl_sync(0xFFFFFFFFu, (int)pr2, 0);
         const uint32_t tsa = (uint32_t)__cvta_generic_to_shared(coef) + 768u;
+        constexpr int kWin = M >= 8 ? kWinBits : kWinBits / 2;  // 16 B slots after the 768 B of coefficients
+        static_assert(768 + 16 * kWin <= 768 * M || M < 4, "window slots fit the coefficient buffer");
         const Tables<true> TS{hw, (uint32_t)__cvta_generic_to_shared(sh->t)};
         const Tables<false> TG{hw, 0u};
         // staged whole: every word up to the next MCU's start plus the look-ahead
@@ -898,17 +928,17 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
         const StagedWords SW{W.st, nst0 - 1};
         uint32_t end;
         if (whole && hw == sh->t)
-          end = cw ? decode_mcu_warp<true, true>(SW, b0, TS, nd, q0, q1, q2, coef, tsa, lane)
-                   : decode_mcu_warp<true, false>(SW, b0, TS, nd, q0, q1, q2, coef, tsa, lane);
+          end = cw ? decode_mcu_warp<true, true, kWin>(SW, b0, TS, nd, q0, q1, q2, coef, tsa, lane)
+                   : decode_mcu_warp<true, false, kWin>(SW, b0, TS, nd, q0, q1, q2, coef, tsa, lane);
         else if (whole)
-          end = cw ? decode_mcu_warp<false, true>(SW, b0, TG, nd, q0, q1, q2, coef, tsa, lane)
-                   : decode_mcu_warp<false, false>(SW, b0, TG, nd, q0, q1, q2, coef, tsa, lane);
+          end = cw ? decode_mcu_warp<false, true, kWin>(SW, b0, TG, nd, q0, q1, q2, coef, tsa, lane)
+                   : decode_mcu_warp<false, false, kWin>(SW, b0, TG, nd, q0, q1, q2, coef, tsa, lane);
         else if (hw == sh->t)
-          end = cw ? decode_mcu_warp<true, true>(W, b0, TS, nd, q0, q1, q2, coef, tsa, lane)
-                   : decode_mcu_warp<true, false>(W, b0, TS, nd, q0, q1, q2, coef, tsa, lane);
+          end = cw ? decode_mcu_warp<true, true, kWin>(W, b0, TS, nd, q0, q1, q2, coef, tsa, lane)
+                   : decode_mcu_warp<true, false, kWin>(W, b0, TS, nd, q0, q1, q2, coef, tsa, lane);
         else
-          end = cw ? decode_mcu_warp<false, true>(W, b0, TG, nd, q0, q1, q2, coef, tsa, lane)
-                   : decode_mcu_warp<false, false>(W, b0, TG, nd, q0, q1, q2, coef, tsa, lane);
+          end = cw ? decode_mcu_warp<false, true, kWin>(W, b0, TG, nd, q0, q1, q2, coef, tsa, lane)
+                   : decode_mcu_warp<false, false, kWin>(W, b0, TG, nd, q0, q1, q2, coef, tsa, lane);
         if (lane == 0 && (end == 0xFFFFFFFFu || (uint64_t)w0 * 32 + end > (cpt ? endbit : nbits))) any_bad = true;
         __syncwarp();
         if (__shfl_sync(0xFFFFFFFFu, (red == 0 && store) ? 1 : 0, 0)) {
