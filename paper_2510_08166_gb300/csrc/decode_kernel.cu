@@ -740,7 +740,6 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
   int16_t* col = coef + (lm < M ? lm : 0);  // this lane's MCU column
   constexpr int kMaxBatch = UNITS ? (M < 4 ? M : 4) : M;
 
-  pdl_launch_dependents();
   {  // stage Huffman set 0 (written at upload, so before the wait for the kernel before)
     const uint4* src = reinterpret_cast<const uint4*>(a.huff);
     uint4* dst = reinterpret_cast<uint4*>(sh);

@@ -24,7 +24,9 @@
 namespace jt {
 
 // ---- programmatic dependent launch ----
-// The frame's kernels after the first are launched with programmatic stream serialisation:
+// The frame's compaction (or cache update) and decode are launched with programmatic stream
+// serialisation (colourise is not: its CTAs, launched early, would wait on the SMs the decode
+// is using, and the 4K frame measured 0.181 ms with it against 0.176 ms without):
 // a kernel may start while the one before it in the stream is still running, and waits on
 // the device (pdl_wait) before it reads or writes anything an earlier kernel of the stream
 // produces or consumes. Each kernel lets its dependents launch as soon as it starts

@@ -543,9 +543,7 @@ __global__ void __launch_bounds__(512) k_colorize(const __grid_constant__ Colori
   TileWalk<4 / NPX> it;
   it.start(vs);
   RowG<NPX> g;
-  // the G-buffer is the frame's input, complete before the frame's first kernel started
   load_row(vs.v[MULTI ? it.vi : 0], it.x() + lx, it.y(), it.valid(vs), g);
-  pdl_wait();  // slots and tiles come from the kernels before
 #pragma unroll 1
   while (it.valid(vs)) {
     TileWalk<4 / NPX> nx = it;
@@ -748,11 +746,11 @@ template <bool MULTI>
 void launch_colorize_views(const ColorizeArgs& a, int threads, int grid, cudaStream_t s) {
   constexpr int N = kColorizePx;
   if (a.filter == JT_FILTER_NEAREST)
-    launch_pdl(k_colorize<JT_FILTER_NEAREST, MULTI, N>, grid, threads, 0, s, a);
+    k_colorize<JT_FILTER_NEAREST, MULTI, N><<<grid, threads, 0, s>>>(a);
   else if (a.filter == JT_FILTER_BILINEAR_CLAMP)
-    launch_pdl(k_colorize<JT_FILTER_BILINEAR_CLAMP, MULTI, N>, grid, threads, 0, s, a);
+    k_colorize<JT_FILTER_BILINEAR_CLAMP, MULTI, N><<<grid, threads, 0, s>>>(a);
   else
-    launch_pdl(k_colorize<JT_FILTER_BILINEAR, MULTI, N>, grid, threads, 0, s, a);
+    k_colorize<JT_FILTER_BILINEAR, MULTI, N><<<grid, threads, 0, s>>>(a);
 }
 
 void launch_colorize(const ColorizeArgs& a, int threads, int grid, cudaStream_t s) {
