@@ -773,10 +773,12 @@ __global__ void k_decode(const __grid_constant__ DecodeArgs a) {
     }
     if (base >= count) break;
 
-    {  // clear the coefficient buffer (768 M bytes)
+    {  // clear the coefficient buffer (768 M bytes; a warp-decoded MCU needs only its
+       // contiguous 768 B: every other byte it reads is written first)
       uint4* z = reinterpret_cast<uint4*>(coef);
-#pragma unroll
-      for (int i = lane; i < 48 * M; i += 32) z[i] = make_uint4(0, 0, 0, 0);
+      const int nz = (SHORT && M >= 4 && meff == 1) ? 48 : 48 * M;
+#pragma unroll 4
+      for (int i = lane; i < nz; i += 32) z[i] = make_uint4(0, 0, 0, 0);
     }
 
     // ---- set-up: lanes of MCU slot m < m_eff take item base + m ----
