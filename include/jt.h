@@ -397,7 +397,10 @@ jt_status jt_colorize_float(jt_ctx* ctx, const jt_gbuffer* g, const float* coeff
 /* Adjoint of jt_colorize_float: grad_coeffs = J^T grad_frame, where grad_frame is
  * float32 [height][width][3] (device). grad_coeffs (device, the coefficients' shape) is
  * overwritten: zero except for the MCUs the frame touches. Recomputes the needed set
- * from the G-buffer; stores no decoded blocks. */
+ * from the G-buffer; stores no decoded blocks and no per-texel gradients: the view's
+ * pixels are bucketed under the MCUs their taps touch and each MCU gathers its bucket.
+ * The bucket array (four 32-byte entries per pixel of the view) is grown on the first call
+ * with a larger view, which synchronises the stream once. */
 jt_status jt_colorize_backward(jt_ctx* ctx, const jt_gbuffer* g, const float* grad_frame, float* grad_coeffs,
                                jt_stream stream);
 

@@ -84,6 +84,11 @@ struct jt_ctx {
   uint32_t coef_gid_base = 0;
   float4* float_tiles = nullptr;
   uint32_t float_tile_cap = 0;
+  uint32_t* bucket_cnt = nullptr;   // [float_tile_cap + 1], cleared at the start of each backward call
+  uint32_t* bucket_off = nullptr;   // [float_tile_cap + 1]
+  uint32_t* bucket_bsum = nullptr;  // one per kBucketScan counts
+  uint32_t* bucket = nullptr;       // [bucket_cap] 32-byte entries
+  uint64_t bucket_cap = 0;
   cudaStream_t capture_stream = nullptr;
 
   // scene rasteriser inputs (jt_raster_scene)
@@ -541,6 +546,9 @@ jt_status float_setup(jt_ctx* c, const jt_gbuffer* g, const float* in, const flo
   a.coef_mcus = (uint32_t)((uint64_t)c->coef_count * (c->coef_w / 16) * (c->coef_h / 16));
   a.tiles = c->float_tiles;
   a.tile_cap = c->float_tile_cap;
+  a.bucket_cnt = c->bucket_cnt;
+  a.bucket_off = c->bucket_off;
+  a.bucket_bsum = c->bucket_bsum;
   a.state = c->state;
   // orthonormal 8-point DCT-III basis, A[x][u] = C(u)/2 cos((2x+1) u pi / 16)
   const double pi = 3.14159265358979323846;
@@ -653,6 +661,10 @@ jt_status jt_destroy(jt_ctx* c) {
   cache_free(c);
   dev_free(c->state);
   dev_free(c->float_tiles);
+  dev_free(c->bucket_cnt);
+  dev_free(c->bucket_off);
+  dev_free(c->bucket_bsum);
+  dev_free(c->bucket);
   dev_free(c->raster_buf);
   if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
   for (cudaEvent_t& e : c->prof)
@@ -1347,6 +1359,9 @@ jt_status jt_register_coeff_textures(jt_ctx* c, int first_tex_id, int count, int
   const uint64_t cap = std::min<uint64_t>(per * count, c->cap_units / 4);
   jt_status s;
   if ((s = dev_alloc(c, &c->float_tiles, cap * 256 * sizeof(float4))) != JT_OK) return s;
+  if ((s = dev_alloc(c, &c->bucket_cnt, (cap + 1) * 4)) != JT_OK) return s;
+  if ((s = dev_alloc(c, &c->bucket_off, (cap + 1) * 4)) != JT_OK) return s;
+  if ((s = dev_alloc(c, &c->bucket_bsum, ((cap + 1 + kBucketScan - 1) / kBucketScan) * 4)) != JT_OK) return s;
   c->float_tile_cap = (uint32_t)cap;
   c->coef_gid_base = (uint32_t)c->ngid;
   for (int t = 0; t < count; ++t) {
@@ -1397,13 +1412,22 @@ jt_status jt_colorize_backward(jt_ctx* c, const jt_gbuffer* g, const float* grad
   a.grad_coef = grad_coeffs;
   DeviceGuard dg(c->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // buckets: a pixel's taps touch at most four MCUs (grown here, stream-ordered, when a
+  // larger view comes)
+  const uint64_t need = 4ull * a.views.v[0].width * a.views.v[0].height;
+  if (need > c->bucket_cap) {
+    JT_CUDA(c, cudaStreamSynchronize(st));
+    dev_free(c->bucket);
+    c->bucket_cap = 0;
+    if ((s = dev_alloc(c, &c->bucket, std::max<uint64_t>(need, 1) * 32)) != JT_OK) return s;
+    c->bucket_cap = need;
+  }
+  a.bucket = c->bucket;
+  a.bucket_cap = (uint32_t)std::min<uint64_t>(c->bucket_cap, 0xFFFFFFFFull);
   if ((s = enqueue_float_needed(c, a, st)) != JT_OK) return s;
-  launch_float_zero_tiles(a, c->sm_count * 8, st);
-  if ((s = check_launch(c, "float zero")) != JT_OK) return s;
-  launch_float_scatter(a, c->tuning.pixel_threads, pixel_grid(c, a.views), st);
-  if ((s = check_launch(c, "float scatter")) != JT_OK) return s;
-  launch_float_adjoint(a, c->sm_count * 8, st);
-  if ((s = check_launch(c, "float adjoint")) != JT_OK) return s;
+  JT_CUDA(c, cudaMemsetAsync(c->bucket_cnt, 0, ((size_t)c->float_tile_cap + 1) * 4, st));
+  launch_float_backward(a, c->tuning.pixel_threads, pixel_grid(c, a.views), c->sm_count * 8, st);
+  if ((s = check_launch(c, "float backward")) != JT_OK) return s;
   c->phase = Phase::Idle;
   c->last_stream = st;
   return JT_OK;

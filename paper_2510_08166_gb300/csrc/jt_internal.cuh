@@ -330,14 +330,24 @@ struct FloatArgs {
   float* frame;           // [npx][3]: forward output, or the gradient input of the backward pass
   float* grad_coef;       // [T][my][mx][6][64]: backward output
   FrameState* state;
+  // backward pass: the view's pixels bucketed under the needed MCUs (work positions) their
+  // taps touch; frame is dL/dF
+  uint32_t* bucket_cnt;   // [tile_cap + 1] per-MCU counts, then fill cursors; zero on entry
+  uint32_t* bucket_off;   // [tile_cap + 1] exclusive offsets into bucket
+  uint32_t* bucket_bsum;  // [ceil((tile_cap + 1) / kBucketScan)] per-block sums of the counts
+  uint32_t* bucket;       // [bucket_cap][8]: a pixel's colour^T terms (3 floats), its taps' texels
+                          // (4 bytes), their weights (4 floats, 0 for a tap in another MCU)
+  uint32_t bucket_cap;    // entries, >= 4 pixels of the view (a pixel's taps touch at most 4 MCUs)
   float basis[64];        // A[x][u] = C(u)/2 cos((2x+1)u pi/16), C(0) = 1/sqrt(2); x*8+u
 };
-constexpr int kFloatWarps = 8;  // warps per CTA of the per-MCU float kernels
+// JFIF colour of the float chain: R = Y + kCr2R Cr, G = Y - kCb2G Cb - kCr2G Cr, B = Y + kCb2B Cb
+constexpr float kCr2R = 1.402f, kCb2G = 0.344136f, kCr2G = 0.714136f, kCb2B = 1.772f;
+constexpr int kFloatWarps = 8;     // warps per CTA of the per-MCU float kernels
+constexpr int kBucketScan = 1024;  // counts per CTA of the bucket-offset scan (256 threads x 4)
 void launch_float_tiles(const FloatArgs& a, int grid, cudaStream_t s);
-void launch_float_zero_tiles(const FloatArgs& a, int grid, cudaStream_t s);
-void launch_float_adjoint(const FloatArgs& a, int grid, cudaStream_t s);
 void launch_float_colorize(const FloatArgs& a, int threads, int grid, cudaStream_t s);
-void launch_float_scatter(const FloatArgs& a, int threads, int grid, cudaStream_t s);
+// backward: count pass, offsets, fill pass, then the per-MCU gather and adjoint
+void launch_float_backward(const FloatArgs& a, int threads, int pixel_grid, int mcu_grid, cudaStream_t s);
 
 // The integer IDCT constants the decode kernel is compiled with, for the host-side check
 // against round(8192 cos(k pi / 16)), k = 1..7.

@@ -605,8 +605,9 @@ __global__ void __launch_bounds__(512) k_colorize(const __grid_constant__ Colori
 // ---------------------------------------------------------------------------------------
 // Float chain (differentiable colourise, not in the paper): bilinear taps as above over
 // the float tiles of the coefficient textures; weights (1-fx)(1-fy), fx(1-fy), (1-fx)fy, fx fy.
-// The forward pass blends the four texels; the backward pass scatters w * dL/dF into the
-// four texels' gradient tiles (float4 atomics; their order is the only non-determinism).
+// The forward pass blends the four texels. The backward pass stores nothing per texel: each
+// pixel is bucketed under the needed MCUs its taps touch, and one warp per MCU gathers its
+// bucket (below).
 // ---------------------------------------------------------------------------------------
 struct FloatTaps {
   uint32_t idx[4];  // float4 index into the tiles (tile * 256 + texel)
@@ -643,7 +644,6 @@ __device__ __forceinline__ FloatTaps float_taps(const FloatArgs& a, const Lvl& L
   return T;
 }
 
-template <bool BACKWARD>
 __global__ void k_float_pixels(const __grid_constant__ FloatArgs a) {
   bool missing = false, over = false;
   for_each_quad(a.views, [&](const View& V, int y, int x) {
@@ -659,44 +659,23 @@ __global__ void k_float_pixels(const __grid_constant__ FloatArgs a) {
     float rgb[12];
 #pragma unroll
     for (int i = 0; i < 12; ++i) rgb[i] = 0.f;
-    if (BACKWARD && n > 0) {
-      if (vec) {
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          const float4 g4 = __ldg(reinterpret_cast<const float4*>(fr) + i);
-          rgb[4 * i] = g4.x; rgb[4 * i + 1] = g4.y; rgb[4 * i + 2] = g4.z; rgb[4 * i + 3] = g4.w;
-        }
-      } else {
-#pragma unroll
-        for (int i = 0; i < 12; ++i) rgb[i] = i < 3 * n ? __ldg(fr + i) : 0.f;
-      }
-    }
     for_quad_pixels(a.tl, q, [&](auto p2, const Lvl& L, int i) {
       const FloatTaps T = float_taps<decltype(p2)::value>(a, L, q.key[i], u[i], v[i], missing, over);
-      if (BACKWARD) {
-        if (T.ok) {
+      float r = 0.f, gg = 0.f, b = 0.f;
+      if (T.ok) {
 #pragma unroll
-          for (int k = 0; k < 4; ++k)
-            atomicAdd(a.tiles + T.idx[k], make_float4(T.w[k] * rgb[3 * i], T.w[k] * rgb[3 * i + 1],
-                                                      T.w[k] * rgb[3 * i + 2], 0.f));
+        for (int k = 0; k < 4; ++k) {
+          const float4 c = __ldg(a.tiles + T.idx[k]);
+          r = fmaf(T.w[k], c.x, r);
+          gg = fmaf(T.w[k], c.y, gg);
+          b = fmaf(T.w[k], c.z, b);
         }
-      } else {
-        float r = 0.f, gg = 0.f, b = 0.f;
-        if (T.ok) {
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const float4 c = __ldg(a.tiles + T.idx[k]);
-            r = fmaf(T.w[k], c.x, r);
-            gg = fmaf(T.w[k], c.y, gg);
-            b = fmaf(T.w[k], c.z, b);
-          }
-        }
-        rgb[3 * i] = r;
-        rgb[3 * i + 1] = gg;
-        rgb[3 * i + 2] = b;
       }
+      rgb[3 * i] = r;
+      rgb[3 * i + 1] = gg;
+      rgb[3 * i + 2] = b;
     });
-    if (!BACKWARD && n > 0) {
+    if (n > 0) {
       if (vec) {
 #pragma unroll
         for (int i = 0; i < 3; ++i)
@@ -712,14 +691,298 @@ __global__ void k_float_pixels(const __grid_constant__ FloatArgs a) {
   if (over) atomicOr(&a.state->err, JT_DEVERR_CAPACITY);
 }
 
+
+// ---- Backward pass (the adjoint of the float chain), with no texel-gradient tiles ----
+//
+// dL/dc of a coefficient MCU is A^T g A per data unit, g the MCU's texel gradients after
+// colour^T and upsample^T. Its texel gradients are the w dL/dF of the pixels whose taps fall
+// in it, so the pass inverts the pixel -> MCU map instead of scattering into tiles:
+//   k_float_buckets<false>  per pixel, +1 to the count of each distinct needed MCU among its
+//                           four taps (the MCU's work position, as the forward tiles);
+//   k_bucket_sums, k_bucket_offsets   exclusive offsets of the counts (two passes, the
+//                           second also turns the counts back into zeroed fill cursors);
+//   k_float_buckets<true>   the same visits again, each writing into the MCU's bucket the
+//                           pixel's dL/dF after colour^T (luma, Cb and Cr terms: the colour
+//                           transform is per pixel) and, for each of its four taps, the
+//                           texel and weight when the tap falls in that MCU, weight 0 when
+//                           it does not (32 B);
+//   k_float_gather          one warp per run of coefficient MCUs (every MCU is written once):
+//                           a needed MCU's bucket is read in order, its w-weighted terms are
+//                           added into the MCU's 384 gradients in shared memory (luma per
+//                           texel, chroma per 2x2 sample; shared atomics, upsample^T), then
+//                           A^T g A; an MCU no pixel needs gets zeros.
+// The sums' order (atomics) is the only non-determinism.
+
+template <bool FILL>
+__global__ void k_float_buckets(const __grid_constant__ FloatArgs a) {
+  bool missing = false, over = false;
+  for_each_quad(a.views, [&](const View& V, int y, int x) {
+    float u[4], v[4];
+    uint32_t t[4], m[4];
+    const int n = load_px4(V, y, x, u, v, t, m);
+    QuadLevels q;
+    quad_levels(a.tl, n, t, m, -1, q);
+    const uint32_t p0 = (uint32_t)y * (uint32_t)V.width + (uint32_t)x;
+    for_quad_pixels(a.tl, q, [&](auto p2, const Lvl& L, int i) {
+      const FloatTaps T = float_taps<decltype(p2)::value>(a, L, q.key[i], u[i], v[i], missing, over);
+      if (!T.ok) return;
+      float gy = 0.f, gcb = 0.f, gcr = 0.f;  // colour^T of the pixel's dL/dF
+      if (FILL) {
+        const float* gf = a.frame + 3 * (size_t)(p0 + (uint32_t)i);
+        const float r = __ldg(gf), gg = __ldg(gf + 1), b = __ldg(gf + 2);
+        gy = r + gg + b;
+        gcb = kCb2B * b - kCb2G * gg;
+        gcr = kCr2R * r - kCr2G * gg;
+      }
+      auto visit = [&](uint32_t tile) {
+        if (FILL) {
+          const uint32_t pos = a.bucket_off[tile] + atomicAdd(a.bucket_cnt + tile, 1u);
+          if (pos < a.bucket_cap) {
+            uint32_t texels = 0;
+            float w[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const bool in = (T.idx[k] >> 8) == tile;
+              texels |= (in ? (T.idx[k] & 255u) : 0u) << (8 * k);
+              w[k] = in ? T.w[k] : 0.f;
+            }
+            uint4* e = reinterpret_cast<uint4*>(a.bucket) + 2 * (size_t)pos;
+            e[0] = make_uint4(__float_as_uint(gy), __float_as_uint(gcb), __float_as_uint(gcr), texels);
+            e[1] = make_uint4(__float_as_uint(w[0]), __float_as_uint(w[1]), __float_as_uint(w[2]), __float_as_uint(w[3]));
+          }
+        } else {
+          atomicAdd(a.bucket_cnt + tile, 1u);
+        }
+      };
+      const uint32_t ta = T.idx[0] >> 8, tb = T.idx[1] >> 8, tc = T.idx[2] >> 8, td = T.idx[3] >> 8;
+      visit(ta);
+      if (tb != ta) visit(tb);
+      if (tc != ta && tc != tb) visit(tc);
+      if (td != ta && td != tb && td != tc) visit(td);
+    });
+  });
+  if (!FILL && missing) atomicOr(&a.state->err, JT_DEVERR_MISSING);
+  if (!FILL && over) atomicOr(&a.state->err, JT_DEVERR_CAPACITY);
+}
+
+__device__ __forceinline__ uint32_t needed_tiles(const FloatArgs& a) {
+  return min(*reinterpret_cast<const volatile uint32_t*>(&a.state->count), a.tile_cap);
+}
+
+// Block-wide sum of one value per thread (256 threads).
+__device__ __forceinline__ uint32_t block_sum256(uint32_t v, uint32_t* s_part) {
+  v = __reduce_add_sync(0xFFFFFFFFu, v);
+  if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = v;
+  __syncthreads();
+  uint32_t t = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) t += s_part[i];
+  __syncthreads();
+  return t;
+}
+
+// Counts [b * kBucketScan, (b + 1) * kBucketScan) of the n needed MCUs, four per thread.
+__device__ __forceinline__ uint4 bucket_counts(const FloatArgs& a, uint32_t n, uint32_t first) {
+  uint32_t c[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) c[k] = first + k < n ? a.bucket_cnt[first + k] : 0u;
+  return make_uint4(c[0], c[1], c[2], c[3]);
+}
+
+__global__ void __launch_bounds__(256) k_bucket_sums(const __grid_constant__ FloatArgs a) {
+  __shared__ uint32_t s_part[8];
+  const uint32_t n = needed_tiles(a);
+  const uint4 c = bucket_counts(a, n, blockIdx.x * kBucketScan + threadIdx.x * 4);
+  const uint32_t t = block_sum256(c.x + c.y + c.z + c.w, s_part);
+  if (threadIdx.x == 0) a.bucket_bsum[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(256) k_bucket_offsets(const __grid_constant__ FloatArgs a) {
+  __shared__ uint32_t s_part[8], s_warp[8];
+  const uint32_t n = needed_tiles(a);
+  const uint32_t b = blockIdx.x, first = b * kBucketScan + threadIdx.x * 4;
+  if (b * kBucketScan > n) return;  // past the last offset (index n)
+  uint32_t pre = 0;  // sums of the blocks before this one
+  for (uint32_t j = threadIdx.x; j < b; j += 256) pre += a.bucket_bsum[j];
+  pre = block_sum256(pre, s_part);
+  const uint4 c = bucket_counts(a, n, first);
+  const uint32_t mine = c.x + c.y + c.z + c.w;
+  // block-wide exclusive scan of the threads' sums
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t inc = mine;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, inc, d);
+    if (lane >= d) inc += o;
+  }
+  if (lane == 31) s_warp[warp] = inc;
+  __syncthreads();
+  uint32_t before = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) before += i < warp ? s_warp[i] : 0u;
+  uint32_t off = pre + before + inc - mine;
+  const uint32_t cc[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const uint32_t i = first + k;
+    if (i <= n) a.bucket_off[i] = off;  // index n: the total
+    if (i < n) a.bucket_cnt[i] = 0;      // the fill pass's cursor
+    off += cc[k];
+  }
+}
+
+constexpr uint32_t kGatherChunk = 32;  // consecutive coefficient MCUs per warp task (one per lane)
+
+// The weighted terms of bucket entry (c, wv) added into g (see k_float_gather).
+__device__ __forceinline__ void gather_entry(float* g, const uint4& c, const uint4& wv) {
+  const float gy = __uint_as_float(c.x), gcb = __uint_as_float(c.y), gcr = __uint_as_float(c.z);
+  const float w[4] = {__uint_as_float(wv.x), __uint_as_float(wv.y), __uint_as_float(wv.z), __uint_as_float(wv.w)};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (w[k] == 0.f) continue;  // the tap falls in another MCU (or weighs nothing)
+    const uint32_t t = (c.w >> (8 * k)) & 255u;
+    const uint32_t tx = t & 15u, ty = t >> 4, s = (ty >> 1) * 8 + (tx >> 1);
+    atomicAdd(g + ((ty >> 3) * 2 + (tx >> 3)) * 64 + (ty & 7) * 8 + (tx & 7), w[k] * gy);
+    atomicAdd(g + 256 + s, w[k] * gcb);
+    atomicAdd(g + 320 + s, w[k] * gcr);
+  }
+}
+
+__device__ __forceinline__ void load_entry(const FloatArgs& a, uint32_t e, uint32_t e1, uint4& c, uint4& wv) {
+  if (e < e1) {
+    const uint4* ent = reinterpret_cast<const uint4*>(a.bucket) + 2 * (size_t)e;
+    c = __ldg(ent);
+    wv = __ldg(ent + 1);
+  } else {
+    c = make_uint4(0, 0, 0, 0);
+    wv = make_uint4(0, 0, 0, 0);  // all weights zero: adds nothing
+  }
+}
+
+__global__ void __launch_bounds__(kFloatWarps * 32) k_float_gather(const __grid_constant__ FloatArgs a) {
+  __shared__ __align__(16) float buf[kFloatWarps][2][384];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* g = buf[warp][0];
+  float* s1 = buf[warp][1];
+  // the transforms: lane l owns, in data units d0, d0 + 2, d0 + 4, the four outputs at
+  // columns ug .. ug + 3 of row r (pass 1: rows of g times A; pass 2: A^T times columns)
+  const int ug = 4 * (lane & 1), r = (lane >> 1) & 7, d0 = lane >> 4;
+  float A4[8][4], Ar[8];  // A[x][ug + j]; A[y][r]
+#pragma unroll
+  for (int x = 0; x < 8; ++x) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) A4[x][j] = a.basis[x * 8 + ug + j];
+    Ar[x] = a.basis[x * 8 + r];
+  }
+  const uint32_t count = needed_tiles(a);
+  const uint32_t nchunks = (a.coef_mcus + kGatherChunk - 1) / kGatherChunk;
+  const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (uint32_t ch = blockIdx.x * kFloatWarps + warp; ch < nchunks; ch += gridDim.x * kFloatWarps) {
+    const uint32_t m0 = ch * kGatherChunk, nm = min(kGatherChunk, a.coef_mcus - m0);
+    // lane l: is MCU m0 + l needed? Its work position is its slot when the work list holds
+    // its gid there (slots of MCUs no pixel needs are stale)
+    const uint32_t gid = a.coef_gid_base + m0 + (uint32_t)lane;
+    uint32_t pl = 0, ob = 0, oe = 0;
+    bool nd = false;
+    if ((uint32_t)lane < nm) {
+      pl = __ldg(a.slot + gid);
+      nd = pl < count && __ldg(a.work + pl) == gid;
+    }
+    if (nd) {  // its bucket
+      ob = __ldg(a.bucket_off + pl);
+      oe = min(__ldg(a.bucket_off + pl + 1), a.bucket_cap);
+    }
+    const uint32_t need = __ballot_sync(0xFFFFFFFFu, nd);
+    // MCUs no pixel needs: zeros
+#pragma unroll 1
+    for (uint32_t rest = ((nm == 32 ? 0xFFFFFFFFu : (1u << nm) - 1u)) & ~need; rest; rest &= rest - 1) {
+      float4* dst = reinterpret_cast<float4*>(a.grad_coef + (size_t)(m0 + __ffs(rest) - 1) * 384);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) dst[lane + 32 * i] = z;
+    }
+    // needed MCUs in order; the first 32 entries of the next one are loaded while the
+    // current one is accumulated and transformed
+    uint32_t cur = need;
+    uint4 c, wv;
+    if (cur) {
+      const int i0 = __ffs(cur) - 1;
+      load_entry(a, __shfl_sync(0xFFFFFFFFu, ob, i0) + lane, __shfl_sync(0xFFFFFFFFu, oe, i0), c, wv);
+    }
+#pragma unroll 1
+    while (cur) {
+      const int i = __ffs(cur) - 1;
+      cur &= cur - 1;
+      const uint32_t e0 = __shfl_sync(0xFFFFFFFFu, ob, i), e1 = __shfl_sync(0xFFFFFFFFu, oe, i);
+      uint4 cn = make_uint4(0, 0, 0, 0), wn = make_uint4(0, 0, 0, 0);
+      if (cur) {
+        const int j = __ffs(cur) - 1;
+        load_entry(a, __shfl_sync(0xFFFFFFFFu, ob, j) + lane, __shfl_sync(0xFFFFFFFFu, oe, j), cn, wn);
+      }
+      // the bucket's weighted terms, accumulated in g: luma texel (tx, ty) of data unit
+      // (ty / 8) * 2 + tx / 8 at 64 d + (ty % 8) * 8 + tx % 8; chroma sample (tx / 2, ty / 2)
+      // at 256 + s (Cb) and 320 + s (Cr), the sum over its four texels (upsample^T)
+#pragma unroll
+      for (int k = 0; k < 12; ++k) g[lane + 32 * k] = 0.f;
+      __syncwarp();
+      gather_entry(g, c, wv);
+#pragma unroll 1
+      for (uint32_t e = e0 + 32 + lane; e < e1; e += 32) {  // beyond the first 32 entries
+        uint4 cx, wx;
+        load_entry(a, e, e1, cx, wx);
+        gather_entry(g, cx, wx);
+      }
+      __syncwarp();
+      // pass 1: s1[d][r][u] = sum_x g[d][r][x] A[x][u], u = ug .. ug + 3
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const int o = (d0 + 2 * k) * 64 + r * 8;
+        const float4 ga = *reinterpret_cast<const float4*>(g + o), gb = *reinterpret_cast<const float4*>(g + o + 4);
+        const float gx[8] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z, gb.w};
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int x = 0; x < 8; ++x)
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) acc[jj] = fmaf(gx[x], A4[x][jj], acc[jj]);
+        *reinterpret_cast<float4*>(s1 + o + ug) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+      }
+      __syncwarp();
+      // pass 2: grad[d][r][u] = sum_y A[y][r] s1[d][y][u], u = ug .. ug + 3
+      float* out = a.grad_coef + (size_t)(m0 + (uint32_t)i) * 384;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const int d = d0 + 2 * k;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int y = 0; y < 8; ++y) {
+          const float4 sv = *reinterpret_cast<const float4*>(s1 + d * 64 + y * 8 + ug);
+          acc[0] = fmaf(Ar[y], sv.x, acc[0]);
+          acc[1] = fmaf(Ar[y], sv.y, acc[1]);
+          acc[2] = fmaf(Ar[y], sv.z, acc[2]);
+          acc[3] = fmaf(Ar[y], sv.w, acc[3]);
+        }
+        *reinterpret_cast<float4*>(out + d * 64 + r * 8 + ug) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+      }
+      __syncwarp();
+      c = cn;
+      wv = wn;
+    }
+  }
+}
 }  // namespace
 
 void launch_float_colorize(const FloatArgs& a, int threads, int grid, cudaStream_t s) {
-  k_float_pixels<false><<<grid, threads, 0, s>>>(a);
+  k_float_pixels<<<grid, threads, 0, s>>>(a);
 }
 
-void launch_float_scatter(const FloatArgs& a, int threads, int grid, cudaStream_t s) {
-  k_float_pixels<true><<<grid, threads, 0, s>>>(a);
+// The backward pass after the needed set and its compaction; bucket_cnt must be zero on
+// entry.
+void launch_float_backward(const FloatArgs& a, int threads, int pixel_grid, int mcu_grid, cudaStream_t s) {
+  const int sblocks = (int)((a.tile_cap + 1 + kBucketScan - 1) / kBucketScan);
+  k_float_buckets<false><<<pixel_grid, threads, 0, s>>>(a);
+  k_bucket_sums<<<sblocks, 256, 0, s>>>(a);
+  k_bucket_offsets<<<sblocks, 256, 0, s>>>(a);
+  k_float_buckets<true><<<pixel_grid, threads, 0, s>>>(a);
+  k_float_gather<<<mcu_grid, kFloatWarps * 32, 0, s>>>(a);
 }
 
 void launch_mark(const MarkArgs& a, int threads, int grid, cudaStream_t s) {

@@ -145,5 +145,11 @@ def test_float_errors(jt):
     small.colorize_float(dgb, c, F)
     st = small.stats(check=False)
     assert st["status"] == 5 and st["error_bits"] & jt.DEVERR_CAPACITY
+    # the same for the backward pass, whose gradient then covers only the MCUs that fit
+    gC = torch.full_like(c, 7.0)
+    small.colorize_backward(dgb, torch.ones_like(F), gC)
+    st = small.stats(check=False)
+    assert st["status"] == 5 and st["error_bits"] & jt.DEVERR_CAPACITY
+    assert torch.isfinite(gC).all() and int((gC.abs().sum(dim=(3, 4)) != 0).sum()) <= 4
     small.close()
     ctx.close()
