@@ -433,13 +433,14 @@ def run_views(ctx, ts, jt, dev, flush, stream, steps):
             "blocks_per_s": union / (ms_graph * 1e-3)}
 
 
-def run_e2e_pipelined(ctx, jt, host, W, H, dev, frames):
+def run_e2e_pipelined(ctx, jt, host, W, H, dev, frames, render=True):
     """Frames streamed from host buffers with the copies overlapped: two device G-buffers and
     framebuffers (one CUDA graph each); frame k's upload runs on an upload stream while frame
     k - 1 renders, and frame k - 1's download on a download stream while frame k renders.
     Returns ms per frame over `frames` frames (first upload to last download) and whether the
     downloaded frames equal the reference. Every frame's G-buffer is freshly uploaded, and
-    the two buffer sets with their framebuffers (250 MB) exceed L2."""
+    the two buffer sets with their framebuffers (250 MB) exceed L2. render=False runs the
+    same copies with no frame in between: the copy bound of the loop."""
     import torch
     uv_h, tex_h, mip_h, out_ref = host
     gbs = [jt.DeviceGBuffer.empty(W, H, dev) for _ in range(2)]
@@ -466,7 +467,8 @@ def run_e2e_pipelined(ctx, jt, host, W, H, dev, frames):
         s_gpu.wait_event(ev_up[i])
         if k >= 2:
             s_gpu.wait_event(ev_dn[i])  # frame k - 2's framebuffer has been downloaded
-        ctx.graph_launch(graphs[i], s_gpu)
+        if render:
+            ctx.graph_launch(graphs[i], s_gpu)
         ev_done[i].record(s_gpu)
         s_dn.wait_event(ev_done[i])
         with torch.cuda.stream(s_dn):
@@ -922,6 +924,8 @@ def run_gpu(args, rank, world, local_rank):
     # the same frames with the copies overlapped with rendering (the serving pattern)
     pipe_ms, pipe_same = run_e2e_pipelined(ctx, jt, (uv_h, tex_h, mip_h, out.cpu()), gb.width, gb.height, dev,
                                            max(10, min(args.steps, 200)))
+    copy_ms, _ = run_e2e_pipelined(ctx, jt, (uv_h, tex_h, mip_h, out.cpu()), gb.width, gb.height, dev,
+                                   max(10, min(args.steps, 200)), render=False)
 
     # the per-texture "plain" pipeline for comparison (same output)
     ref_out = out.clone()
@@ -990,7 +994,9 @@ def run_gpu(args, rank, world, local_rank):
             "e2e_pipelined": {"value": world * nblocks / (pipe_ms * 1e-3), "unit": UNIT, "ms_per_step": pipe_ms,
                               "same_output": pipe_same, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                               "how": "double-buffered G-buffers and framebuffers, uploads and downloads on their "
-                                     "own streams overlapped with the previous / next frame's graph"},
+                                     "own streams overlapped with the previous / next frame's graph",
+                              "copy_only_ms": copy_ms, "frame_ms": frame_ms,
+                              "over_bound": pipe_ms / max(copy_ms, frame_ms)},
             "plain": {"ms_per_frame": statistics.mean(plain_ms), "same_output": plain_same,
                       "graph_speedup": statistics.mean(plain_ms) / frame_ms},
             "gpu_launches": LAUNCHES_PER_FRAME * args.steps,
