@@ -816,6 +816,13 @@ def run_gpu(args, rank, world, local_rank):
 
     if args.only == "motion":
         return run_only_motion(args, local_rank) if rank == 0 else 0
+    if args.only == "adjoint":
+        if rank == 0:
+            torch.cuda.set_device(local_rank)
+            dev = torch.device("cuda", local_rank)
+            out = run_adjoint(jt, dev, L2Flush(dev), torch.cuda.current_stream(dev), args.steps, peaks()[0])
+            print(json.dumps({"adjoint": out}), flush=True)
+        return 0
     ts, gb = workload(compact=not args.no_extra)
     pool = ts4 = None
     if rank == 0 and world == 1 and not args.no_cpu and not args.quick:
@@ -1040,8 +1047,9 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the batched-views and adjoint measurements")
     ap.add_argument("--full-decode-textures", type=int, default=256,
                     help="textures of the full-decode leg (256 is the stated configuration)")
-    ap.add_argument("--only", choices=["motion"], default=None,
-                    help="run one leg alone and print its JSON (motion: the 1080p and VR motion legs)")
+    ap.add_argument("--only", choices=["motion", "adjoint"], default=None,
+                    help="run one leg alone and print its JSON (motion: the 1080p and VR motion legs; "
+                         "adjoint: the float chain's forward and backward on config 5)")
     ap.add_argument("--motion-reps", type=int, default=100,
                     help="turns of the motion legs after the warm-up turn (100 is the paper's protocol)")
     args = ap.parse_args()
