@@ -831,7 +831,10 @@ __global__ void __launch_bounds__(256) k_bucket_offsets(const __grid_constant__ 
   }
 }
 
-constexpr uint32_t kGatherChunk = 32;  // consecutive coefficient MCUs per warp task (one per lane)
+// consecutive coefficient MCUs per warp task (lane l < kGatherChunk checks MCU l): 16 rather
+// than 32 spreads the 262,144 MCUs of config 5 over twice the tasks, so the last wave of the
+// grid is less empty (backward 0.312 against 0.364 ms)
+constexpr uint32_t kGatherChunk = 16;
 
 // The weighted terms of bucket entry (c, wv) added into g (see k_float_gather).
 __device__ __forceinline__ void gather_entry(float* g, const uint4& c, const uint4& wv) {
