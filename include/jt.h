@@ -332,7 +332,9 @@ jt_status jt_set_block_cache(jt_ctx* ctx, int persistent);
  * captured while enabled) records CUDA events on its stream at the pass boundaries; the
  * events belong to the context. jt_profile_read waits for the last recorded frame and
  * returns its durations in milliseconds: ms[0] mark, ms[1] compaction, ms[2] decode,
- * ms[3] colourise. */
+ * ms[3] colourise. The events between the passes also keep the compaction and the decode
+ * from starting before the pass ahead of them ends (programmatic launch), so a profiled
+ * frame takes longer than an unprofiled one. */
 jt_status jt_profile(jt_ctx* ctx, int enable);
 jt_status jt_profile_read(jt_ctx* ctx, float ms[4]);
 
