@@ -392,7 +392,11 @@ jt_status jt_register_coeff_textures(jt_ctx* ctx, int first_tex_id, int count, i
 /* Forward of the float chain F = bilinear(RGB(upsample(IDCT_f(c) + 128))) with the
  * orthonormal 8x8 IDCT, JFIF colour matrix, chroma replication and bilinear weights of
  * jt_colorize, without rounding or clamping. coeffs: device float32 as registered;
- * out_rgb: device float32 [height][width][3]; empty pixels get 0. */
+ * out_rgb: device float32 [height][width][3], overwritten; empty pixels get 0. The view's
+ * pixels are bucketed under the MCUs their taps touch (as in jt_colorize_backward); the sum
+ * of a pixel whose taps span two or more MCUs is added in float atomics, so its last bits
+ * may differ between calls. At most max_cache_blocks needed coefficient MCUs are served;
+ * beyond that the error word gets JT_DEVERR_CAPACITY and those pixels get 0. */
 jt_status jt_colorize_float(jt_ctx* ctx, const jt_gbuffer* g, const float* coeffs, float* out_rgb,
                             jt_stream stream);
 

@@ -82,8 +82,7 @@ struct jt_ctx {
   // coefficient textures (float chain)
   int coef_first = -1, coef_count = 0, coef_w = 0, coef_h = 0;
   uint32_t coef_gid_base = 0;
-  float4* float_tiles = nullptr;
-  uint32_t float_tile_cap = 0;
+  uint32_t float_tile_cap = 0;     // needed coefficient MCUs a float pass can serve
   uint32_t* bucket_cnt = nullptr;   // [float_tile_cap + 1], cleared at the start of each backward call
   uint32_t* bucket_off = nullptr;   // [float_tile_cap + 1]
   uint32_t* bucket_bsum = nullptr;  // one per kBucketScan counts
@@ -544,7 +543,6 @@ jt_status float_setup(jt_ctx* c, const jt_gbuffer* g, const float* in, const flo
   a.work = c->work;
   a.coef_gid_base = c->coef_gid_base;
   a.coef_mcus = (uint32_t)((uint64_t)c->coef_count * (c->coef_w / 16) * (c->coef_h / 16));
-  a.tiles = c->float_tiles;
   a.tile_cap = c->float_tile_cap;
   a.bucket_cnt = c->bucket_cnt;
   a.bucket_off = c->bucket_off;
@@ -558,11 +556,25 @@ jt_status float_setup(jt_ctx* c, const jt_gbuffer* g, const float* in, const flo
   return JT_OK;
 }
 
-// Needed set of the coefficient textures (bilinear taps) and its compaction.
-jt_status enqueue_float_needed(jt_ctx* c, const FloatArgs& a, cudaStream_t st) {
+// Needed set of the coefficient textures (bilinear taps) and its compaction, then the
+// buckets' room (a pixel's taps touch at most four MCUs; grown, stream-ordered, when a larger
+// view comes) and their zeroed counts.
+jt_status enqueue_float_needed(jt_ctx* c, FloatArgs& a, cudaStream_t st) {
   jt_status s;
+  const uint64_t need = 4ull * a.views.v[0].width * a.views.v[0].height;
+  if (need > c->bucket_cap) {
+    JT_CUDA(c, cudaStreamSynchronize(st));
+    dev_free(c->bucket);
+    c->bucket_cap = 0;
+    if ((s = dev_alloc(c, &c->bucket, std::max<uint64_t>(need, 1) * 32)) != JT_OK) return s;
+    c->bucket_cap = need;
+  }
+  a.bucket = c->bucket;
+  a.bucket_cap = (uint32_t)std::min<uint64_t>(c->bucket_cap, 0xFFFFFFFFull);
   if ((s = enqueue_mark(c, a.views, JT_FILTER_BILINEAR, -1, 1, st)) != JT_OK) return s;
-  return enqueue_scan(c, c->coef_gid_base, (uint64_t)c->coef_gid_base + a.coef_mcus, st);
+  if ((s = enqueue_scan(c, c->coef_gid_base, (uint64_t)c->coef_gid_base + a.coef_mcus, st)) != JT_OK) return s;
+  JT_CUDA(c, cudaMemsetAsync(c->bucket_cnt, 0, ((size_t)c->float_tile_cap + 1) * 4, st));
+  return JT_OK;
 }
 
 }  // namespace
@@ -660,7 +672,6 @@ jt_status jt_destroy(jt_ctx* c) {
   dev_free(c->d_desc_of_gid);
   cache_free(c);
   dev_free(c->state);
-  dev_free(c->float_tiles);
   dev_free(c->bucket_cnt);
   dev_free(c->bucket_off);
   dev_free(c->bucket_bsum);
@@ -1358,7 +1369,6 @@ jt_status jt_register_coeff_textures(jt_ctx* c, int first_tex_id, int count, int
   if (!dg.ok) return fail(c, JT_ERR_CUDA, "cannot select device %d", c->device);
   const uint64_t cap = std::min<uint64_t>(per * count, c->cap_units / 4);
   jt_status s;
-  if ((s = dev_alloc(c, &c->float_tiles, cap * 256 * sizeof(float4))) != JT_OK) return s;
   if ((s = dev_alloc(c, &c->bucket_cnt, (cap + 1) * 4)) != JT_OK) return s;
   if ((s = dev_alloc(c, &c->bucket_off, (cap + 1) * 4)) != JT_OK) return s;
   if ((s = dev_alloc(c, &c->bucket_bsum, ((cap + 1 + kBucketScan - 1) / kBucketScan) * 4)) != JT_OK) return s;
@@ -1393,10 +1403,9 @@ jt_status jt_colorize_float(jt_ctx* c, const jt_gbuffer* g, const float* coeffs,
   DeviceGuard dg(c->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if ((s = enqueue_float_needed(c, a, st)) != JT_OK) return s;
-  launch_float_tiles(a, c->sm_count * 8, st);
-  if ((s = check_launch(c, "float tiles")) != JT_OK) return s;
-  launch_float_colorize(a, c->tuning.pixel_threads, pixel_grid(c, a.views), st);
-  if ((s = check_launch(c, "float colourise")) != JT_OK) return s;
+  JT_CUDA(c, cudaMemsetAsync(out_rgb, 0, (size_t)a.views.v[0].width * a.views.v[0].height * 3 * sizeof(float), st));
+  launch_float_forward(a, c->tuning.pixel_threads, pixel_grid(c, a.views), c->sm_count * 8, st);
+  if ((s = check_launch(c, "float forward")) != JT_OK) return s;
   c->phase = Phase::Idle;  // the work list now describes coefficient MCUs
   c->last_stream = st;
   return JT_OK;
@@ -1412,20 +1421,7 @@ jt_status jt_colorize_backward(jt_ctx* c, const jt_gbuffer* g, const float* grad
   a.grad_coef = grad_coeffs;
   DeviceGuard dg(c->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  // buckets: a pixel's taps touch at most four MCUs (grown here, stream-ordered, when a
-  // larger view comes)
-  const uint64_t need = 4ull * a.views.v[0].width * a.views.v[0].height;
-  if (need > c->bucket_cap) {
-    JT_CUDA(c, cudaStreamSynchronize(st));
-    dev_free(c->bucket);
-    c->bucket_cap = 0;
-    if ((s = dev_alloc(c, &c->bucket, std::max<uint64_t>(need, 1) * 32)) != JT_OK) return s;
-    c->bucket_cap = need;
-  }
-  a.bucket = c->bucket;
-  a.bucket_cap = (uint32_t)std::min<uint64_t>(c->bucket_cap, 0xFFFFFFFFull);
   if ((s = enqueue_float_needed(c, a, st)) != JT_OK) return s;
-  JT_CUDA(c, cudaMemsetAsync(c->bucket_cnt, 0, ((size_t)c->float_tile_cap + 1) * 4, st));
   launch_float_backward(a, c->tuning.pixel_threads, pixel_grid(c, a.views), c->sm_count * 8, st);
   if ((s = check_launch(c, "float backward")) != JT_OK) return s;
   c->phase = Phase::Idle;

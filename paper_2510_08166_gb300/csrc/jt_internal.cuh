@@ -325,18 +325,17 @@ struct FloatArgs {
   const float* coef;      // [T][my][mx][6][64], natural order k = v*8+u
   uint32_t coef_gid_base; // gid of coefficient texture 0, MCU 0
   uint32_t coef_mcus;     // MCUs of all coefficient textures
-  float4* tiles;          // [tile_cap][16][16] float4 (R, G, B, 0): forward texels or their gradients
-  uint32_t tile_cap;
-  float* frame;           // [npx][3]: forward output, or the gradient input of the backward pass
+  uint32_t tile_cap;      // needed coefficient MCUs a pass can serve (more: JT_DEVERR_CAPACITY)
+  float* frame;           // [npx][3]: forward output (zero on entry), or the backward's dL/dF
   float* grad_coef;       // [T][my][mx][6][64]: backward output
   FrameState* state;
-  // backward pass: the view's pixels bucketed under the needed MCUs (work positions) their
-  // taps touch; frame is dL/dF
+  // the view's pixels bucketed under the needed MCUs (work positions) their taps touch
   uint32_t* bucket_cnt;   // [tile_cap + 1] per-MCU counts, then fill cursors; zero on entry
   uint32_t* bucket_off;   // [tile_cap + 1] exclusive offsets into bucket
   uint32_t* bucket_bsum;  // [ceil((tile_cap + 1) / kBucketScan)] per-block sums of the counts
-  uint32_t* bucket;       // [bucket_cap][8]: a pixel's colour^T terms (3 floats), its taps' texels
-                          // (4 bytes), their weights (4 floats, 0 for a tap in another MCU)
+  uint32_t* bucket;       // [bucket_cap][8]: the pixel's index (forward) or its colour^T terms
+                          // (3 floats, backward), its taps' texels (4 bytes), their weights
+                          // (4 floats, 0 for a tap in another MCU)
   uint32_t bucket_cap;    // entries, >= 4 pixels of the view (a pixel's taps touch at most 4 MCUs)
   float basis[64];        // A[x][u] = C(u)/2 cos((2x+1)u pi/16), C(0) = 1/sqrt(2); x*8+u
 };
@@ -344,9 +343,9 @@ struct FloatArgs {
 constexpr float kCr2R = 1.402f, kCb2G = 0.344136f, kCr2G = 0.714136f, kCb2B = 1.772f;
 constexpr int kFloatWarps = 8;     // warps per CTA of the per-MCU float kernels
 constexpr int kBucketScan = 1024;  // counts per CTA of the bucket-offset scan (256 threads x 4)
-void launch_float_tiles(const FloatArgs& a, int grid, cudaStream_t s);
-void launch_float_colorize(const FloatArgs& a, int threads, int grid, cudaStream_t s);
-// backward: count pass, offsets, fill pass, then the per-MCU gather and adjoint
+// count pass, offsets, fill pass, then the per-MCU gather (forward: weighted texels into the
+// pixels; backward: the adjoint into the coefficients)
+void launch_float_forward(const FloatArgs& a, int threads, int pixel_grid, int mcu_grid, cudaStream_t s);
 void launch_float_backward(const FloatArgs& a, int threads, int pixel_grid, int mcu_grid, cudaStream_t s);
 
 // The integer IDCT constants the decode kernel is compiled with, for the host-side check

@@ -603,11 +603,12 @@ __global__ void __launch_bounds__(512) k_colorize(const __grid_constant__ Colori
 }
 
 // ---------------------------------------------------------------------------------------
-// Float chain (differentiable colourise, not in the paper): bilinear taps as above over
-// the float tiles of the coefficient textures; weights (1-fx)(1-fy), fx(1-fy), (1-fx)fy, fx fy.
-// The forward pass blends the four texels. The backward pass stores nothing per texel: each
-// pixel is bucketed under the needed MCUs its taps touch, and one warp per MCU gathers its
-// bucket (below).
+// Float chain (differentiable colourise, not in the paper): bilinear taps as above over the
+// texels of the coefficient textures; weights (1-fx)(1-fy), fx(1-fy), (1-fx)fy, fx fy. Neither
+// pass stores anything per texel: each pixel is bucketed under the needed MCUs its taps touch,
+// and one warp per MCU transforms it once and serves its bucket (below): the forward adds the
+// weighted texels into the pixels' values, the backward the pixels' weighted gradients into
+// the MCU's.
 // ---------------------------------------------------------------------------------------
 struct FloatTaps {
   uint32_t idx[4];  // float4 index into the tiles (tile * 256 + texel)
@@ -644,77 +645,35 @@ __device__ __forceinline__ FloatTaps float_taps(const FloatArgs& a, const Lvl& L
   return T;
 }
 
-__global__ void k_float_pixels(const __grid_constant__ FloatArgs a) {
-  bool missing = false, over = false;
-  for_each_quad(a.views, [&](const View& V, int y, int x) {
-    float u[4], v[4];
-    uint32_t t[4], m[4];
-    const int n = load_px4(V, y, x, u, v, t, m);
-    QuadLevels q;
-    quad_levels(a.tl, n, t, m, -1, q);
-    // every lane goes on to for_quad_pixels (it may vote); lanes without pixels touch no memory
-    const uint32_t p0 = (uint32_t)y * (uint32_t)V.width + (uint32_t)x;
-    float* fr = a.frame + (size_t)p0 * 3;  // 12 floats of the quad, 16-byte aligned when p0 % 4 == 0
-    const bool vec = n == 4 && (V.width & 3) == 0;
-    float rgb[12];
-#pragma unroll
-    for (int i = 0; i < 12; ++i) rgb[i] = 0.f;
-    for_quad_pixels(a.tl, q, [&](auto p2, const Lvl& L, int i) {
-      const FloatTaps T = float_taps<decltype(p2)::value>(a, L, q.key[i], u[i], v[i], missing, over);
-      float r = 0.f, gg = 0.f, b = 0.f;
-      if (T.ok) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const float4 c = __ldg(a.tiles + T.idx[k]);
-          r = fmaf(T.w[k], c.x, r);
-          gg = fmaf(T.w[k], c.y, gg);
-          b = fmaf(T.w[k], c.z, b);
-        }
-      }
-      rgb[3 * i] = r;
-      rgb[3 * i + 1] = gg;
-      rgb[3 * i + 2] = b;
-    });
-    if (n > 0) {
-      if (vec) {
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-          reinterpret_cast<float4*>(fr)[i] = make_float4(rgb[4 * i], rgb[4 * i + 1], rgb[4 * i + 2], rgb[4 * i + 3]);
-      } else {
-#pragma unroll
-        for (int i = 0; i < 12; ++i)
-          if (i < 3 * n) fr[i] = rgb[i];
-      }
-    }
-  });
-  if (missing) atomicOr(&a.state->err, JT_DEVERR_MISSING);
-  if (over) atomicOr(&a.state->err, JT_DEVERR_CAPACITY);
-}
-
-
-// ---- Backward pass (the adjoint of the float chain), with no texel-gradient tiles ----
+// ---- Forward and backward passes over buckets of pixels per MCU ----
 //
-// dL/dc of a coefficient MCU is A^T g A per data unit, g the MCU's texel gradients after
-// colour^T and upsample^T. Its texel gradients are the w dL/dF of the pixels whose taps fall
-// in it, so the pass inverts the pixel -> MCU map instead of scattering into tiles:
-//   k_float_buckets<false>  per pixel, +1 to the count of each distinct needed MCU among its
-//                           four taps (the MCU's work position, as the forward tiles);
+// F at a pixel is sum_k w_k colour(texel_k), each texel from f = A c A^T of its MCU; dL/dc of a
+// coefficient MCU is A^T g A per data unit, g the MCU's texel gradients after colour^T and
+// upsample^T, and those are the w dL/dF of the pixels whose taps fall in it. Both passes
+// therefore invert the pixel -> MCU map rather than going through per-texel tiles:
+//   k_float_buckets<count>  per pixel, +1 to the count of each distinct needed MCU among its
+//                           four taps (the MCU's work position);
 //   k_bucket_sums, k_bucket_offsets   exclusive offsets of the counts (two passes, the
 //                           second also turns the counts back into zeroed fill cursors);
-//   k_float_buckets<true>   the same visits again, each writing into the MCU's bucket the
-//                           pixel's dL/dF after colour^T (luma, Cb and Cr terms: the colour
-//                           transform is per pixel) and, for each of its four taps, the
-//                           texel and weight when the tap falls in that MCU, weight 0 when
-//                           it does not (32 B);
-//   k_float_gather          one warp per run of coefficient MCUs (every MCU is written once):
-//                           a needed MCU's bucket is read in order, its w-weighted terms are
-//                           added into the MCU's 384 gradients in shared memory (luma per
-//                           texel, chroma per 2x2 sample; shared atomics, upsample^T), then
-//                           A^T g A; an MCU no pixel needs gets zeros.
+//   k_float_buckets<fill>   the same visits again, each writing a 32 B entry into the MCU's
+//                           bucket: for each of the pixel's four taps the texel and weight when
+//                           the tap falls in that MCU (weight 0 when it does not), and the
+//                           pixel's index (forward) or its dL/dF after colour^T (backward:
+//                           luma, Cb and Cr terms; the colour transform is per pixel);
+//   k_float_gather_fwd      one warp per run of coefficient MCUs: a needed MCU is transformed
+//                           once in shared memory and its bucket's pixels get their weighted
+//                           texels added into their values (global atomics);
+//   k_float_gather          one warp per run of coefficient MCUs (every MCU written once): a
+//                           needed MCU's bucket terms are added into its 384 gradients in
+//                           shared memory (luma per texel, chroma per 2x2 sample; shared
+//                           atomics, upsample^T), then A^T g A; an MCU no pixel needs gets zeros.
 // The sums' order (atomics) is the only non-determinism.
 
-template <bool FILL>
+constexpr int kBucketCount = 0, kBucketGrad = 1, kBucketPixel = 2;
+
+template <int MODE>
 __global__ void k_float_buckets(const __grid_constant__ FloatArgs a) {
+  constexpr bool FILL = MODE != kBucketCount;
   bool missing = false, over = false;
   for_each_quad(a.views, [&](const View& V, int y, int x) {
     float u[4], v[4];
@@ -727,7 +686,7 @@ __global__ void k_float_buckets(const __grid_constant__ FloatArgs a) {
       const FloatTaps T = float_taps<decltype(p2)::value>(a, L, q.key[i], u[i], v[i], missing, over);
       if (!T.ok) return;
       float gy = 0.f, gcb = 0.f, gcr = 0.f;  // colour^T of the pixel's dL/dF
-      if (FILL) {
+      if (MODE == kBucketGrad) {
         const float* gf = a.frame + 3 * (size_t)(p0 + (uint32_t)i);
         const float r = __ldg(gf), gg = __ldg(gf + 1), b = __ldg(gf + 2);
         gy = r + gg + b;
@@ -747,7 +706,9 @@ __global__ void k_float_buckets(const __grid_constant__ FloatArgs a) {
               w[k] = in ? T.w[k] : 0.f;
             }
             uint4* e = reinterpret_cast<uint4*>(a.bucket) + 2 * (size_t)pos;
-            e[0] = make_uint4(__float_as_uint(gy), __float_as_uint(gcb), __float_as_uint(gcr), texels);
+            e[0] = MODE == kBucketGrad
+                       ? make_uint4(__float_as_uint(gy), __float_as_uint(gcb), __float_as_uint(gcr), texels)
+                       : make_uint4(p0 + (uint32_t)i, 0u, 0u, texels);
             e[1] = make_uint4(__float_as_uint(w[0]), __float_as_uint(w[1]), __float_as_uint(w[2]), __float_as_uint(w[3]));
           }
         } else {
@@ -971,20 +932,118 @@ __global__ void __launch_bounds__(kFloatWarps * 32) k_float_gather(const __grid_
     }
   }
 }
-}  // namespace
 
-void launch_float_colorize(const FloatArgs& a, int threads, int grid, cudaStream_t s) {
-  k_float_pixels<<<grid, threads, 0, s>>>(a);
+// Forward gather: one warp per run of kGatherChunk coefficient MCUs; each needed MCU is
+// transformed once in shared memory (f = A c A^T per data unit, two passes) and each pixel of
+// its bucket gets, added into its frame value (zeroed before), the sum over its taps in this
+// MCU of w times the texel's colour (computed from f on demand: Y = f + 128, chroma of the
+// 2x2 sample, the JFIF matrix; the same fp32 operations as the per-texel form). A pixel whose
+// taps all lie in one MCU gets exactly the fused sum in tap order.
+__global__ void __launch_bounds__(kFloatWarps * 32) k_float_gather_fwd(const __grid_constant__ FloatArgs a) {
+  __shared__ __align__(16) float buf[kFloatWarps][2][384];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* c = buf[warp][0];
+  float* t = buf[warp][1];
+  const int x = lane & 7, y0 = lane >> 3;
+  float Ax[8], Ay0[8], Ay1[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    Ax[k] = a.basis[x * 8 + k];
+    Ay0[k] = a.basis[y0 * 8 + k];
+    Ay1[k] = a.basis[(y0 + 4) * 8 + k];
+  }
+  const uint32_t count = needed_tiles(a);
+  const uint32_t nchunks = (a.coef_mcus + kGatherChunk - 1) / kGatherChunk;
+  for (uint32_t ch = blockIdx.x * kFloatWarps + warp; ch < nchunks; ch += gridDim.x * kFloatWarps) {
+    const uint32_t m0 = ch * kGatherChunk, nm = min(kGatherChunk, a.coef_mcus - m0);
+    const uint32_t gid = a.coef_gid_base + m0 + (uint32_t)lane;
+    uint32_t pl = 0, ob = 0, oe = 0;
+    bool nd = false;
+    if ((uint32_t)lane < nm) {
+      pl = __ldg(a.slot + gid);
+      nd = pl < count && __ldg(a.work + pl) == gid;
+    }
+    if (nd) {
+      ob = __ldg(a.bucket_off + pl);
+      oe = min(__ldg(a.bucket_off + pl + 1), a.bucket_cap);
+    }
+#pragma unroll 1
+    for (uint32_t cur = __ballot_sync(0xFFFFFFFFu, nd); cur; cur &= cur - 1) {
+      const int i = __ffs(cur) - 1;
+      const uint32_t m = m0 + (uint32_t)i;
+      const uint32_t e0 = __shfl_sync(0xFFFFFFFFu, ob, i), e1 = __shfl_sync(0xFFFFFFFFu, oe, i);
+      const float4* src = reinterpret_cast<const float4*>(a.coef + (size_t)m * 384);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) reinterpret_cast<float4*>(c)[lane + 32 * k] = __ldg(src + lane + 32 * k);
+      __syncwarp();
+      // pass 1: t[d][v][x] = sum_u A[x][u] c[d][v][u]
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        const int o = lane + 32 * k;
+        const float* row = c + (o & ~7);
+        float sum = 0.f;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) sum = fmaf(Ax[u], row[u], sum);
+        t[o] = sum;
+      }
+      __syncwarp();
+      // pass 2: f[d][y][x] = sum_v A[y][v] t[d][v][x]  (y = y0 for even k, y0 + 4 for odd k)
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        const int o = lane + 32 * k;
+        const float* col = t + (o & ~63) + x;
+        float sum = 0.f;
+#pragma unroll
+        for (int v = 0; v < 8; ++v) sum = fmaf((k & 1) ? Ay1[v] : Ay0[v], col[v * 8], sum);
+        c[o] = sum;
+      }
+      __syncwarp();
+#pragma unroll 1
+      for (uint32_t e = e0 + lane; e < e1; e += 32) {
+        const uint4* ent = reinterpret_cast<const uint4*>(a.bucket) + 2 * (size_t)e;
+        const uint4 ce = __ldg(ent), wv = __ldg(ent + 1);
+        const float w[4] = {__uint_as_float(wv.x), __uint_as_float(wv.y), __uint_as_float(wv.z), __uint_as_float(wv.w)};
+        float r = 0.f, gg = 0.f, b = 0.f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (w[k] == 0.f) continue;  // the tap falls in another MCU (or weighs nothing)
+          const uint32_t tq = (ce.w >> (8 * k)) & 255u, tx = tq & 15u, ty = tq >> 4;
+          const float Y = c[((ty >> 3) * 2 + (tx >> 3)) * 64 + (ty & 7) * 8 + (tx & 7)] + 128.f;
+          const uint32_t ci = (ty >> 1) * 8 + (tx >> 1);
+          const float cb = c[256 + ci], cr = c[320 + ci];
+          r = fmaf(w[k], Y + kCr2R * cr, r);
+          gg = fmaf(w[k], Y - kCb2G * cb - kCr2G * cr, gg);
+          b = fmaf(w[k], Y + kCb2B * cb, b);
+        }
+        float* out = a.frame + 3 * (size_t)ce.x;
+        atomicAdd(out, r);
+        atomicAdd(out + 1, gg);
+        atomicAdd(out + 2, b);
+      }
+      __syncwarp();
+    }
+  }
 }
 
-// The backward pass after the needed set and its compaction; bucket_cnt must be zero on
-// entry.
-void launch_float_backward(const FloatArgs& a, int threads, int pixel_grid, int mcu_grid, cudaStream_t s) {
+}  // namespace
+
+// The forward and backward passes after the needed set and its compaction; bucket_cnt must
+// be zero on entry (and the frame, for the forward).
+void launch_float_forward(const FloatArgs& a, int threads, int pixel_grid, int mcu_grid, cudaStream_t s) {
   const int sblocks = (int)((a.tile_cap + 1 + kBucketScan - 1) / kBucketScan);
-  k_float_buckets<false><<<pixel_grid, threads, 0, s>>>(a);
+  k_float_buckets<kBucketCount><<<pixel_grid, threads, 0, s>>>(a);
   k_bucket_sums<<<sblocks, 256, 0, s>>>(a);
   k_bucket_offsets<<<sblocks, 256, 0, s>>>(a);
-  k_float_buckets<true><<<pixel_grid, threads, 0, s>>>(a);
+  k_float_buckets<kBucketPixel><<<pixel_grid, threads, 0, s>>>(a);
+  k_float_gather_fwd<<<mcu_grid, kFloatWarps * 32, 0, s>>>(a);
+}
+
+void launch_float_backward(const FloatArgs& a, int threads, int pixel_grid, int mcu_grid, cudaStream_t s) {
+  const int sblocks = (int)((a.tile_cap + 1 + kBucketScan - 1) / kBucketScan);
+  k_float_buckets<kBucketCount><<<pixel_grid, threads, 0, s>>>(a);
+  k_bucket_sums<<<sblocks, 256, 0, s>>>(a);
+  k_bucket_offsets<<<sblocks, 256, 0, s>>>(a);
+  k_float_buckets<kBucketGrad><<<pixel_grid, threads, 0, s>>>(a);
   k_float_gather<<<mcu_grid, kFloatWarps * 32, 0, s>>>(a);
 }
 
