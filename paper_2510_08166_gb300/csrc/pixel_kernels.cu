@@ -967,14 +967,27 @@ __global__ void __launch_bounds__(kFloatWarps * 32) k_float_gather_fwd(const __g
       ob = __ldg(a.bucket_off + pl);
       oe = min(__ldg(a.bucket_off + pl + 1), a.bucket_cap);
     }
-#pragma unroll 1
-    for (uint32_t cur = __ballot_sync(0xFFFFFFFFu, nd); cur; cur &= cur - 1) {
-      const int i = __ffs(cur) - 1;
-      const uint32_t m = m0 + (uint32_t)i;
-      const uint32_t e0 = __shfl_sync(0xFFFFFFFFu, ob, i), e1 = __shfl_sync(0xFFFFFFFFu, oe, i);
-      const float4* src = reinterpret_cast<const float4*>(a.coef + (size_t)m * 384);
+    // needed MCUs in order; the next one's coefficients are loaded while the current one is
+    // transformed and served
+    uint32_t cur = __ballot_sync(0xFFFFFFFFu, nd);
+    float4 cf[3];
+    if (cur) {
+      const float4* src = reinterpret_cast<const float4*>(a.coef + (size_t)(m0 + __ffs(cur) - 1) * 384);
 #pragma unroll
-      for (int k = 0; k < 3; ++k) reinterpret_cast<float4*>(c)[lane + 32 * k] = __ldg(src + lane + 32 * k);
+      for (int k = 0; k < 3; ++k) cf[k] = __ldg(src + lane + 32 * k);
+    }
+#pragma unroll 1
+    for (; cur; cur &= cur - 1) {
+      const int i = __ffs(cur) - 1;
+      const uint32_t e0 = __shfl_sync(0xFFFFFFFFu, ob, i), e1 = __shfl_sync(0xFFFFFFFFu, oe, i);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) reinterpret_cast<float4*>(c)[lane + 32 * k] = cf[k];
+      const uint32_t rest = cur & (cur - 1);
+      if (rest) {
+        const float4* src = reinterpret_cast<const float4*>(a.coef + (size_t)(m0 + __ffs(rest) - 1) * 384);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) cf[k] = __ldg(src + lane + 32 * k);
+      }
       __syncwarp();
       // pass 1: t[d][v][x] = sum_u A[x][u] c[d][v][u]
 #pragma unroll
