@@ -4,14 +4,16 @@
 // pixel of the frame needs are evicted (the paper evicts what is not visible).
 //
 // The paper keys a GPU hash map by a packed 32-bit MCU key. Our keys are the dense global
-// MCU ids (gids, one range per uploaded level), so the map is a direct array resident[gid]
-// (a block index), valid where the gid's bit in the residency bitmap is set. Free blocks sit
-// in a ring: positions [head, head + free_count) modulo the block count.
+// MCU ids (gids, one range per uploaded level), so the map is a residency bitmap over the
+// gids plus the slot array itself: a resident MCU was needed by the frame before (the cache
+// keeps nothing a frame does not need), so its slot from that frame still holds its block
+// (slot = 4 x block). Free blocks sit in a ring: positions [head, head + free_count) modulo
+// the block count.
 //
 // Per frame, after the mark pass has set flags[gid] (cache units needed, 0 = not needed), ONE
 // launch updates the cache. Each thread owns 16 gids (16 flag bytes and a 16-bit word of the
 // bitmap), so the decisions for one gid never race:
-//   flagged and resident      its slot is its block (a hit);
+//   flagged and resident      nothing to do: its slot already points at its block (a hit);
 //   flagged, not resident     it takes the next free block of the ring and joins the work
 //                             list (a miss);
 //   resident, not flagged     its block goes back to the ring, behind the blocks that were
@@ -68,17 +70,28 @@ __global__ void __launch_bounds__(kCacheThreads) k_cache_update(const __grid_con
     }
     const uint32_t hit = fm & rb, miss = fm & ~rb, evm = rb & ~fm;
     visible += __popc(fm);
-    // the 16 gids' blocks in one go (resident is padded to whole groups of 16)
+    auto clear_flags = [&] {  // for the next frame
+      if (first + 16 <= a.n)
+        reinterpret_cast<uint4*>(a.flags)[w] = make_uint4(0, 0, 0, 0);
+      else
+        for (uint32_t i = 0; first + i < a.n; ++i) a.flags[first + i] = 0;
+    };
+    if (fm == hit && evm == 0) {  // only hits: their slots already hold their blocks
+      if (any_flag) clear_flags();
+      continue;
+    }
+    // the 16 gids' slots in one go when some are evicted (the slot array holds whole groups
+    // of 16): an evicted MCU's block is its slot / 4
     uint32_t res[16];
-    if (rb) {
-      const uint4* rp = reinterpret_cast<const uint4*>(a.resident + first);
+    if (evm) {
+      const uint4* rp = reinterpret_cast<const uint4*>(a.slot + first);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const uint4 r4 = rp[q];
-        res[4 * q] = r4.x;
-        res[4 * q + 1] = r4.y;
-        res[4 * q + 2] = r4.z;
-        res[4 * q + 3] = r4.w;
+        res[4 * q] = r4.x >> 2;
+        res[4 * q + 1] = r4.y >> 2;
+        res[4 * q + 2] = r4.z >> 2;
+        res[4 * q + 3] = r4.w >> 2;
       }
     } else {
 #pragma unroll
@@ -96,13 +109,11 @@ __global__ void __launch_bounds__(kCacheThreads) k_cache_update(const __grid_con
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
       const uint32_t bit = 1u << i, g = first + i;
-      if (hit & bit) a.slot[g] = res[i] * 4;  // a block is 4 cache units
       if (miss & bit) {
         const uint32_t rank = __popc(miss & (bit - 1u)), pos = pos0 + rank;
         if (rank < nnow) {
           const uint32_t b = *ring_at(a, head + pos);
-          a.resident[g] = b;
-          a.slot[g] = b * 4;
+          a.slot[g] = b * 4;  // a block is 4 cache units
           nrb |= bit;
           if (pos < a.work_cap)
             a.work[pos] = g;
@@ -118,12 +129,7 @@ __global__ void __launch_bounds__(kCacheThreads) k_cache_update(const __grid_con
       if (evm & bit) *ring_at(a, head + free0 + e0 + __popc(evm & (bit - 1u))) = res[i];
     }
     if (nrb != rb) a.resbits[w] = (uint16_t)nrb;
-    if (any_flag) {  // clear for the next frame
-      if (first + 16 <= a.n)
-        reinterpret_cast<uint4*>(a.flags)[w] = make_uint4(0, 0, 0, 0);
-      else
-        for (uint32_t i = 0; first + i < a.n; ++i) a.flags[first + i] = 0;
-    }
+    if (any_flag) clear_flags();
   }
   visible = __reduce_add_sync(0xFFFFFFFFu, visible);
   if ((threadIdx.x & 31) == 0 && visible) atomicAdd(&a.cs->visible_acc, visible);
@@ -145,7 +151,6 @@ __global__ void __launch_bounds__(kCacheThreads) k_cache_update(const __grid_con
     const uint32_t g = a.deferred[j];
     if (j < served) {
       const uint32_t b = *ring_at(a, head + free0 + j);
-      a.resident[g] = b;
       a.slot[g] = b * 4;
       atomicOr(&a.resbits32[g >> 5], 1u << (g & 31));
       if (items + j < a.work_cap)

@@ -71,12 +71,11 @@ struct jt_ctx {
   // cross-frame block cache (jt_set_block_cache)
   bool persistent = false;
   bool unit_mode = false;  // some level has data-unit starts
-  uint32_t* resident = nullptr;   // [ngid]
   uint32_t* resbits = nullptr;    // residency bitmap, one bit per gid
   uint32_t* ring = nullptr;       // [nblocks] free blocks
   uint32_t* deferred = nullptr;   // [nblocks]
   uint32_t nblocks = 0;
-  uint64_t resident_ngid = 0;     // gids covered by `resident`
+  uint64_t resident_ngid = 0;     // gids covered by the residency bitmap
   CacheState* cstate = nullptr;
 
   // coefficient textures (float chain)
@@ -387,7 +386,6 @@ jt_status enqueue_scan(jt_ctx* c, uint64_t gid_lo, uint64_t gid_hi, cudaStream_t
 
 // Frees the cross-frame block cache's arrays.
 void cache_free(jt_ctx* c) {
-  dev_free(c->resident);
   dev_free(c->resbits);
   dev_free(c->ring);
   dev_free(c->deferred);
@@ -404,8 +402,6 @@ jt_status cache_reset(jt_ctx* c) {
   jt_status s;
   if (c->nblocks == 0) return fail(c, JT_ERR_INVALID_ARG, "the block cache needs at least one block");
   const uint64_t nbits = std::max<uint64_t>(1, (c->ngid + 31) / 32) * 4;  // whole 32-bit words
-  const uint64_t nres = std::max<uint64_t>(1, (c->ngid + 15) / 16) * 16;  // whole groups of 16 gids
-  if ((s = dev_alloc(c, &c->resident, nres * 4)) != JT_OK) return s;
   if ((s = dev_alloc(c, &c->resbits, nbits)) != JT_OK) return s;
   if ((s = dev_alloc(c, &c->ring, (size_t)c->nblocks * 4)) != JT_OK) return s;
   if ((s = dev_alloc(c, &c->deferred, (size_t)c->nblocks * 4)) != JT_OK) return s;
@@ -414,7 +410,6 @@ jt_status cache_reset(jt_ctx* c) {
   for (uint32_t i = 0; i < c->nblocks; ++i) fl[i] = i;  // blocks are handed out 0, 1, 2, ...
   CacheState cs{};
   cs.free_count = c->nblocks;
-  JT_CUDA(c, cudaMemset(c->resident, 0xFF, nres * 4));
   JT_CUDA(c, cudaMemset(c->resbits, 0, nbits));
   JT_CUDA(c, cudaMemcpy(c->ring, fl.data(), (size_t)c->nblocks * 4, cudaMemcpyHostToDevice));
   JT_CUDA(c, cudaMemcpy(c->cstate, &cs, sizeof cs, cudaMemcpyHostToDevice));
@@ -432,7 +427,6 @@ jt_status enqueue_cache_update(jt_ctx* c, cudaStream_t s) {
   CacheArgs a{};
   a.flags = c->flags;
   a.n = (uint32_t)c->ngid;
-  a.resident = c->resident;
   a.resbits = reinterpret_cast<uint16_t*>(c->resbits);
   a.resbits32 = c->resbits;
   a.ring = c->ring;

@@ -226,10 +226,10 @@ constexpr int kScanPerThread = 16;  // one 16-byte load
 constexpr int kScanTile = kScanThreads * kScanPerThread;  // 4096 flags
 void launch_scan(const ScanArgs& a, cudaStream_t s);  // two launches; tile_status: one word per tile
 
-// Cross-frame block cache (Sec. 4.1, Sec. 4.5): resident[gid] = the gid's block where its bit
-// in the residency bitmap is set; free blocks in a ring, positions [head, head + free_count)
-// modulo nblocks. A block is 4 cache units. Every counter but head, free_count, visible and
-// evicted is zero between frames.
+// Cross-frame block cache (Sec. 4.1, Sec. 4.5): a residency bitmap over the gids; a resident
+// gid's slot (4 x its block) is the one the previous frame gave it; free blocks in a ring,
+// positions [head, head + free_count) modulo nblocks. A block is 4 cache units. Every counter
+// but head, free_count, visible and evicted is zero between frames.
 struct CacheState {
   uint32_t head;         // ring position of the first free block
   uint32_t free_count;   // free blocks
@@ -244,7 +244,6 @@ struct CacheState {
 struct CacheArgs {
   uint8_t* flags;  // flags[gid], cleared by the update
   uint32_t n;      // gids
-  uint32_t* resident;   // [n]
   uint16_t* resbits;    // residency bitmap, 16 gids per word ...
   uint32_t* resbits32;  // ... the same memory as 32-bit words (a whole number of them)
   uint32_t* ring;       // [nblocks] free blocks
