@@ -465,24 +465,38 @@ __device__ __forceinline__ uint32_t blend_h(uint32_t c00, uint32_t c10, uint32_t
   return __byte_perm(h2_as_u32(rg), h2_as_u32(ba), 0x6420u);
 }
 
-// One pixel's colour from its taps: slots of up to four MCUs (predicated loads beyond the
-// first) and four texel gathers, then the blend (bilinear) or the texel itself (nearest).
+// Slot at a, or 0 without touching memory when p is false: a predicated load, so that no
+// branch orders one pixel's loads behind another's.
+__device__ __forceinline__ uint32_t ldg_slot_if(bool p, const uint32_t* a) {
+  uint32_t v;
+  asm("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\tmov.u32 %0, 0;\n\t@q ld.global.nc.u32 %0, [%1];\n\t}"
+      : "=r"(v)
+      : "l"(a), "r"((uint32_t)p));
+  return v;
+}
+
+// One pixel's colour from its taps: slots of up to four MCUs (predicated loads, the ones
+// beyond the first only when the footprint straddles MCUs) and four texel gathers, then the
+// blend (bilinear) or the texel itself (nearest). Branch-free: a pixel that is not shaded
+// (ok false) reads no slot and gathers its texels from unit 0 (the cache holds at least one
+// block), so the pixels of a lane overlap their chains.
 template <int FILTER>
 __device__ __forceinline__ uint32_t shade(const uint32_t* __restrict__ slot, const uint32_t* __restrict__ cache,
-                                          const PixL& P, int xa, int xb, int ya, int yb, float fx, float fy) {
+                                          const PixL& P, bool ok, int xa, int xb, int ya, int yb, float fx,
+                                          float fy) {
   const uint32_t s = P.shift, mwm = (1u << s) - 1u;
   const uint32_t xas = (uint32_t)xa >> s, xbs = (uint32_t)xb >> s;
   const uint32_t rowa = P.gid_base + ((uint32_t)ya >> s) * P.mcus_x;
-  const uint32_t o00 = __ldg(slot + rowa + xas);
+  const uint32_t o00 = ldg_slot_if(ok, slot + rowa + xas);
   const uint32_t ia = ((uint32_t)ya & mwm) << s, ja = (uint32_t)xa & mwm;
   if (FILTER == JT_FILTER_NEAREST) return __ldg(cache + (size_t)o00 * (kUnitBytes / 4) + (ia | ja));
   const uint32_t rowb = P.gid_base + ((uint32_t)yb >> s) * P.mcus_x;
   const bool sx = xbs != xas, sy = rowb != rowa;
-  uint32_t o10 = o00, o01 = o00;
-  if (sx) o10 = __ldg(slot + rowa + xbs);
-  if (sy) o01 = __ldg(slot + rowb + xas);
-  uint32_t o11 = sx ? o10 : o01;
-  if (sx && sy) o11 = __ldg(slot + rowb + xbs);
+  const uint32_t l10 = ldg_slot_if(ok && sx, slot + rowa + xbs);
+  const uint32_t l01 = ldg_slot_if(ok && sy, slot + rowb + xas);
+  const uint32_t l11 = ldg_slot_if(ok && sx && sy, slot + rowb + xbs);
+  const uint32_t o10 = sx ? l10 : o00, o01 = sy ? l01 : o00;
+  const uint32_t o11 = sx ? (sy ? l11 : o10) : o01;
   const uint32_t ib = ((uint32_t)yb & mwm) << s, jb = (uint32_t)xb & mwm;
   const uint32_t c00 = __ldg(cache + (size_t)o00 * (kUnitBytes / 4) + (ia | ja));
   const uint32_t c10 = __ldg(cache + (size_t)o10 * (kUnitBytes / 4) + (ia | jb));
@@ -519,7 +533,7 @@ __device__ __noinline__ uint32_t colour_any(const uint32_t* slot, const uint32_t
       clamp_taps(P.shift, nx, ny, xa, xb, ya, yb);
     }
   }
-  return shade<FILTER>(slot, cache, P, xa, xb, ya, yb, fx, fy);
+  return shade<FILTER>(slot, cache, P, true, xa, xb, ya, yb, fx, fy);
 }
 
 // A lane owns pixel lane + 32 k (k < NPX) of each step of a row (32 NPX pixels), so a warp's
@@ -534,7 +548,7 @@ __device__ __noinline__ uint32_t colour_any(const uint32_t* slot, const uint32_t
 // would end past the cache), and the all-zero record of keys outside the table addresses
 // unit 0, so no load needs a bound check.
 template <int FILTER, bool MULTI, int NPX>
-__global__ void __launch_bounds__(512) k_colorize(const __grid_constant__ ColorizeArgs a) {
+__global__ void __launch_bounds__(512, 2) k_colorize(const __grid_constant__ ColorizeArgs a) {
   const uint32_t* __restrict__ cache = reinterpret_cast<const uint32_t*>(a.cache);
   const uint32_t* __restrict__ slot = a.slot;
   const ViewSet& vs = a.views;
@@ -583,7 +597,8 @@ __global__ void __launch_bounds__(512) k_colorize(const __grid_constant__ Colori
             clamp_taps(P.shift, nxp, nyp, xa, xb, ya, yb);
           }
         }
-        if (ok) px[k] = shade<FILTER>(slot, cache, P, xa, xb, ya, yb, fx, fy);
+        const uint32_t c = shade<FILTER>(slot, cache, P, ok, xa, xb, ya, yb, fx, fy);
+        px[k] = ok ? c : px[k];
         slow |= (ok && !fast) ? (1u << k) : 0u;
       }
       if (slow) {  // rare: redo those pixels on the general path
