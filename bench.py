@@ -68,8 +68,8 @@ def peaks():
 
 def workload(compact: bool = False):
     import synth
-    ts = synth.config2_textures(compact=compact)
-    gb = synth.config2_gbuffer(ts)
+    ts = synth.scene_textures(compact=compact)
+    gb = synth.scene_gbuffer(ts)
     return ts, gb
 
 
@@ -197,10 +197,10 @@ def _cpu_band(rows):
     return oracle_frame_band(_CPU["o"], _CPU["gb"], slice(rows[0], rows[1]))
 
 
-def _cpu_decode4(i):
-    """Sequential full decode of config-4 texture i (one 4096^2 level); (seconds, MCUs, bytes)."""
+def _cpu_full_decode(i):
+    """Sequential full decode of full-decode texture i (one 4096^2 level); (seconds, MCUs, bytes)."""
     import oracle
-    e = _CPU["ts4"][i]
+    e = _CPU["ts_full"][i]
     t0 = time.perf_counter()
     d = oracle.Decoded(e.jfif)
     dt = time.perf_counter() - t0
@@ -208,9 +208,9 @@ def _cpu_decode4(i):
 
 
 class CpuPool:
-    def __init__(self, ts, gb, ts4, n: int):
+    def __init__(self, ts, gb, ts_full, n: int):
         import multiprocessing
-        _CPU.update(ts=ts, gb=gb, ts4=ts4)
+        _CPU.update(ts=ts, gb=gb, ts_full=ts_full)
         self.n = n
         self.pool = multiprocessing.get_context("fork").Pool(n)
 
@@ -230,10 +230,10 @@ class CpuPool:
         return {"value": frames * needed / wall, "frames": frames, "wall_s": wall,
                 "decoded_per_frame": decoded / frames}
 
-    def decode4(self, nt: int):
-        """Config-4 full decode: the n workers each decode textures round-robin from nt."""
+    def full_decode(self, nt: int):
+        """Full decode of 4096^2 textures: the n workers each decode textures round-robin from nt."""
         t0 = time.perf_counter()
-        res = self.pool.map(_cpu_decode4, [i % nt for i in range(self.n)], chunksize=1)
+        res = self.pool.map(_cpu_full_decode, [i % nt for i in range(self.n)], chunksize=1)
         wall = time.perf_counter() - t0
         mcus = sum(r[1] for r in res)
         out = sum(r[2] for r in res)
@@ -255,17 +255,17 @@ def cpu_model() -> str:
     return "unknown"
 
 
-def config4_cpu_textures():
-    """One 4096^2 level of each sampling at quality 90 (the config-4 texture shape)."""
+def full_decode_cpu_textures():
+    """One 4096^2 level of each sampling at quality 90 (the full-decode texture shape)."""
     import synth
-    ts = synth.config4_textures(ntex=2)  # texture 0 at 4:4:4, texture 1 at 4:2:0
+    ts = synth.full_decode_textures(ntex=2)  # texture 0 at 4:4:4, texture 1 at 4:2:0
     return [lv[0] for lv in ts.levels]
 
 
-def oracle_all(pool, ts, ts4, gb, needed):
-    """The CPU baseline: the 4K frame on 1 core (the line's value) and on all cores; config 4's
-    sequential full decode on 1 core and on all cores; config 5's FP64 backward on a band
-    (1 core)."""
+def oracle_all(pool, ts, ts_full, gb, needed):
+    """The CPU baseline: the 4K frame on 1 core (the line's value) and on all cores; the
+    sequential full decode of 4096^2 Q90 textures on 1 core and on all cores; the FP64 backward
+    of the coefficient scene on a band (1 core)."""
     import oracle
     import synth
     one = oracle_baseline(ts, gb)
@@ -275,9 +275,9 @@ def oracle_all(pool, ts, ts4, gb, needed):
                                 f"{pool.n} processes (cold tile cache per band: {fa['decoded_per_frame']:.0f} MCU "
                                 f"decodes per frame for {needed} needed)")
     res = {}
-    # config 4, one core: both samplings decoded in the main process
+    # full decode, one core: both samplings decoded in the main process
     t, mc, ob = 0.0, 0, 0
-    for e in ts4:
+    for e in ts_full:
         t0 = time.perf_counter()
         d = oracle.Decoded(e.jfif)
         t += time.perf_counter() - t0
@@ -285,17 +285,17 @@ def oracle_all(pool, ts, ts4, gb, needed):
         ob += int(d.rgba.size)
     res["full_decode_1_core"] = {"blocks_per_s": mc / t, "gbs": ob / t / 1e9,
                                  "sample": "one 4096^2 Q90 texture at 4:4:4 and one at 4:2:0"}
-    res["full_decode_all_cores"] = dict(pool.decode4(len(ts4)), sample="one 4096^2 Q90 texture per core, "
+    res["full_decode_all_cores"] = dict(pool.full_decode(len(ts_full)), sample="one 4096^2 Q90 texture per core, "
                                         "alternating 4:4:4 and 4:2:0")
-    # config 5, one core: FP64 loss and gradient over a band of 1/16 of the rows
-    ts5, coef, gb5, target = synth.config5()
-    r = gb5.height // 16
-    band = synth.GBuffer(gb5.width, r, gb5.uv[:r], gb5.tex_id[:r], gb5.mip[:r])
+    # coefficient scene, one core: FP64 loss and gradient over a band of 1/16 of the rows
+    ts_coef, coef, gb_coef, target = synth.coefficient_scene()
+    r = gb_coef.height // 16
+    band = synth.GBuffer(gb_coef.width, r, gb_coef.uv[:r], gb_coef.tex_id[:r], gb_coef.mip[:r])
     t0 = time.perf_counter()
     oracle.float_loss_grad(coef, band, target[:r])
     dt = time.perf_counter() - t0
-    res["adjoint_fp64_1_core"] = {"band_ms": 1000 * dt, "rows": r, "of_rows": gb5.height,
-                                  "full_frame_ms_scaled": 1000 * dt * gb5.height / r,
+    res["adjoint_fp64_1_core"] = {"band_ms": 1000 * dt, "rows": r, "of_rows": gb_coef.height,
+                                  "full_frame_ms_scaled": 1000 * dt * gb_coef.height / r,
                                   "sample": f"FP64 loss and gradient of the 1920x1080 plane's first {r} rows "
                                             f"(the full frame scaled by rows)"}
     return one, res
@@ -401,7 +401,7 @@ def run_views(ctx, ts, jt, dev, flush, stream, steps):
     pipeline."""
     import torch
     import synth
-    views = synth.config3_views(ts)
+    views = synth.eight_views(ts)
     dv = [jt.DeviceGBuffer.from_host(v, dev) for v in views]
     outs = [torch.empty((v.height, v.width, 4), dtype=torch.uint8, device=dev) for v in views]
     pairs = list(zip(dv, outs))
@@ -595,7 +595,7 @@ def run_raster(jt, ctx, ts, gb_host, dev, flush, stream, steps):
     import torch
     import synth
     d = synth.scene_desc(synth.SEED_BASE + 2, gb_host.width, gb_host.height, ts.sizes, ts.nlevels,
-                         synth.config2_pose(), nquads=200)
+                         synth.scene_pose(), nquads=200)
     gb = jt.DeviceGBuffer.empty(d.width, d.height, dev)
     out = torch.empty((d.height, d.width, 4), dtype=torch.uint8, device=dev)
     ms_raster = timed(lambda: ctx.raster_scene(d, gb), steps, 3, stream, flush)
@@ -639,7 +639,7 @@ def run_full_decode(jt, dev, flush, stream, steps, peak, tuning, ntex=256):
     import torch
     import synth
     t0 = time.perf_counter()
-    ts = synth.config4_textures(ntex=ntex)
+    ts = synth.full_decode_textures(ntex=ntex)
     encode_s = time.perf_counter() - t0
     units = sum(e.nmcu * (4 if e.sampling == 420 else 1) for _, _, e in ts.uploads())
     ctx = jt.Context(dev.index, max_cache_blocks=units // 4 + 1024)
@@ -758,7 +758,7 @@ def run_adjoint(jt, dev, flush, stream, steps, peak):
     L = sum (F - T)^2 to the coefficients."""
     import torch
     import synth
-    ts, coef, gb, target = synth.config5()
+    ts, coef, gb, target = synth.coefficient_scene()
     T, my, mx = coef.shape[:3]
     ctx = jt.Context(dev.index, max_cache_blocks=T * my * mx)  # a float tile for every MCU (4 KiB each)
     ctx.register_coeff_textures(0, T, mx * 16, my * 16)
@@ -822,11 +822,11 @@ def run_gpu(args, rank, world, local_rank):
             print(json.dumps({"adjoint": out}), flush=True)
         return 0
     ts, gb = workload(compact=not args.no_extra)
-    pool = ts4 = None
+    pool = ts_full = None
     if rank == 0 and world == 1 and not args.no_cpu and not args.quick:
         # the CPU baseline's workers are forked here, before the first CUDA call
-        ts4 = config4_cpu_textures()
-        pool = CpuPool(ts, gb, ts4, len(os.sched_getaffinity(0)))
+        ts_full = full_decode_cpu_textures()
+        pool = CpuPool(ts, gb, ts_full, len(os.sched_getaffinity(0)))
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     ctx = jt.Context(local_rank, max_cache_blocks=1 << 18)
@@ -975,7 +975,7 @@ def run_gpu(args, rank, world, local_rank):
     e2e_value = world * nblocks / (statistics.mean(e2e_ms) * 1e-3)
 
     if rank == 0:
-        cpu, cpu_legs = oracle_all(pool, ts, ts4, gb, nblocks) if pool is not None else (None, None)
+        cpu, cpu_legs = oracle_all(pool, ts, ts_full, gb, nblocks) if pool is not None else (None, None)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": frame_ms, "higher_is_better": True, "scaling": "weak",
@@ -1047,7 +1047,7 @@ def main():
                     help="textures of the full-decode leg (256 is the stated configuration)")
     ap.add_argument("--only", choices=["motion", "adjoint"], default=None,
                     help="run one leg alone and print its JSON (motion: the 1080p and VR motion legs; "
-                         "adjoint: the float chain's forward and backward on config 5)")
+                         "adjoint: the float chain's forward and backward on the coefficient scene)")
     ap.add_argument("--motion-reps", type=int, default=100,
                     help="turns of the motion legs after the warm-up turn (100 is the paper's protocol)")
     args = ap.parse_args()

@@ -808,8 +808,9 @@ __global__ void __launch_bounds__(256) k_bucket_offsets(const __grid_constant__ 
 }
 
 // consecutive coefficient MCUs per warp task (lane l < kGatherChunk checks MCU l): with 8
-// rather than 32 the 262,144 MCUs of config 5 make four times the tasks, so the grid's last
-// wave is nearly full (config 5 backward 0.308 ms with 8, 0.315 with 16, 0.364 with 32)
+// rather than 32 the 262,144 MCUs of sixteen 2048^2 coefficient textures make four times the
+// tasks, so the grid's last wave is nearly full (their backward over a 1920x1080 plane: 0.308 ms
+// with 8, 0.315 with 16, 0.364 with 32)
 constexpr uint32_t kGatherChunk = 8;
 
 // The weighted terms of bucket entry (c, wv) added into g (see k_float_gather).

@@ -433,7 +433,7 @@ def make_texture_set(seed: int, sizes, qualities, samplings, full_chain: bool = 
     return TextureSet(levels)
 
 
-def config1():
+def small_scene():
     """512x512 texture, Q80, 4:2:0; 256x256 affine G-buffer (17 deg, x1.3), nearest."""
     seed = SEED_BASE + 1
     ts = make_texture_set(seed, [(512, 512)], [80], [420], full_chain=False)
@@ -441,7 +441,7 @@ def config1():
     return ts, gb
 
 
-def config2_draws(ntex: int = 64):
+def scene_draws(ntex: int = 64):
     """Sizes (uniform in {1024,2048,4096}^2) and qualities (uniform in [50,95]) of the
     64 scene textures, without encoding them."""
     seed = SEED_BASE + 2
@@ -453,33 +453,33 @@ def config2_draws(ntex: int = 64):
     return sizes, quals
 
 
-def config2_textures(ntex: int = 64, threads: int | None = None, compact: bool = False) -> TextureSet:
+def scene_textures(ntex: int = 64, threads: int | None = None, compact: bool = False) -> TextureSet:
     """64 textures, sizes uniform in {1024,2048,4096}^2, Q uniform in [50,95], 4:2:0,
     full mip chains each level encoded separately."""
-    sizes, quals = config2_draws(ntex)
+    sizes, quals = scene_draws(ntex)
     return make_texture_set(SEED_BASE + 2, sizes, quals, [420] * ntex, full_chain=True, threads=threads,
                             compact=compact)
 
 
-def config2_pose() -> Pose:
+def scene_pose() -> Pose:
     return Pose(cam=(0.0, 1.7, 0.0), yaw=20.0, pitch=-25.0, vfov=60.0,
                 quad_seed=mix_seed(SEED_BASE + 2, 300, 0))
 
 
-def config2_gbuffer(ts: TextureSet, W: int = 3840, H: int = 2160) -> GBuffer:
-    return gbuffer_scene(SEED_BASE + 2, W, H, ts.sizes, ts.nlevels, config2_pose(), nquads=200)
+def scene_gbuffer(ts: TextureSet, W: int = 3840, H: int = 2160) -> GBuffer:
+    return gbuffer_scene(SEED_BASE + 2, W, H, ts.sizes, ts.nlevels, scene_pose(), nquads=200)
 
 
-def config3_views(ts: TextureSet):
+def eight_views(ts: TextureSet):
     """8 views: 1280x720, 1920x1080, 2560x1440, 3840x2160 and VR stereo 2x(2064x2208) at two
     poses (eye separation 0.064 m). The 720p view pitches up 35 degrees, above the ground, and
     holds six screen quads, so that the views' needed-block counts span more than 50x (the
     tests check the span on the needed sets)."""
-    return config3_views_for(ts.sizes, ts.nlevels)
+    return eight_views_for(ts.sizes, ts.nlevels)
 
 
-def config3_views_for(sizes, nlevels):
-    """config3_views from the textures' sizes and level counts alone."""
+def eight_views_for(sizes, nlevels):
+    """eight_views from the textures' sizes and level counts alone."""
     seed = SEED_BASE + 3
     qs = mix_seed(seed, 300, 0)
     views = []
@@ -506,7 +506,7 @@ def motion_views(ts: TextureSet, W: int = 1920, H: int = 1080, ndir: int = 60, s
     `step_deg` per frame, `ndir` frames for a full turn. Returns one list of G-buffers per
     direction: one view, or with `stereo` two eyes 0.064 m apart with a 90 degree field of
     view (the VR variant)."""
-    p0 = config2_pose()
+    p0 = scene_pose()
     seed = SEED_BASE + 2
     jobs = []
     for k in range(ndir):
@@ -526,7 +526,7 @@ def motion_views(ts: TextureSet, W: int = 1920, H: int = 1080, ndir: int = 60, s
     return out
 
 
-def config4_textures(ntex: int = 256, size: int = 4096, threads: int | None = None) -> TextureSet:
+def full_decode_textures(ntex: int = 256, size: int = 4096, threads: int | None = None) -> TextureSet:
     """Full-decode stress: `ntex` textures size^2 at Q90; the first half 4:4:4, the second
     half 4:2:0; level 0 only."""
     seed = SEED_BASE + 4
@@ -534,7 +534,7 @@ def config4_textures(ntex: int = 256, size: int = 4096, threads: int | None = No
     return make_texture_set(seed, [(size, size)] * ntex, [90] * ntex, samp, full_chain=False, threads=threads)
 
 
-def config5(ntex: int = 16, size: int = 2048, W: int = 1920, H: int = 1080):
+def coefficient_scene(ntex: int = 16, size: int = 2048, W: int = 1920, H: int = 1080):
     """Differentiable colourise: ntex textures size^2, 4:2:0, Q75, level 0 only, with the
     dequantised DCT coefficients as float32 [ntex, size/16, size/16, 6, 64]; a perspective
     plane G-buffer (no quads, level 0) and a seeded target frame [H, W, 3]."""

@@ -34,7 +34,7 @@ def _coef_set(seed, T, size, q=75):
 
 
 def _case(seed, T, size, W, H, kind="plane"):
-    """kind "plane": the config-5 perspective ground plane (touches most MCUs at these sizes);
+    """kind "plane": the coefficient scene's perspective ground plane (touches most MCUs at these sizes);
     "bands": one rotated, magnified window per texture 0..T-2 (a part of each texture's MCUs),
     texture T-1 untouched, 3 % empty pixels."""
     ts, coef = _coef_set(seed, T, size)

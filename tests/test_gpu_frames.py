@@ -192,7 +192,7 @@ def test_truncated_stream_reports_status(jt, short):
 
 
 def test_capacity_overflow_reports_status(jt):
-    ts, gb = synth.config1()
+    ts, gb = synth.small_scene()
     ctx = jt.Context(0, max_cache_blocks=100)  # 1024 MCUs are needed
     ctx.upload_set(ts)
     frame(ctx, jt.DeviceGBuffer.from_host(gb), 0, torch)
@@ -202,7 +202,7 @@ def test_capacity_overflow_reports_status(jt):
 
 
 def test_missing_level_reports_status(jt):
-    ts, gb = synth.config1()
+    ts, gb = synth.small_scene()
     ctx = jt.Context(0, 1 << 12)
     ctx.upload_set(ts)
     gb.mip[:4, :] = 3  # level 3 was never uploaded
@@ -213,7 +213,7 @@ def test_missing_level_reports_status(jt):
 
 
 def test_state_and_argument_errors(jt):
-    ts, gb = synth.config1()
+    ts, gb = synth.small_scene()
     ctx = jt.Context(0, 1 << 12)
     with pytest.raises(jt.JTError) as e:
         ctx.decode()

@@ -28,8 +28,8 @@ def jt():
 
 
 def test_4k_frame_in_benchmark_configuration(jt):
-    ts = synth.config2_textures()
-    gb = synth.config2_gbuffer(ts)
+    ts = synth.scene_textures()
+    gb = synth.scene_gbuffer(ts)
     ctx = jt.Context(0, max_cache_blocks=1 << 18)  # as the benchmark
     ctx.upload_set(ts)
     dgb = jt.DeviceGBuffer.from_host(gb)
@@ -56,8 +56,8 @@ def test_4k_frame_in_benchmark_configuration(jt):
     ctx.close()
 
 
-def test_config5_adjoint_full_size(jt):
-    ts, coef, gb, target = synth.config5()
+def test_coefficient_scene_adjoint_full_size(jt):
+    ts, coef, gb, target = synth.coefficient_scene()
     T, my, mx = coef.shape[:3]
     ctx = jt.Context(0, max_cache_blocks=T * my * mx)  # as the benchmark
     ctx.register_coeff_textures(0, T, mx * 16, my * 16)
@@ -134,8 +134,8 @@ def _sampled_pixels(o, gb, got, n, seed, filt=1):
 def test_4k_frame_compact_form(jt):
     """The 4K frame over the same textures in the paper's compact form: identical pixels to
     the standard form, work list and sampled tiles equal to the oracle's compact decode."""
-    ts = synth.config2_textures(compact=True)
-    gb = synth.config2_gbuffer(ts)
+    ts = synth.scene_textures(compact=True)
+    gb = synth.scene_gbuffer(ts)
     dgb = jt.DeviceGBuffer.from_host(gb)
     outs = []
     for compact in (False, True):
@@ -162,8 +162,8 @@ def test_4k_frame_compact_form(jt):
 def test_4k_frame_reduced_mips(jt):
     """The 4K frame with levels 1, 2, 4, 5, ... decoded from levels 0, 3, 6, ... by reduction:
     work list equal to the oracle's, sampled tiles bit-exact, sampled pixels within 1 LSB."""
-    ts = synth.config2_textures()
-    gb = synth.config2_gbuffer(ts)
+    ts = synth.scene_textures()
+    gb = synth.scene_gbuffer(ts)
     ctx = jt.Context(0, max_cache_blocks=1 << 18)
     o = oracle.TexSet()
     items = []
@@ -200,8 +200,8 @@ def test_batched_views_full_size(jt):
     """The 8 batched views (720p looking up, 1080p, 1440p, 4K and two VR stereo pairs) in one
     graph over the scene textures: the work list equals the oracle's union of the views'
     needed sets, and sampled pixels of every view are within 1 LSB of the oracle."""
-    ts = synth.config2_textures()
-    views = synth.config3_views(ts)
+    ts = synth.scene_textures()
+    views = synth.eight_views(ts)
     ctx = jt.Context(0, max_cache_blocks=1 << 18)
     ctx.upload_set(ts)
     dv = [jt.DeviceGBuffer.from_host(v) for v in views]

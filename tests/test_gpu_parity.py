@@ -28,8 +28,8 @@ def _ctx(jt, blocks=1 << 15):
 
 
 @pytest.mark.parametrize("filt", [0, 1, 2])
-def test_config1(jt, filt):
-    ts, gb = synth.config1()
+def test_affine_view_of_one_texture(jt, filt):
+    ts, gb = synth.small_scene()
     ctx = _ctx(jt)
     ctx.upload_set(ts)
     o = oracle.texset_from(ts)
@@ -119,7 +119,7 @@ def test_small_scene(jt, filt):
 
 def test_flags_cleared_between_frames(jt):
     """A second frame with a different G-buffer needs only its own MCUs."""
-    ts, gb = synth.config1()
+    ts, gb = synth.small_scene()
     ctx = _ctx(jt)
     ctx.upload_set(ts)
     o = oracle.texset_from(ts)
@@ -160,7 +160,7 @@ def test_levels_smaller_than_an_mcu_and_odd_sizes(jt, filt):
 def test_degenerate_g_buffers(jt):
     """A G-buffer with no textured pixel needs no MCU and writes (0, 0, 0, 255) everywhere; a
     1x1 G-buffer needs exactly its pixel's MCU; a 0-pixel G-buffer is an argument error."""
-    ts, _ = synth.config1()
+    ts, _ = synth.small_scene()
     ctx = _ctx(jt)
     ctx.upload_set(ts)
     o = oracle.texset_from(ts)

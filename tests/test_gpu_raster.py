@@ -54,8 +54,8 @@ def test_raster_bit_exact(jt, W, H, pose, nq, mips):
 def test_4k_scene_and_frame(jt):
     """The 4K scene in the benchmark's pose and its frame: the frame over the rastered
     G-buffer equals the frame over the oracle's G-buffer uploaded from the host."""
-    ts = synth.config2_textures(ntex=8)
-    pose = synth.config2_pose()
+    ts = synth.scene_textures(ntex=8)
+    pose = synth.scene_pose()
     d = synth.scene_desc(synth.SEED_BASE + 2, 3840, 2160, ts.sizes, ts.nlevels, pose, nquads=200)
     ctx = jt.Context(0, max_cache_blocks=1 << 18)
     ctx.upload_set(ts)

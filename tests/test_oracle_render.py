@@ -102,8 +102,8 @@ def _small_scene(seed=3, W=320, H=180, nq=30):
 
 
 @pytest.mark.parametrize("filt", [0, 1, 2])
-def test_mark_equals_brute_force_config1(filt):
-    ts, gb = synth.config1()
+def test_mark_equals_brute_force_small_scene(filt):
+    ts, gb = synth.small_scene()
     o = oracle.texset_from(ts)
     flags = o.mark(gb, filt)
     assert set(np.nonzero(flags)[0].tolist()) == _brute_marks(ts, gb, filt)

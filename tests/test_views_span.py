@@ -31,10 +31,10 @@ def needed_count(gb: synth.GBuffer, sizes) -> int:
     return int(np.unique(np.concatenate(keys)).size)
 
 
-def test_config3_views_span_more_than_50x():
-    sizes, _ = synth.config2_draws()
+def test_eight_views_span_more_than_50x():
+    sizes, _ = synth.scene_draws()
     nlevels = [int(np.log2(s[0])) + 1 for s in sizes]  # full chains down to 1 x 1
-    views = synth.config3_views_for(sizes, nlevels)
+    views = synth.eight_views_for(sizes, nlevels)
     assert [(v.width, v.height) for v in views] == [(1280, 720), (1920, 1080), (2560, 1440), (3840, 2160)] + \
         [(2064, 2208)] * 4
     counts = [needed_count(v, sizes) for v in views]
