@@ -106,7 +106,7 @@ struct jt_graph {
 
 namespace {
 
-constexpr uint64_t kMaxGids = 1ull << 26;   // count field of the scan status word
+constexpr uint64_t kMaxGids = 1ull << 26;   // MCUs over all levels: unit sums of 4 per MCU stay below 2^28
 constexpr uint64_t kMaxUnits = 1ull << 28;  // block cache of at most 64 GiB (2^28 units of 256 B)
 
 jt_status fail(jt_ctx* c, jt_status s, const char* fmt, ...) {
