@@ -293,7 +293,11 @@ jt_status jt_frame(jt_ctx* ctx, const jt_view* views, int nviews, int filter, jt
 
 /* The same frame captured once into a CUDA graph; replay with jt_graph_launch. The views'
  * pointers are baked into the graph: their contents may change between launches, the
- * buffers may not move. The graph belongs to ctx and must be destroyed before it. */
+ * buffers may not move. The context's own tables are baked in too: an upload of any kind
+ * (jt_upload_texture, jt_upload_texture_compact, jt_add_reduced_level, jt_set_du_offsets,
+ * jt_register_coeff_textures) or a jt_set_block_cache call after the capture makes
+ * jt_graph_launch refuse the graph with JT_ERR_STATE (nothing is launched); capture it
+ * again. The graph belongs to ctx and must be destroyed before it. */
 jt_status jt_frame_graph(jt_ctx* ctx, const jt_view* views, int nviews, int filter, jt_stream stream,
                          jt_graph** out);
 jt_status jt_graph_launch(jt_graph* g, jt_stream stream);

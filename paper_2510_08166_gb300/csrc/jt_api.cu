@@ -36,6 +36,10 @@ struct jt_ctx {
   std::string last_error;
   cudaStream_t last_stream = nullptr;
   Phase phase = Phase::Idle;
+  // Bumped whenever a device table or buffer that a captured graph bakes in is freed,
+  // moved or rewritten by an upload (descriptors, level tables, Huffman and quantisation
+  // sets, frame buffers, the block cache's arrays): graphs captured before are refused.
+  uint64_t generation = 0;
   jt_tuning tuning{};
   int decode_occ[33][17] = {};  // resident decode CTAs per SM by [MCUs per warp][warps per CTA]
 
@@ -102,6 +106,7 @@ struct jt_graph {
   jt_ctx* ctx;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  uint64_t generation = 0;  // the context's generation at capture
 };
 
 namespace {
@@ -230,6 +235,7 @@ bool build_table(const jt_huff_spec& spec, bool dc, HuffTable& t, std::string& w
 
 jt_status grow_frame_buffers(jt_ctx* c, uint64_t need) {
   if (need <= c->gid_cap) return JT_OK;
+  ++c->generation;
   uint64_t cap = std::max<uint64_t>(need, c->gid_cap + c->gid_cap / 2);
   cap = std::min<uint64_t>(std::max<uint64_t>(cap, 4096), kMaxGids);
   cap = (cap + 15) & ~15ull;
@@ -253,6 +259,7 @@ jt_status grow_frame_buffers(jt_ctx* c, uint64_t need) {
 }
 
 jt_status sync_descs(jt_ctx* c) {
+  ++c->generation;  // the level tables below are reallocated
   if (c->descs.size() > c->d_descs_cap) {
     dev_free(c->d_descs);
     size_t cap = std::max<size_t>(64, c->descs.size() * 2);
@@ -279,6 +286,7 @@ jt_status sync_descs(jt_ctx* c) {
 }
 
 jt_status sync_tables(jt_ctx* c) {
+  ++c->generation;
   dev_free(c->d_huff);
   jt_status s = dev_alloc(c, &c->d_huff, std::max<size_t>(1, c->hsets.size()) * sizeof(HuffSet));
   if (s != JT_OK) return s;
@@ -386,6 +394,7 @@ jt_status enqueue_scan(jt_ctx* c, uint64_t gid_lo, uint64_t gid_hi, cudaStream_t
 
 // Frees the cross-frame block cache's arrays.
 void cache_free(jt_ctx* c) {
+  ++c->generation;
   dev_free(c->resbits);
   dev_free(c->ring);
   dev_free(c->deferred);
@@ -1120,6 +1129,10 @@ jt_status jt_frame_graph(jt_ctx* c, const jt_view* views, int nviews, int filter
   if (s != JT_OK) return s;
   if (c->descs.empty()) return fail(c, JT_ERR_STATE, "no textures uploaded");
   DeviceGuard dg(c->device);
+  if (c->persistent && c->resident_ngid != c->ngid) {  // levels uploaded since: start the cache over
+    s = cache_reset(c);                                // here, since no allocation may run in a capture
+    if (s != JT_OK) return s;
+  }
   if (!c->capture_stream) JT_CUDA(c, cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
   cudaStream_t cs = c->capture_stream;
   // capture on the context's own stream (the caller's may be the legacy default stream)
@@ -1136,6 +1149,7 @@ jt_status jt_frame_graph(jt_ctx* c, const jt_view* views, int nviews, int filter
   jt_graph* gr = new jt_graph();
   gr->ctx = c;
   gr->graph = graph;
+  gr->generation = c->generation;
   e = cudaGraphInstantiate(&gr->exec, graph, 0);
   if (e != cudaSuccess) {
     cudaGraphDestroy(graph);
@@ -1150,6 +1164,9 @@ jt_status jt_graph_launch(jt_graph* g, jt_stream stream) {
   if (!g || !g->exec) return JT_ERR_INVALID_ARG;
   jt_ctx* c = g->ctx;
   if (c->phase == Phase::Marked) return fail(c, JT_ERR_STATE, "a marked frame is pending");
+  if (g->generation != c->generation)
+    return fail(c, JT_ERR_STATE, "the context's tables moved since the graph was captured (an upload or a "
+                                 "block-cache switch): capture it again");
   DeviceGuard dg(c->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   JT_CUDA(c, cudaGraphLaunch(g->exec, st));
